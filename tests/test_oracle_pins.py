@@ -1,0 +1,342 @@
+"""Pins for the CPU oracle: values printed in the paper, closed forms, textbook
+routines, brute force and invariants.  Nothing here touches the CUDA path."""
+import itertools
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_14688_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _pairs(mat, n):
+    """Product-matrix bits as {((s, x), (t, y))}."""
+    return {((int(a) // n, int(a) % n), (int(b) // n, int(b) % n)) for a, b in np.argwhere(mat)}
+
+
+def _as_pairs(lst):
+    return {(tuple(a), tuple(b)) for a, b in lst}
+
+
+# --- Sec. 3.3 worked example -------------------------------------------------
+
+def test_worked_example_trace_matches_paper():
+    gold = json.load(open(os.path.join(GOLDEN, "worked_example.json")))
+    g, r = W.worked_example()
+    res = oracle.kron_fixpoint(g, r, max_iter=10, trace=True)
+    n = g.n
+    it = gold["iterations"]
+    assert res.iterations == len(it) == 3
+    # iteration 1: M3,(1) exactly as printed, closure = M3 + one length-2 path
+    assert _pairs(res.trace_m3[0], n) == _as_pairs(it[0]["m3"])
+    assert _pairs(res.trace_c[0], n) == _as_pairs(it[0]["closure_new"])
+    # iterations 2 and 3: the M3 bits the text says are added
+    for k in (1, 2):
+        added = _pairs(res.trace_m3[k] & ~res.trace_m3[k - 1], n)
+        assert added == _as_pairs(it[k]["m3_added"])
+    # iteration 2: the three new closure paths named in the text are new
+    new_c = _pairs(res.trace_c[1] & ~res.trace_c[0], n)
+    assert _as_pairs(it[1]["closure_new_paths"]) <= new_c
+    # one S edge per iteration, then none
+    assert list(res.trace_new) == [len(x["new_edges_S"]) for x in it]
+    assert {tuple(p) for p in np.argwhere(res.m2[0]).tolist()} == {tuple(p) for p in gold["result_S"]}
+
+
+def test_worked_example_all_oracles_agree():
+    g, r = W.worked_example()
+    expect = np.zeros((1, 2, 2), dtype=bool)
+    expect[0, 0, 1] = expect[0, 1, 1] = True
+    assert (oracle.kron_fixpoint(g, r).m2 == expect).all()
+    assert (oracle.worklist(g, r) == expect).all()
+    assert (oracle.brute_reach(g, r, 8) == expect).all()
+
+
+def test_worked_example_shortest_path():
+    gold = json.load(open(os.path.join(GOLDEN, "worked_example.json")))
+    g, r = W.worked_example()
+    paths = oracle.brute_paths(g, r, 0, 1, 1, 6)
+    names = {"a": 0, "b": 1}
+    want = tuple((u, names[l], v) for u, l, v in gold["get_paths_1_1_S_shortest"])
+    assert paths[0] == want
+    # every returned path spells a^k b^k
+    for p in paths:
+        w = "".join("ab"[l] for _, l, _ in p)
+        k = len(w) // 2
+        assert w == "a" * k + "b" * k and k > 0
+
+
+# --- two coprime cycles: closed form -----------------------------------------
+
+def _two_cycle_answer(p, q):
+    n = p + q - 1
+    A = list(range(p))            # a-cycle vertices
+    Bv = [0] + list(range(p, n))  # b-cycle vertices
+    out = np.zeros((n, n), dtype=bool)
+    for x in A:
+        for y in Bv:
+            out[x, y] = True
+    return out
+
+
+@pytest.mark.parametrize("p,q", [(3, 4), (5, 6), (7, 8), (4, 9)])
+def test_two_cycles_closed_form_kron(p, q):
+    """a^k b^k from x on the a-cycle must end the a-run at 0 (k = -x mod p), the
+    b-run then ends at b-position k mod q; by the CRT every pair of the a-cycle
+    and the b-cycle is reached and the largest minimal k is p*q, so the loop
+    adds one edge per iteration for p*q iterations and stops on the next."""
+    g, r = W.two_cycles(p, q)
+    res = oracle.kron_fixpoint(g, r, max_iter=10000)
+    assert (res.m2[0] == _two_cycle_answer(p, q)).all()
+    assert res.iterations == p * q + 1
+    assert list(res.trace_new) == [1] * (p * q) + [0]
+    assert (oracle.worklist(g, r)[0] == _two_cycle_answer(p, q)).all()
+
+
+def test_two_cycles_full_size():
+    g, r = W.two_cycles(63, 64)
+    assert g.n == 126
+    want = _two_cycle_answer(63, 64)
+    assert want.sum() == 4032
+    assert (oracle.worklist(g, r)[0] == want).all()
+    res = oracle.kron_fixpoint(g, r, max_iter=5000)
+    assert res.iterations == 4033 and (res.m2[0] == want).all()
+
+
+# --- regular queries -------------------------------------------------------------
+
+def test_abc_dfa_is_the_regex():
+    d = W.abc_dfa_rsm()
+    for L in range(0, 9):
+        for w in itertools.product(range(3), repeat=L):
+            s = "".join("abc"[c] for c in w)
+            assert oracle.rsm_accepts(d, 3, 0, list(w)) == bool(re.fullmatch(W.ABC_REGEX, s)), s
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_rpq_equals_product_automaton_bfs(seed):
+    g, r = W.rpq_abc(n=48, out_deg=2, seed=seed)
+    bfs = oracle.product_bfs(g, r, list(range(g.n)))
+    a = oracle.kron_fixpoint(g, r, max_iter=10)
+    b = oracle.worklist(g, r)
+    assert (a.m2[0] == bfs).all()
+    assert (b[0] == bfs).all()
+    # RPQ: one appending iteration, then one that adds nothing
+    assert a.iterations <= 2 and a.trace_new[-1] == 0
+    # the empty word is in the language: the diagonal is answered
+    assert bfs.diagonal().all()
+
+
+def test_rpq_full_size_sampled_rows():
+    g, r = W.rpq_abc()
+    rows = list(range(0, g.n, 1024))
+    b = oracle.worklist(g, r, sources=rows)
+    bfs = oracle.product_bfs(g, r, rows)
+    assert (b[0][rows] == bfs).all()
+
+
+# --- context-free queries: two independent oracles and brute force -------------
+
+@pytest.mark.parametrize("seed", range(12))
+def test_kron_equals_worklist_random(seed):
+    n = 6 + seed % 5 * 4
+    g, r = W.small_random_instance(seed, n=n, m=3 * n, n_labels=2 + seed % 3)
+    a = oracle.kron_fixpoint(g, r, max_iter=100000)
+    b = oracle.worklist(g, r)
+    assert (a.m2 == b).all()
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_brute_force_exact_on_dags(seed):
+    """On a DAG every path has at most n-1 edges, so enumerating all paths up
+    to n-1 edges gives the exact answer of the reachability semantics."""
+    rng = np.random.Generator(np.random.PCG64(1000 + seed))
+    n, m, L = 5, 8, 2 + seed % 2
+    u = rng.integers(0, n, size=m)
+    v = rng.integers(0, n, size=m)
+    keep = u != v
+    s, d = np.minimum(u, v)[keep], np.maximum(u, v)[keep]
+    lbl = rng.integers(0, L, size=s.shape[0])
+    g = W.Graph(n, L, s.astype(np.uint32), lbl.astype(np.uint32), d.astype(np.uint32))
+    _, _, r = W.random_grammar(rng, L, 3, 10)
+    a = oracle.kron_fixpoint(g, r)
+    assert (a.m2 == oracle.brute_reach(g, r, n - 1)).all()
+    assert (oracle.worklist(g, r) == a.m2).all()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_brute_force_subset_on_cyclic(seed):
+    g, r = W.small_random_instance(500 + seed, n=4, m=6, n_labels=2)
+    a = oracle.kron_fixpoint(g, r)
+    br = oracle.brute_reach(g, r, 7)
+    assert not (br & ~a.m2).any()
+
+
+def test_nullable_grammar_epsilon_rule():
+    """S -> a S b | eps: every vertex pairs with itself, and a b between
+    distinct vertices joins them (needs the epsilon edges to take part in the
+    product, not only to sit in M2)."""
+    gram = {0: [(), (("t", 0), ("n", 0), ("t", 1))]}
+    r = W.grammar_to_rsm(gram, 1)
+    g = W.make_graph(4, 2, [(0, 0, 1), (1, 1, 2), (2, 0, 3), (3, 1, 0)])
+    a = oracle.kron_fixpoint(g, r)
+    want = np.eye(4, dtype=bool)
+    want[0, 2] = want[2, 0] = True
+    assert (a.m2[0] == want).all()
+    assert (oracle.worklist(g, r)[0] == want).all()
+    assert (oracle.brute_reach(g, r, 8)[0] == want).all()
+
+
+# --- grammar -> RSM and the membership chart ----------------------------------
+
+def _derivable(gram, nn, nt, k):
+    """Words of length <= k over terminals derivable from each nonterminal:
+    least fixpoint of L_N = union over alternatives of the concatenation of the
+    symbols' sets, truncated at length k."""
+    L = {a: set() for a in range(nn)}
+    changed = True
+    while changed:
+        changed = False
+        for a in range(nn):
+            for alt in gram.get(a, []):
+                acc = {()}
+                for kind, sym in alt:
+                    parts = {(sym,)} if kind == "t" else L[sym]
+                    acc = {x + y for x in acc for y in parts if len(x) + len(y) <= k}
+                    if not acc:
+                        break
+                new = acc - L[a]
+                if new:
+                    L[a] |= new
+                    changed = True
+    return L
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_grammar_rsm_language(seed):
+    rng = np.random.Generator(np.random.PCG64(77 + seed))
+    nt = 2
+    gram, nn, r = W.random_grammar(rng, nt, 3, 14)
+    k = 5
+    L = _derivable(gram, nn, nt, k)
+    for b in range(nn):
+        acc = set()
+        for ln in range(k + 1):
+            for w in itertools.product(range(nt), repeat=ln):
+                if oracle.rsm_accepts(r, nt, b, list(w)):
+                    acc.add(w)
+        assert acc == L[b], (gram, b)
+
+
+def test_paper_box_for_anbn():
+    """The CFG -> RSM construction gives the four-state box of Fig. 3."""
+    gram = {0: [(("t", 0), ("n", 0), ("t", 1)), (("t", 0), ("t", 1))]}
+    r = W.grammar_to_rsm(gram, 1)
+    ref = W.anbn_rsm()
+    assert r.n_states == 4
+    got = set(zip(r.tr_from.tolist(), r.tr_kind.tolist(), r.tr_sym.tolist(), r.tr_to.tolist()))
+    # states: 0 start, 1 final (shared), 2 after 'a', 3 after 'a S'
+    relabel = {0: 0, 1: 3, 2: 1, 3: 2}
+    got = {(relabel[a], k, s, relabel[b]) for a, k, s, b in got}
+    want = set(zip(ref.tr_from.tolist(), ref.tr_kind.tolist(), ref.tr_sym.tolist(), ref.tr_to.tolist()))
+    assert got == want
+
+
+# --- closure invariants ---------------------------------------------------------
+
+def _warshall(m):
+    c = m.copy()
+    for k in range(c.shape[0]):
+        c |= np.outer(c[:, k], c[k, :])
+    return c
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_closure_invariants(seed):
+    g, r = W.small_random_instance(900 + seed, n=7, m=16, n_labels=2)
+    a = oracle.kron_fixpoint(g, r, trace=True, want_c=True)
+    m3 = a.trace_m3[-1]
+    c = a.c
+    assert not (m3 & ~c).any()                                   # C contains M3
+    cc = (c.astype(np.uint8) @ c.astype(np.uint8)) > 0
+    assert not (cc & ~c).any()                                   # C . C in C
+    assert (c == _warshall(m3)).all()                            # = Warshall closure
+    rows = [(s, x) for s in range(r.n_states) for x in range(g.n)]
+    assert (oracle.closure_rows(g, r, a.m2, rows) == c).all()    # = BFS rows
+    # the final C's start-to-final blocks are exactly M2 minus epsilon edges
+    n = g.n
+    for b in range(r.n_boxes):
+        q0 = int(r.box_start[b])
+        got = np.zeros((n, n), dtype=bool)
+        for f in np.nonzero((r.state_box == b) & (r.state_final == 1))[0]:
+            got |= c[q0 * n:(q0 + 1) * n, f * n:(f + 1) * n]
+        if r.state_final[q0]:
+            got |= np.eye(n, dtype=bool)
+        assert (got == a.m2[b]).all()
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_monotone_growth(seed):
+    g, r = W.small_random_instance(1200 + seed, n=8, m=20, n_labels=2)
+    a = oracle.kron_fixpoint(g, r, trace=True)
+    for k in range(1, a.iterations):
+        assert not (a.trace_m3[k - 1] & ~a.trace_m3[k]).any()
+        assert not (a.trace_c[k - 1] & ~a.trace_c[k]).any()
+
+
+# --- metamorphic ------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(4))
+def test_vertex_permutation(seed):
+    g, r = W.small_random_instance(300 + seed, n=12, m=30, n_labels=3)
+    perm = np.random.Generator(np.random.PCG64(seed)).permutation(g.n).astype(np.uint32)
+    g2 = W.Graph(g.n, g.n_terminals, perm[g.src], g.lbl.copy(), perm[g.dst])
+    a = oracle.worklist(g, r)
+    b = oracle.worklist(g2, r)
+    assert (b[:, perm][:, :, perm] == a).all()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_state_renumbering(seed):
+    g, r = W.small_random_instance(400 + seed, n=10, m=24, n_labels=2)
+    perm = np.random.Generator(np.random.PCG64(seed)).permutation(r.n_states).astype(np.uint32)
+    fin = np.zeros_like(r.state_final)
+    fin[perm] = r.state_final
+    sb = np.zeros_like(r.state_box)
+    sb[perm] = r.state_box
+    r2 = W.RSM(r.n_states, r.n_boxes, r.start_box, perm[r.box_start], sb, fin,
+               perm[r.tr_from], r.tr_kind.copy(), r.tr_sym.copy(), perm[r.tr_to])
+    assert (oracle.kron_fixpoint(g, r2).m2 == oracle.kron_fixpoint(g, r).m2).all()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_adding_edges_never_removes_answers(seed):
+    g, r = W.small_random_instance(600 + seed, n=10, m=20, n_labels=2)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    extra = 6
+    g2 = W.Graph(g.n, g.n_terminals,
+                 np.concatenate([g.src, rng.integers(0, g.n, extra).astype(np.uint32)]),
+                 np.concatenate([g.lbl, rng.integers(0, g.n_terminals, extra).astype(np.uint32)]),
+                 np.concatenate([g.dst, rng.integers(0, g.n, extra).astype(np.uint32)]))
+    a, b = oracle.worklist(g, r), oracle.worklist(g2, r)
+    assert not (a & ~b).any()
+
+
+def test_duplicate_edges_are_merged():
+    g, r = W.small_random_instance(31, n=9, m=20, n_labels=2)
+    g2 = W.Graph(g.n, g.n_terminals, np.tile(g.src, 3), np.tile(g.lbl, 3), np.tile(g.dst, 3))
+    assert (oracle.kron_fixpoint(g2, r).m2 == oracle.kron_fixpoint(g, r).m2).all()
+
+
+def test_rejects_bad_input():
+    g, r = W.worked_example()
+    bad = W.Graph(2, 2, np.array([0], np.uint32), np.array([5], np.uint32), np.array([1], np.uint32))
+    with pytest.raises(oracle.OracleError):
+        oracle.kron_fixpoint(bad, r)
+    bad = W.Graph(2, 2, np.array([0], np.uint32), np.array([0], np.uint32), np.array([2], np.uint32))
+    with pytest.raises(oracle.OracleError):
+        oracle.worklist(bad, r)
