@@ -1,0 +1,271 @@
+/*
+ * cfpq.h -- C ABI of libcfpq: Kronecker-product context-free and regular path
+ * querying on one GB300 GPU (sm_103a).
+ *
+ * Method: Shemetova, Azimov, Orachev, Epelbaum, Grigorev, "One Algorithm to
+ * Evaluate Them All: Unified Linear Algebra Based Approach to Evaluate Both
+ * Regular and Context-Free Path Queries" (arXiv 2103.14688).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns an int status: CFPQ_OK (0) or a negative CFPQ_ERR_*
+ *    code; cfpq_status_string() names it and cfpq_last_error() gives the
+ *    context's last message.  No C++ exception crosses this boundary.
+ *  - The caller owns every buffer it passes.  Inputs are copied before the
+ *    call returns (host pointers) or read on the context's stream (device
+ *    pointers, *_device calls).  Output buffers follow a two-call protocol:
+ *    passing NULL (or a capacity too small) reports the required count and
+ *    returns CFPQ_ERR_BUFFER_TOO_SMALL when the buffer was too small.
+ *  - A context is used by one host thread at a time.  It owns its device
+ *    memory, obtained through the optional allocator callbacks in
+ *    cfpq_options (else cudaMallocAsync on the context's stream), and issues
+ *    all its work on the stream given to cfpq_create (a cudaStream_t; NULL
+ *    selects the legacy default stream).
+ *  - Vertices are 0-based (Sec. 2.1, Def. of an edge-labelled graph:
+ *    V = {0..|V|-1}).  Terminal labels are 0..n_terminals-1; nonterminals are
+ *    the RSM's boxes 0..n_boxes-1, a namespace disjoint from the terminals
+ *    (Sec. 2.3, Def. of an RSM: Sigma and B are disjoint).
+ *  - Product-graph index (Sec. 2.4, Def. of the Kronecker product, and the
+ *    getStates/getCoordinates helpers of Listing 1): a product vertex
+ *    (state s, vertex x) has index s * n + x.
+ */
+#ifndef CFPQ_H
+#define CFPQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define CFPQ_OK 0
+#define CFPQ_ERR_INVALID_ARG (-1)      /* bad pointer, id out of range, malformed RSM */
+#define CFPQ_ERR_OUT_OF_MEMORY (-2)    /* device or host allocation failed / budget exceeded */
+#define CFPQ_ERR_BUFFER_TOO_SMALL (-3) /* output capacity too small; the count was reported */
+#define CFPQ_ERR_TIMEOUT (-4)          /* iteration or round cap reached before the fixpoint */
+#define CFPQ_ERR_NOT_READY (-5)        /* result asked for before it exists */
+#define CFPQ_ERR_CUDA (-6)             /* a CUDA runtime call failed */
+#define CFPQ_ERR_STATE (-7)            /* calls in the wrong order (e.g. run before load) */
+#define CFPQ_ERR_UNSUPPORTED (-8)      /* size or mode this build does not handle */
+
+typedef struct cfpq_ctx cfpq_ctx;
+
+/* Device allocator callbacks.  alloc returns a device pointer of at least
+ * `bytes` bytes usable on `stream` (aligned to 256 bytes) or NULL; free
+ * releases it.  Both run on the calling host thread inside cfpq_* calls. */
+typedef void *(*cfpq_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*cfpq_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+/* Closure kernels (Listing 1, incremental transitive closure). */
+#define CFPQ_CLOSURE_AUTO 0      /* bit-packed rows; tensor-core tiles where a label matrix is dense */
+#define CFPQ_CLOSURE_BITPACKED 1 /* bit-packed uint64 rows only */
+#define CFPQ_CLOSURE_TC_FP8 2    /* dense tiles as 0/1 FP8-E4M3 tcgen05 products, FP32 accumulate, > 0 */
+#define CFPQ_CLOSURE_TC_I8 3     /* dense tiles as 0/1 INT8 tcgen05 products, INT32 accumulate, > 0 */
+
+/* Fixpoint loop driver (Listing 1, "while M2 is changing"). */
+#define CFPQ_LOOP_DEVICE 0 /* one CUDA-graph launch; device-side convergence flags */
+#define CFPQ_LOOP_HOST 1   /* host reads the convergence flags after every pass */
+
+typedef struct {
+    uint32_t struct_size;    /* sizeof(cfpq_options); set by cfpq_default_options */
+    int32_t device;          /* CUDA device ordinal */
+    uint32_t max_iterations; /* fixpoint iteration cap; 0 = no cap (the loop always ends) */
+    uint32_t max_rounds;     /* closure passes per iteration cap; 0 = no cap */
+    uint32_t closure_mode;   /* CFPQ_CLOSURE_* */
+    uint32_t loop_mode;      /* CFPQ_LOOP_* */
+    size_t memory_budget;    /* bytes of device memory a context may hold; 0 = no limit */
+    cfpq_alloc_fn alloc;     /* NULL = cudaMallocAsync */
+    cfpq_free_fn free;
+    void *alloc_user;
+} cfpq_options;
+
+/* Recursive state machine (Sec. 2.3, Def. of an RSM).  States are numbered
+ * globally 0..n_states-1; state_box[s] is the box owning s (boxes have
+ * disjoint state sets), box_start[b] its start state q_b^0, state_final[s]
+ * != 0 marks s as final in its box.  Transition k is
+ * tr_from[k] --(tr_kind[k], tr_sym[k])--> tr_to[k], with tr_kind 0 for a
+ * terminal symbol tr_sym < n_terminals and 1 for a call of box tr_sym; both
+ * ends must lie in the same box.  Nondeterminism is allowed; duplicate
+ * transitions are merged.  A regular query is a one-box RSM without calls
+ * (Sec. 3.1, index creation for RPQ). */
+typedef struct {
+    uint32_t n_states;
+    uint32_t n_boxes;
+    uint32_t start_box;           /* the initial box m */
+    uint32_t n_trans;
+    const uint32_t *box_start;    /* [n_boxes] */
+    const uint32_t *state_box;    /* [n_states] */
+    const uint8_t *state_final;   /* [n_states] */
+    const uint32_t *tr_from;      /* [n_trans] */
+    const uint32_t *tr_kind;      /* [n_trans] */
+    const uint32_t *tr_sym;       /* [n_trans] */
+    const uint32_t *tr_to;        /* [n_trans] */
+} cfpq_rsm;
+
+/* Statistics of one cfpq_run (or one query of a batch). */
+typedef struct {
+    uint32_t iterations;       /* loop iterations, counting the last one that adds no edge */
+    uint32_t rounds;           /* closure passes over all blocks, all iterations */
+    uint32_t status;           /* 0, or the CFPQ_ERR_* that stopped the loop */
+    uint32_t gpu_launches;     /* kernels launched by the call (graph nodes executed) */
+    uint64_t edges_added;      /* nonterminal edges found, epsilon edges included */
+    uint64_t closure_bits;     /* nnz(C3) at the fixpoint (counted on request, else 0) */
+    uint64_t m3_bits;          /* nnz(M3) at the fixpoint (counted on request, else 0) */
+    uint64_t row_ors;          /* bit-packed source-row ORs issued by the closure */
+    uint64_t tile_mmas;        /* dense tensor-core tile products issued */
+    uint64_t closure_blocks;   /* n x n state blocks of C3 held on the device */
+    uint64_t device_bytes;     /* device memory held by the query */
+    double ms_total;           /* wall time of the call (host clock) */
+} cfpq_run_stats;
+
+/* ---- context ---------------------------------------------------------------- */
+
+/* Fill *opt with defaults (device 0, no caps, AUTO closure, device loop). */
+int cfpq_default_options(cfpq_options *opt);
+
+/* Create a context on opt->device (NULL = defaults) issuing work on `stream`
+ * (a cudaStream_t).  *out receives the context; destroy it with cfpq_destroy. */
+int cfpq_create(cfpq_ctx **out, const cfpq_options *opt, void *stream);
+
+/* Release every device buffer and the context.  NULL is accepted. */
+int cfpq_destroy(cfpq_ctx *ctx);
+
+/* ---- inputs ------------------------------------------------------------------- */
+
+/* Load the labelled graph G = <V, E, L> as an edge list (Sec. 2.1): edge e is
+ * (src[e], label[e], dst[e]) with src, dst < n_vertices and label <
+ * n_terminals.  Host pointers; duplicate edges are merged, self-loops kept.
+ * An out-of-range id fails the call with CFPQ_ERR_INVALID_ARG and leaves no
+ * graph loaded.  Replaces any earlier graph and clears earlier results. */
+int cfpq_load_graph(cfpq_ctx *ctx, uint32_t n_vertices, uint32_t n_terminals, size_t n_edges,
+                    const uint32_t *src, const uint32_t *label, const uint32_t *dst);
+
+/* Same as cfpq_load_graph with the three arrays in device memory, read on the
+ * context's stream.  Range errors are detected on the device and reported by
+ * this call (it synchronises the stream once). */
+int cfpq_load_graph_device(cfpq_ctx *ctx, uint32_t n_vertices, uint32_t n_terminals, size_t n_edges,
+                           const uint32_t *d_src, const uint32_t *d_label, const uint32_t *d_dst);
+
+/* Load the query RSM (Sec. 2.3).  The RSM is copied.  Validation failures
+ * (state or box id out of range, a transition leaving its box, a terminal
+ * symbol >= the graph's n_terminals once both are loaded) return
+ * CFPQ_ERR_INVALID_ARG. */
+int cfpq_load_rsm(cfpq_ctx *ctx, const cfpq_rsm *rsm);
+
+/* ---- index creation (Listing 1) ------------------------------------------------- */
+
+/* Run index creation to its fixpoint: epsilon initialisation, then while M2
+ * changes: M3' = OR_l M1^l (x) A2^l over the new edges (computed tile by tile,
+ * never stored), incremental closure C3 <- (C3 + M3')^+, extraction of new
+ * nonterminal edges from the start-state to final-state blocks of C3.
+ * Returns CFPQ_ERR_TIMEOUT if an iteration or round cap stopped the loop
+ * (the partial index stays readable).  stats may be NULL. */
+int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats);
+
+/* Count nnz(C3) and nnz(M3) of the last run into *closure_bits / *m3_bits. */
+int cfpq_count_index(cfpq_ctx *ctx, uint64_t *closure_bits, uint64_t *m3_bits);
+
+/* ---- results ----------------------------------------------------------------------- */
+
+/* Pairs (x, y) with M2^box[x, y] = 1 (Theorem 1: a path x -> y whose word box
+ * derives), in (src, dst) lexicographic order.  src/dst hold `cap` entries;
+ * *count receives the number of pairs.  NULL buffers or a small cap return the
+ * count with CFPQ_ERR_BUFFER_TOO_SMALL (count-only query when both are NULL
+ * and cap is 0 returns CFPQ_OK). */
+int cfpq_get_reachable(cfpq_ctx *ctx, uint32_t box, uint32_t *src, uint32_t *dst, size_t cap, size_t *count);
+
+/* Number of pairs of M2^box, counted on the device; one 8-byte read back. */
+int cfpq_count_reachable(cfpq_ctx *ctx, uint32_t box, uint64_t *count);
+
+/* M2^box as host bit rows: row x occupies ceil(n/64) uint64 words at
+ * bits + x * ceil(n/64); bit y of the row is word y/64, bit y%64. */
+int cfpq_get_reachable_bits(cfpq_ctx *ctx, uint32_t box, uint64_t *bits);
+
+/* Rows of the closure index C3 = M3^+ (Listing 1's C3 at the fixpoint).  For
+ * k < n_rows the product vertex (row_state[k], row_vertex[k]) gets row
+ * out + k * ceil(Q*n/64) with bit t*n + y set iff (t, y) is reachable from it
+ * by a path of one or more M3 edges. */
+int cfpq_get_closure_rows(cfpq_ctx *ctx, uint32_t n_rows, const uint32_t *row_state,
+                          const uint32_t *row_vertex, uint64_t *out);
+
+/* All-path semantics (Sec. 3.2, Listing 2): the paths vs -> vf of at most
+ * max_len edges whose word box derives, deduplicated, in order of (length,
+ * lexicographic sequence of (src, label, dst) triples), at most max_paths of
+ * them.  Path k's edges are the triples edge_buf[3*j .. 3*j+2] for
+ * path_offsets[k] <= j < path_offsets[k+1] (path_offsets has max_paths + 1
+ * entries).  *n_paths receives the number of paths returned; *truncated (may
+ * be NULL) is set to 1 if max_paths stopped the enumeration.  The empty path
+ * is returned for vs == vf when box derives the empty word.
+ * CFPQ_ERR_BUFFER_TOO_SMALL if edge_cap (in triples) was too small. */
+int cfpq_extract_paths(cfpq_ctx *ctx, uint32_t box, uint32_t vs, uint32_t vf, uint32_t max_len, size_t max_paths,
+                       uint32_t *edge_buf, size_t edge_cap, size_t *path_offsets, size_t *n_paths,
+                       int *truncated);
+
+/* ---- batched index creation ------------------------------------------------------- */
+
+/* One query of a batch: a graph (host edge list) and an RSM. */
+typedef struct {
+    uint32_t n_vertices;
+    uint32_t n_terminals;
+    size_t n_edges;
+    const uint32_t *src;
+    const uint32_t *label;
+    const uint32_t *dst;
+    const cfpq_rsm *rsm;
+} cfpq_query;
+
+/* Run index creation for every query of the batch in shared persistent
+ * launches: one CUDA graph drives all queries' fixpoints, each pass of the
+ * closure covers the blocks of every unfinished query, and each query keeps
+ * its own convergence flag.  Results stay on the device until the next
+ * batch.  per_query_stats (may be NULL) has n_queries entries. */
+int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_query *queries, cfpq_run_stats *per_query_stats,
+                   cfpq_run_stats *total_stats);
+
+/* M2^box of query q of the last batch as host bit rows (layout of
+ * cfpq_get_reachable_bits with that query's n). */
+int cfpq_batch_get_reachable_bits(cfpq_ctx *ctx, uint32_t q, uint32_t box, uint64_t *bits);
+
+/* ---- serving ------------------------------------------------------------------------- */
+
+typedef struct cfpq_server cfpq_server;
+
+/* A server keeps one graph resident and answers RSM queries submitted at any
+ * time.  Each admitted query gets its own device state (sized by its
+ * |Q|n x |Q|n closure blocks) and joins the running batch at the next pass;
+ * queries that do not fit the memory budget wait until running ones finish
+ * (continuous batching). */
+int cfpq_server_create(cfpq_server **out, const cfpq_options *opt, void *stream, uint32_t n_vertices,
+                       uint32_t n_terminals, size_t n_edges, const uint32_t *src, const uint32_t *label,
+                       const uint32_t *dst);
+int cfpq_server_destroy(cfpq_server *srv);
+
+/* Queue a query; *ticket identifies it.  Never blocks on the GPU. */
+int cfpq_submit(cfpq_server *srv, const cfpq_rsm *rsm, uint64_t *ticket);
+
+/* Advance the server: admit waiting queries that fit, run one fixpoint pass
+ * for every running query, retire finished ones.  *n_running / *n_waiting
+ * (may be NULL) report the queue sizes after the step. */
+int cfpq_server_step(cfpq_server *srv, uint32_t *n_running, uint32_t *n_waiting);
+
+/* *done = 1 once the query's fixpoint is reached (its result is readable). */
+int cfpq_poll(cfpq_server *srv, uint64_t ticket, int *done);
+
+/* M2^box of a finished query as host bit rows (layout of
+ * cfpq_get_reachable_bits). */
+int cfpq_result_reachable_bits(cfpq_server *srv, uint64_t ticket, uint32_t box, uint64_t *bits);
+
+/* Free a finished query's device state and forget the ticket. */
+int cfpq_release(cfpq_server *srv, uint64_t ticket);
+
+/* ---- diagnostics ----------------------------------------------------------------------- */
+
+const char *cfpq_status_string(int status);
+const char *cfpq_last_error(const cfpq_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CFPQ_H */

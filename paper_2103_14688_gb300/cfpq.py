@@ -1,0 +1,364 @@
+"""Thin Python binding of libcfpq (include/cfpq.h).
+
+Argument marshalling only: every step of index creation runs inside the CUDA
+library.  The functions keep the C names; the :class:`Context` wrapper adds
+ownership and numpy conversion.  PyTorch supplies device memory (through the
+allocator callbacks of ``cfpq_options``) and the CUDA stream.
+
+The library must exist: :func:`load` builds it with nvcc for sm_103a when it
+is missing and raises when that fails.  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from ctypes import (CFUNCTYPE, POINTER, Structure, c_char_p, c_double, c_int, c_int32, c_size_t,
+                    c_uint8, c_uint32, c_uint64, c_void_p)
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+CFPQ_OK = 0
+CFPQ_ERR_INVALID_ARG = -1
+CFPQ_ERR_OUT_OF_MEMORY = -2
+CFPQ_ERR_BUFFER_TOO_SMALL = -3
+CFPQ_ERR_TIMEOUT = -4
+CFPQ_ERR_NOT_READY = -5
+CFPQ_ERR_CUDA = -6
+CFPQ_ERR_STATE = -7
+CFPQ_ERR_UNSUPPORTED = -8
+
+CFPQ_CLOSURE_AUTO = 0
+CFPQ_CLOSURE_BITPACKED = 1
+CFPQ_CLOSURE_TC_FP8 = 2
+CFPQ_CLOSURE_TC_I8 = 3
+CFPQ_LOOP_DEVICE = 0
+CFPQ_LOOP_HOST = 1
+
+cfpq_alloc_fn = CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+cfpq_free_fn = CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
+
+
+class cfpq_options(Structure):
+    _fields_ = [("struct_size", c_uint32), ("device", c_int32), ("max_iterations", c_uint32),
+                ("max_rounds", c_uint32), ("closure_mode", c_uint32), ("loop_mode", c_uint32),
+                ("memory_budget", c_size_t), ("alloc", cfpq_alloc_fn), ("free", cfpq_free_fn),
+                ("alloc_user", c_void_p)]
+
+
+class cfpq_rsm(Structure):
+    _fields_ = [("n_states", c_uint32), ("n_boxes", c_uint32), ("start_box", c_uint32), ("n_trans", c_uint32),
+                ("box_start", POINTER(c_uint32)), ("state_box", POINTER(c_uint32)),
+                ("state_final", POINTER(c_uint8)), ("tr_from", POINTER(c_uint32)),
+                ("tr_kind", POINTER(c_uint32)), ("tr_sym", POINTER(c_uint32)), ("tr_to", POINTER(c_uint32))]
+
+
+class cfpq_run_stats(Structure):
+    _fields_ = [("iterations", c_uint32), ("rounds", c_uint32), ("status", c_uint32), ("gpu_launches", c_uint32),
+                ("edges_added", c_uint64), ("closure_bits", c_uint64), ("m3_bits", c_uint64),
+                ("row_ors", c_uint64), ("tile_mmas", c_uint64), ("closure_blocks", c_uint64),
+                ("device_bytes", c_uint64), ("ms_total", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class cfpq_query(Structure):
+    _fields_ = [("n_vertices", c_uint32), ("n_terminals", c_uint32), ("n_edges", c_size_t),
+                ("src", POINTER(c_uint32)), ("label", POINTER(c_uint32)), ("dst", POINTER(c_uint32)),
+                ("rsm", POINTER(cfpq_rsm))]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+class CfpqError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def library_path() -> str:
+    from . import build as _b
+    return _b.LIB
+
+
+def load():
+    """Load libcfpq.so, building it first if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _b
+        path = _b.build()
+        lib = ctypes.CDLL(path)
+        _declare(lib)
+        _lib = lib
+        return lib
+
+
+def _declare(lib):
+    P = c_void_p
+    u32p = POINTER(c_uint32)
+    u64p = POINTER(c_uint64)
+    sig = {
+        "cfpq_default_options": (c_int, [POINTER(cfpq_options)]),
+        "cfpq_create": (c_int, [POINTER(P), POINTER(cfpq_options), P]),
+        "cfpq_destroy": (c_int, [P]),
+        "cfpq_load_graph": (c_int, [P, c_uint32, c_uint32, c_size_t, u32p, u32p, u32p]),
+        "cfpq_load_graph_device": (c_int, [P, c_uint32, c_uint32, c_size_t, P, P, P]),
+        "cfpq_load_rsm": (c_int, [P, POINTER(cfpq_rsm)]),
+        "cfpq_run": (c_int, [P, POINTER(cfpq_run_stats)]),
+        "cfpq_count_index": (c_int, [P, u64p, u64p]),
+        "cfpq_get_reachable": (c_int, [P, c_uint32, u32p, u32p, c_size_t, POINTER(c_size_t)]),
+        "cfpq_count_reachable": (c_int, [P, c_uint32, u64p]),
+        "cfpq_get_reachable_bits": (c_int, [P, c_uint32, P]),
+        "cfpq_get_closure_rows": (c_int, [P, c_uint32, u32p, u32p, P]),
+        "cfpq_extract_paths": (c_int, [P, c_uint32, c_uint32, c_uint32, c_uint32, c_size_t, u32p, c_size_t,
+                                       POINTER(c_size_t), POINTER(c_size_t), POINTER(c_int)]),
+        "cfpq_batch_run": (c_int, [P, c_uint32, POINTER(cfpq_query), POINTER(cfpq_run_stats),
+                                   POINTER(cfpq_run_stats)]),
+        "cfpq_batch_get_reachable_bits": (c_int, [P, c_uint32, c_uint32, P]),
+        "cfpq_server_create": (c_int, [POINTER(P), POINTER(cfpq_options), P, c_uint32, c_uint32, c_size_t,
+                                       u32p, u32p, u32p]),
+        "cfpq_server_destroy": (c_int, [P]),
+        "cfpq_submit": (c_int, [P, POINTER(cfpq_rsm), u64p]),
+        "cfpq_server_step": (c_int, [P, u32p, u32p]),
+        "cfpq_poll": (c_int, [P, c_uint64, POINTER(c_int)]),
+        "cfpq_result_reachable_bits": (c_int, [P, c_uint64, c_uint32, P]),
+        "cfpq_release": (c_int, [P, c_uint64]),
+        "cfpq_status_string": (c_char_p, [c_int]),
+        "cfpq_last_error": (c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def _u32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+
+
+def _u32p(a: np.ndarray):
+    return a.ctypes.data_as(POINTER(c_uint32))
+
+
+class RSMArgs:
+    """Holds a cfpq_rsm and the arrays it points to."""
+
+    def __init__(self, r):
+        self.box_start = _u32(r.box_start)
+        self.state_box = _u32(r.state_box)
+        self.state_final = np.ascontiguousarray(r.state_final, dtype=np.uint8)
+        self.tr_from = _u32(r.tr_from)
+        self.tr_kind = _u32(r.tr_kind)
+        self.tr_sym = _u32(r.tr_sym)
+        self.tr_to = _u32(r.tr_to)
+        self.c = cfpq_rsm(r.n_states, r.n_boxes, r.start_box, len(self.tr_from), _u32p(self.box_start),
+                          _u32p(self.state_box), self.state_final.ctypes.data_as(POINTER(c_uint8)),
+                          _u32p(self.tr_from), _u32p(self.tr_kind), _u32p(self.tr_sym), _u32p(self.tr_to))
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations to PyTorch's caching allocator."""
+
+    def __init__(self, device: int):
+        import torch
+        self.torch = torch
+        self.device = device
+
+        def alloc(nbytes, stream, user):
+            try:
+                return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream or 0)
+            except Exception:
+                return None
+
+        def free(ptr, nbytes, stream, user):
+            self.torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc = cfpq_alloc_fn(alloc)
+        self.free = cfpq_free_fn(free)
+
+
+def default_options(**kw) -> cfpq_options:
+    lib = load()
+    o = cfpq_options()
+    lib.cfpq_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def status_string(code: int) -> str:
+    return load().cfpq_status_string(code).decode()
+
+
+class Context:
+    """A cfpq_ctx on one device and stream.
+
+    ``use_torch`` routes allocations through torch's caching allocator and
+    uses torch's current stream (the default); otherwise the library uses
+    cudaMallocAsync on the legacy default stream.
+    """
+
+    def __init__(self, device: int = 0, use_torch: bool = True, stream=None, **options):
+        self.lib = load()
+        self._alloc = None
+        o = default_options(device=device, **options)
+        if use_torch:
+            import torch
+            torch.cuda.init()
+            self._alloc = _TorchAllocator(device)
+            o.alloc = self._alloc.alloc
+            o.free = self._alloc.free
+            if stream is None:
+                with torch.cuda.device(device):
+                    stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        self._opt = o
+        h = c_void_p()
+        self._check(self.lib.cfpq_create(ctypes.byref(h), ctypes.byref(o), c_void_p(stream or 0)), "cfpq_create",
+                    with_ctx=False)
+        self.h = h
+        self.n = None
+        self.n_boxes = None
+        self.n_states = None
+
+    # -- plumbing --
+    def _check(self, rc: int, what: str, with_ctx: bool = True):
+        if rc != CFPQ_OK:
+            msg = self.lib.cfpq_status_string(rc).decode()
+            if with_ctx and getattr(self, "h", None):
+                detail = self.lib.cfpq_last_error(self.h)
+                if detail:
+                    msg += ": " + detail.decode()
+            raise CfpqError(rc, f"{what}: {msg}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cfpq_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- inputs --
+    def load_graph(self, g):
+        s, l, d = _u32(g.src), _u32(g.lbl), _u32(g.dst)
+        self._check(self.lib.cfpq_load_graph(self.h, g.n, g.n_terminals, len(s), _u32p(s), _u32p(l), _u32p(d)),
+                    "cfpq_load_graph")
+        self.n = g.n
+
+    def load_graph_device(self, n: int, n_terminals: int, src, lbl, dst):
+        """src/lbl/dst: torch CUDA tensors of int32/uint32 (same length)."""
+        m = int(src.numel())
+        self._check(self.lib.cfpq_load_graph_device(self.h, n, n_terminals, m, c_void_p(src.data_ptr()),
+                                                    c_void_p(lbl.data_ptr()), c_void_p(dst.data_ptr())),
+                    "cfpq_load_graph_device")
+        self.n = n
+
+    def load_rsm(self, r):
+        self._rsm = RSMArgs(r)
+        self._check(self.lib.cfpq_load_rsm(self.h, ctypes.byref(self._rsm.c)), "cfpq_load_rsm")
+        self.n_boxes = r.n_boxes
+        self.n_states = r.n_states
+
+    # -- index creation --
+    def run(self) -> cfpq_run_stats:
+        st = cfpq_run_stats()
+        self._check(self.lib.cfpq_run(self.h, ctypes.byref(st)), "cfpq_run")
+        return st
+
+    def count_index(self) -> Tuple[int, int]:
+        a, b = c_uint64(), c_uint64()
+        self._check(self.lib.cfpq_count_index(self.h, ctypes.byref(a), ctypes.byref(b)), "cfpq_count_index")
+        return a.value, b.value
+
+    # -- results --
+    def reachable_words(self, box: int = 0) -> np.ndarray:
+        wn = (self.n + 63) // 64
+        out = np.zeros(self.n * wn, dtype=np.uint64)
+        self._check(self.lib.cfpq_get_reachable_bits(self.h, box, c_void_p(out.ctypes.data)),
+                    "cfpq_get_reachable_bits")
+        return out.reshape(self.n, wn)
+
+    def reachable_bits(self, box: int = 0) -> np.ndarray:
+        w = self.reachable_words(box)
+        return np.unpackbits(w.view(np.uint8), axis=1, bitorder="little")[:, : self.n].astype(bool)
+
+    def reachable_pairs(self, box: int = 0) -> np.ndarray:
+        cnt = c_size_t()
+        rc = self.lib.cfpq_get_reachable(self.h, box, None, None, 0, ctypes.byref(cnt))
+        self._check(rc, "cfpq_get_reachable")
+        k = cnt.value
+        s = np.zeros(max(k, 1), dtype=np.uint32)
+        d = np.zeros(max(k, 1), dtype=np.uint32)
+        self._check(self.lib.cfpq_get_reachable(self.h, box, _u32p(s), _u32p(d), k, ctypes.byref(cnt)),
+                    "cfpq_get_reachable")
+        return np.stack([s[:k], d[:k]], axis=1)
+
+    def count_reachable(self, box: int = 0) -> int:
+        c = c_uint64()
+        self._check(self.lib.cfpq_count_reachable(self.h, box, ctypes.byref(c)), "cfpq_count_reachable")
+        return c.value
+
+    def closure_rows(self, rows: Sequence[Tuple[int, int]]) -> np.ndarray:
+        """Rows of C3 as bool [len(rows), Q*n], column t*n + y."""
+        rs = _u32([a for a, _ in rows])
+        rv = _u32([b for _, b in rows])
+        N = self.n_states * self.n
+        wN = (N + 63) // 64
+        out = np.zeros(len(rows) * wN, dtype=np.uint64)
+        self._check(self.lib.cfpq_get_closure_rows(self.h, len(rows), _u32p(rs), _u32p(rv),
+                                                   c_void_p(out.ctypes.data)), "cfpq_get_closure_rows")
+        return np.unpackbits(out.reshape(len(rows), wN).view(np.uint8), axis=1, bitorder="little")[:, :N].astype(bool)
+
+    def extract_paths(self, box: int, vs: int, vf: int, max_len: int, max_paths: int = 1 << 16,
+                      edge_cap: int = 1 << 22):
+        edges = np.zeros(3 * max(edge_cap, 1), dtype=np.uint32)
+        offs = (c_size_t * (max_paths + 1))()
+        npaths = c_size_t()
+        trunc = c_int()
+        self._check(self.lib.cfpq_extract_paths(self.h, box, vs, vf, max_len, max_paths, _u32p(edges), edge_cap,
+                                                offs, ctypes.byref(npaths), ctypes.byref(trunc)),
+                    "cfpq_extract_paths")
+        out = []
+        for i in range(npaths.value):
+            a, b = offs[i], offs[i + 1]
+            out.append(tuple((int(edges[3 * j]), int(edges[3 * j + 1]), int(edges[3 * j + 2])) for j in range(a, b)))
+        return out, bool(trunc.value)
+
+    # -- batches --
+    def batch_run(self, queries) -> Tuple[List[cfpq_run_stats], cfpq_run_stats]:
+        keep = []
+        arr = (cfpq_query * len(queries))()
+        for i, (g, r) in enumerate(queries):
+            s, l, d = _u32(g.src), _u32(g.lbl), _u32(g.dst)
+            ra = RSMArgs(r)
+            keep.append((s, l, d, ra))
+            arr[i] = cfpq_query(g.n, g.n_terminals, len(s), _u32p(s), _u32p(l), _u32p(d), ctypes.pointer(ra.c))
+        per = (cfpq_run_stats * len(queries))()
+        tot = cfpq_run_stats()
+        self._check(self.lib.cfpq_batch_run(self.h, len(queries), arr, per, ctypes.byref(tot)), "cfpq_batch_run")
+        self._batch_n = [g.n for g, _ in queries]
+        return list(per), tot
+
+    def batch_reachable_bits(self, q: int, box: int = 0) -> np.ndarray:
+        n = self._batch_n[q]
+        wn = (n + 63) // 64
+        out = np.zeros(n * wn, dtype=np.uint64)
+        self._check(self.lib.cfpq_batch_get_reachable_bits(self.h, q, box, c_void_p(out.ctypes.data)),
+                    "cfpq_batch_get_reachable_bits")
+        return np.unpackbits(out.reshape(n, wn).view(np.uint8), axis=1, bitorder="little")[:, :n].astype(bool)

@@ -1,0 +1,727 @@
+// cfpq_api.cu -- the C ABI of libcfpq (include/cfpq.h).
+//
+// Every entry point catches C++ exceptions and maps CUDA errors to status
+// codes; nothing but plain C types crosses the boundary.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "cfpq_engine.cuh"
+
+using namespace cfpq;
+
+struct cfpq_ctx {
+    cfpq_options opt;
+    cudaStream_t stream = nullptr;
+    Allocator A;
+    std::string err;
+    GraphDev graph;
+    bool has_graph = false;
+    bool has_rsm = false;
+    QueryDev query;
+    Executor exec;
+    uint64_t exec_generation = ~0ull;
+    bool exec_dirty = true;
+    bool has_result = false;
+    // batch
+    std::vector<std::unique_ptr<GraphDev>> bgraphs;
+    std::vector<std::unique_ptr<QueryDev>> bqueries;
+    Executor bexec;
+    bool has_batch = false;
+    // scratch for small transfers
+    DBuf counter;
+    DBuf rows_ptrs, rows_idx, rows_out;
+    ~cfpq_ctx() {
+        // Buffers are released by their destructors through A (declared first).
+    }
+};
+
+namespace {
+
+constexpr uint32_t kDefaultPassCap = 1u << 20;
+
+int fail(cfpq_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+#define API_TRY try {
+#define API_CATCH(ctx)                                                   \
+    }                                                                    \
+    catch (const std::bad_alloc &) {                                     \
+        return fail(ctx, CFPQ_ERR_OUT_OF_MEMORY, "host allocation failed"); \
+    }                                                                    \
+    catch (const std::exception &e) {                                    \
+        return fail(ctx, CFPQ_ERR_CUDA, e.what());                       \
+    }                                                                    \
+    catch (...) {                                                        \
+        return fail(ctx, CFPQ_ERR_CUDA, "unknown exception");            \
+    }
+
+#define CK(ctx, call)                                                                               \
+    do {                                                                                            \
+        cudaError_t _e = (call);                                                                    \
+        if (_e != cudaSuccess) return fail(ctx, CFPQ_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+int set_device(cfpq_ctx *ctx) {
+    CK(ctx, cudaSetDevice(ctx->opt.device));
+    return CFPQ_OK;
+}
+
+uint32_t pass_cap(const cfpq_options &o) { return kDefaultPassCap; }
+
+void fill_stats(cfpq_run_stats *s, const QCtl &c, const QueryDev &q, double ms) {
+    memset(s, 0, sizeof(*s));
+    s->iterations = c.iters_done;
+    s->rounds = (uint32_t)c.rounds_total;
+    s->status = c.status == kStatusOk ? 0 : (uint32_t)(-CFPQ_ERR_TIMEOUT);
+    s->edges_added = c.edges_total;
+    s->row_ors = c.row_ors;
+    s->tile_mmas = c.tile_mmas;
+    s->closure_blocks = q.blocks.size();
+    s->device_bytes = q.device_bytes;
+    s->ms_total = ms;
+}
+
+int status_of(const QCtl &c) { return c.status == kStatusOk ? CFPQ_OK : CFPQ_ERR_TIMEOUT; }
+
+// Run the executor's queries to their fixpoint.
+int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t *launches) {
+    const cudaStream_t st = ctx->stream;
+    const uint32_t mi = ctx->opt.max_iterations, mr = ctx->opt.max_rounds, mp = pass_cap(ctx->opt);
+    uint32_t n_gather = 0, n_extract = 0;
+    for (int v = 0; v < 5; ++v) {
+        n_gather += ex.n_items[v] ? 1 : 0;
+        n_extract += ex.n_xitems[v] ? 1 : 0;
+    }
+    const uint32_t per_pass = n_gather + n_extract + 1;
+    if (ctx->opt.loop_mode == CFPQ_LOOP_HOST) {
+        if (ex.enqueue_prologue(st, mi, mr, mp)) return fail(ctx, CFPQ_ERR_CUDA, "prologue launch failed");
+        int running = 1;
+        uint32_t passes = 0;
+        while (running) {
+            if (ex.enqueue_pass(st, 0, 0, ex.running.as<int>()))
+                return fail(ctx, CFPQ_ERR_CUDA, "pass launch failed");
+            CK(ctx, cudaMemcpyAsync(&running, ex.running.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(ctx, cudaStreamSynchronize(st));
+            ++passes;
+        }
+        if (launches) *launches = passes * per_pass + 2;
+    } else {
+        if (!ex.exec) {
+            std::string e;
+            if (ex.build_graph(st, mi, mr, mp, &e)) return fail(ctx, CFPQ_ERR_CUDA, e);
+        }
+        CK(ctx, cudaGraphLaunch(ex.exec, st));
+    }
+    std::string e;
+    if (ex.read_ctls(st, ctls)) return fail(ctx, CFPQ_ERR_CUDA, "reading loop state failed");
+    if (ctx->opt.loop_mode != CFPQ_LOOP_HOST && launches) {
+        uint32_t passes = 0;
+        for (const auto &c : *ctls) passes = std::max(passes, c.passes);
+        *launches = passes * per_pass + 2;
+    }
+    CK(ctx, cudaGetLastError());
+    return CFPQ_OK;
+}
+
+int ensure_query(cfpq_ctx *ctx) {
+    if (!ctx->has_graph) return fail(ctx, CFPQ_ERR_STATE, "no graph loaded");
+    if (!ctx->has_rsm) return fail(ctx, CFPQ_ERR_STATE, "no RSM loaded");
+    QueryDev &q = ctx->query;
+    q.g = &ctx->graph;
+    if (!q.prepared || q.graph_generation != ctx->graph.generation || ctx->exec_dirty) {
+        std::string e;
+        int rc = q.prepare(&ctx->A, &e);
+        if (rc) return fail(ctx, rc, e);
+        ctx->exec.qs.assign(1, &q);
+        rc = ctx->exec.assemble(&ctx->A, ctx->stream, &e);
+        if (rc) return fail(ctx, rc, e);
+        ctx->exec_dirty = false;
+    }
+    return CFPQ_OK;
+}
+
+int bits_to_host(cfpq_ctx *ctx, const uint64_t *dev_rows, uint32_t n, uint32_t W, uint64_t *bits) {
+    const size_t wn = (n + 63) / 64;
+    CK(ctx, cudaMemcpy2DAsync(bits, wn * 8, dev_rows, (size_t)W * 8, wn * 8, n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return CFPQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cfpq_status_string(int status) {
+    switch (status) {
+        case CFPQ_OK: return "ok";
+        case CFPQ_ERR_INVALID_ARG: return "invalid argument";
+        case CFPQ_ERR_OUT_OF_MEMORY: return "out of memory";
+        case CFPQ_ERR_BUFFER_TOO_SMALL: return "buffer too small";
+        case CFPQ_ERR_TIMEOUT: return "iteration or round cap reached";
+        case CFPQ_ERR_NOT_READY: return "result not ready";
+        case CFPQ_ERR_CUDA: return "CUDA error";
+        case CFPQ_ERR_STATE: return "calls out of order";
+        case CFPQ_ERR_UNSUPPORTED: return "unsupported size or mode";
+        default: return "unknown status";
+    }
+}
+
+const char *cfpq_last_error(const cfpq_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int cfpq_default_options(cfpq_options *opt) {
+    if (!opt) return CFPQ_ERR_INVALID_ARG;
+    memset(opt, 0, sizeof(*opt));
+    opt->struct_size = sizeof(cfpq_options);
+    opt->device = 0;
+    opt->closure_mode = CFPQ_CLOSURE_AUTO;
+    opt->loop_mode = CFPQ_LOOP_DEVICE;
+    return CFPQ_OK;
+}
+
+int cfpq_create(cfpq_ctx **out, const cfpq_options *opt, void *stream) {
+    if (!out) return CFPQ_ERR_INVALID_ARG;
+    *out = nullptr;
+    API_TRY
+    std::unique_ptr<cfpq_ctx> c(new cfpq_ctx());
+    if (opt) {
+        if (opt->struct_size != sizeof(cfpq_options)) return CFPQ_ERR_INVALID_ARG;
+        c->opt = *opt;
+    } else {
+        cfpq_default_options(&c->opt);
+    }
+    if (c->opt.loop_mode > CFPQ_LOOP_HOST || c->opt.closure_mode > CFPQ_CLOSURE_TC_I8) return CFPQ_ERR_INVALID_ARG;
+    if ((c->opt.alloc == nullptr) != (c->opt.free == nullptr)) return CFPQ_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || c->opt.device < 0 || c->opt.device >= ndev) {
+        cudaGetLastError();
+        return CFPQ_ERR_CUDA;
+    }
+    if (cudaSetDevice(c->opt.device) != cudaSuccess) return CFPQ_ERR_CUDA;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->A.alloc = c->opt.alloc;
+    c->A.free = c->opt.free;
+    c->A.user = c->opt.alloc_user;
+    c->A.stream = c->stream;
+    c->A.budget = c->opt.memory_budget;
+    *out = c.release();
+    return CFPQ_OK;
+    API_CATCH(nullptr)
+}
+
+int cfpq_destroy(cfpq_ctx *ctx) {
+    if (!ctx) return CFPQ_OK;
+    API_TRY
+    cudaSetDevice(ctx->opt.device);
+    cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+    return CFPQ_OK;
+    API_CATCH(nullptr)
+}
+
+static int load_graph_impl(cfpq_ctx *ctx, uint32_t n, uint32_t nt, size_t m, const uint32_t *s, const uint32_t *l,
+                           const uint32_t *d, bool dev) {
+    if (!ctx) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (int rc = set_device(ctx)) return rc;
+    ctx->has_result = false;
+    std::string e;
+    int rc = stage_graph(&ctx->graph, &ctx->A, ctx->stream, n, nt, m, s, l, d, dev, &e);
+    if (rc) {
+        ctx->has_graph = false;
+        return fail(ctx, rc, e);
+    }
+    ctx->has_graph = true;
+    if (ctx->has_rsm && ctx->query.rsm.max_terminal_plus1 > nt)
+        return fail(ctx, CFPQ_ERR_INVALID_ARG, "the loaded RSM reads a terminal >= n_terminals");
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+int cfpq_load_graph(cfpq_ctx *ctx, uint32_t n_vertices, uint32_t n_terminals, size_t n_edges, const uint32_t *src,
+                    const uint32_t *label, const uint32_t *dst) {
+    return load_graph_impl(ctx, n_vertices, n_terminals, n_edges, src, label, dst, false);
+}
+
+int cfpq_load_graph_device(cfpq_ctx *ctx, uint32_t n_vertices, uint32_t n_terminals, size_t n_edges,
+                           const uint32_t *d_src, const uint32_t *d_label, const uint32_t *d_dst) {
+    return load_graph_impl(ctx, n_vertices, n_terminals, n_edges, d_src, d_label, d_dst, true);
+}
+
+int cfpq_load_rsm(cfpq_ctx *ctx, const cfpq_rsm *rsm) {
+    if (!ctx) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    HostRSM h;
+    std::string e;
+    int rc = copy_rsm(rsm, &h, &e);
+    if (rc) return fail(ctx, rc, e);
+    if (ctx->has_graph && h.max_terminal_plus1 > ctx->graph.n_term)
+        return fail(ctx, CFPQ_ERR_INVALID_ARG, "the RSM reads a terminal >= the graph's n_terminals");
+    ctx->query.rsm = std::move(h);
+    ctx->has_rsm = true;
+    ctx->has_result = false;
+    ctx->exec_dirty = true;
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats) {
+    if (!ctx) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    const auto t0 = std::chrono::steady_clock::now();
+    if (int rc = set_device(ctx)) return rc;
+    if (int rc = ensure_query(ctx)) return rc;
+    std::vector<QCtl> ctls;
+    uint32_t launches = 0;
+    if (int rc = run_executor(ctx, ctx->exec, &ctls, &launches)) return rc;
+    ctx->has_result = true;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) {
+        fill_stats(stats, ctls[0], ctx->query, ms);
+        stats->gpu_launches = launches;
+    }
+    const int st = status_of(ctls[0]);
+    if (st) return fail(ctx, st, "iteration, round or pass cap reached before the fixpoint");
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+int cfpq_count_index(cfpq_ctx *ctx, uint64_t *closure_bits, uint64_t *m3_bits) {
+    if (!ctx) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (!ctx->has_result) return fail(ctx, CFPQ_ERR_NOT_READY, "no result");
+    if (int rc = set_device(ctx)) return rc;
+    QueryDev &q = ctx->query;
+    std::string e;
+    if (!ctx->counter.ensure(&ctx->A, 64, &e)) return fail(ctx, CFPQ_ERR_OUT_OF_MEMORY, e);
+    unsigned long long *cnt = ctx->counter.as<unsigned long long>();
+    CK(ctx, cudaMemsetAsync(cnt, 0, 64, ctx->stream));
+    CK(ctx, launch_popcount(q.blk_mem.as<uint64_t>(), q.blocks.size() * (size_t)q.n * q.W, cnt, ctx->stream));
+    for (uint32_t b = 0; b < q.B; ++b)
+        CK(ctx, launch_popcount(q.m2_ptr(b), (size_t)q.n * q.W, cnt + 1 + (b < 6 ? b : 6), ctx->stream));
+    unsigned long long h[8];
+    CK(ctx, cudaMemcpyAsync(h, cnt, 64, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (closure_bits) *closure_bits = h[0];
+    if (m3_bits) {
+        // nnz(M3) = sum over transitions s -l-> u of nnz(M2^l) (exact when no
+        // two transitions join the same pair of states).
+        std::vector<uint32_t> off((size_t)ctx->graph.n_term * q.n + 1);
+        CK(ctx, cudaMemcpy(off.data(), ctx->graph.csr_off.p, off.size() * 4, cudaMemcpyDeviceToHost));
+        std::vector<uint64_t> nnz_nt(q.B, 0);
+        if (q.B > 6) {
+            for (uint32_t b = 0; b < q.B; ++b) {
+                CK(ctx, cudaMemsetAsync(cnt, 0, 8, ctx->stream));
+                CK(ctx, launch_popcount(q.m2_ptr(b), (size_t)q.n * q.W, cnt, ctx->stream));
+                unsigned long long v = 0;
+                CK(ctx, cudaMemcpyAsync(&v, cnt, 8, cudaMemcpyDeviceToHost, ctx->stream));
+                CK(ctx, cudaStreamSynchronize(ctx->stream));
+                nnz_nt[b] = v;
+            }
+        } else {
+            for (uint32_t b = 0; b < q.B; ++b) nnz_nt[b] = h[1 + b];
+        }
+        uint64_t s = 0;
+        for (const auto &t : q.rsm.tr) {
+            if (t.kind == 0) s += off[(size_t)(t.sym + 1) * q.n] - off[(size_t)t.sym * q.n];
+            else s += nnz_nt[t.sym];
+        }
+        *m3_bits = s;
+    }
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+int cfpq_get_reachable_bits(cfpq_ctx *ctx, uint32_t box, uint64_t *bits) {
+    if (!ctx || !bits) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (!ctx->has_result) return fail(ctx, CFPQ_ERR_NOT_READY, "no result");
+    if (box >= ctx->query.B) return fail(ctx, CFPQ_ERR_INVALID_ARG, "box out of range");
+    if (int rc = set_device(ctx)) return rc;
+    return bits_to_host(ctx, ctx->query.m2_ptr(box), ctx->query.n, ctx->query.W, bits);
+    API_CATCH(ctx)
+}
+
+int cfpq_count_reachable(cfpq_ctx *ctx, uint32_t box, uint64_t *count) {
+    if (!ctx || !count) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (!ctx->has_result) return fail(ctx, CFPQ_ERR_NOT_READY, "no result");
+    if (box >= ctx->query.B) return fail(ctx, CFPQ_ERR_INVALID_ARG, "box out of range");
+    if (int rc = set_device(ctx)) return rc;
+    std::string e;
+    if (!ctx->counter.ensure(&ctx->A, 64, &e)) return fail(ctx, CFPQ_ERR_OUT_OF_MEMORY, e);
+    unsigned long long *cnt = ctx->counter.as<unsigned long long>();
+    CK(ctx, cudaMemsetAsync(cnt, 0, 8, ctx->stream));
+    CK(ctx, launch_popcount(ctx->query.m2_ptr(box), (size_t)ctx->query.n * ctx->query.W, cnt, ctx->stream));
+    unsigned long long v = 0;
+    CK(ctx, cudaMemcpyAsync(&v, cnt, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    *count = v;
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+int cfpq_get_reachable(cfpq_ctx *ctx, uint32_t box, uint32_t *src, uint32_t *dst, size_t cap, size_t *count) {
+    if (!ctx || !count) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (!ctx->has_result) return fail(ctx, CFPQ_ERR_NOT_READY, "no result");
+    if (box >= ctx->query.B) return fail(ctx, CFPQ_ERR_INVALID_ARG, "box out of range");
+    const uint32_t n = ctx->query.n;
+    const size_t wn = (n + 63) / 64;
+    std::vector<uint64_t> bits((size_t)n * wn);
+    if (int rc = cfpq_get_reachable_bits(ctx, box, bits.data())) return rc;
+    size_t total = 0;
+    for (uint64_t w : bits) total += (size_t)__builtin_popcountll(w);
+    *count = total;
+    if (!src && !dst && cap == 0) return CFPQ_OK;
+    if (!src || !dst || cap < total) return fail(ctx, CFPQ_ERR_BUFFER_TOO_SMALL, "pair buffers too small");
+    size_t k = 0;
+    for (uint32_t x = 0; x < n; ++x)
+        for (size_t w = 0; w < wn; ++w) {
+            uint64_t b = bits[(size_t)x * wn + w];
+            while (b) {
+                const uint32_t y = (uint32_t)(w * 64 + (uint64_t)__builtin_ctzll(b));
+                b &= b - 1;
+                src[k] = x;
+                dst[k] = y;
+                ++k;
+            }
+        }
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+int cfpq_get_closure_rows(cfpq_ctx *ctx, uint32_t n_rows, const uint32_t *row_state, const uint32_t *row_vertex,
+                          uint64_t *out) {
+    if (!ctx || (n_rows && (!row_state || !row_vertex || !out))) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (!ctx->has_result) return fail(ctx, CFPQ_ERR_NOT_READY, "no result");
+    if (int rc = set_device(ctx)) return rc;
+    QueryDev &q = ctx->query;
+    const uint32_t n = q.n, Q = q.Q, W = q.W;
+    const size_t wN = ((size_t)Q * n + 63) / 64;
+    for (uint32_t k = 0; k < n_rows; ++k)
+        if (row_state[k] >= Q || row_vertex[k] >= n) return fail(ctx, CFPQ_ERR_INVALID_ARG, "row out of range");
+    const uint32_t chunk = 4096;
+    std::vector<const uint64_t *> ptrs;
+    std::vector<uint32_t> rows;
+    std::vector<uint64_t> host;
+    std::string e;
+    for (uint32_t k0 = 0; k0 < n_rows; k0 += chunk / Q + 1) {
+        const uint32_t k1 = std::min(n_rows, k0 + chunk / Q + 1);
+        ptrs.clear();
+        rows.clear();
+        for (uint32_t k = k0; k < k1; ++k)
+            for (uint32_t t = 0; t < Q; ++t) {
+                const int32_t b = q.blk_of[(size_t)row_state[k] * Q + t];
+                ptrs.push_back(b >= 0 ? q.blk_ptr((uint32_t)b) : nullptr);
+                rows.push_back(row_vertex[k]);
+            }
+        const uint32_t nj = (uint32_t)ptrs.size();
+        if (!ctx->rows_ptrs.ensure(&ctx->A, nj * sizeof(void *), &e) || !ctx->rows_idx.ensure(&ctx->A, nj * 4, &e) ||
+            !ctx->rows_out.ensure(&ctx->A, (size_t)nj * W * 8, &e))
+            return fail(ctx, CFPQ_ERR_OUT_OF_MEMORY, e);
+        CK(ctx, cudaMemcpyAsync(ctx->rows_ptrs.p, ptrs.data(), nj * sizeof(void *), cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, cudaMemcpyAsync(ctx->rows_idx.p, rows.data(), nj * 4, cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, launch_copy_rows(ctx->rows_ptrs.as<const uint64_t *>(), ctx->rows_idx.as<uint32_t>(), nj, W,
+                                 ctx->rows_out.as<uint64_t>(), ctx->stream));
+        host.resize((size_t)nj * W);
+        CK(ctx, cudaMemcpyAsync(host.data(), ctx->rows_out.p, host.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        // Remap block-local columns (t, y) to the paper's index t * n + y.
+        for (uint32_t k = k0; k < k1; ++k) {
+            uint64_t *o = out + (size_t)k * wN;
+            memset(o, 0, wN * 8);
+            for (uint32_t t = 0; t < Q; ++t) {
+                const uint64_t *src = host.data() + ((size_t)(k - k0) * Q + t) * W;
+                for (uint32_t w = 0; w < W; ++w) {
+                    uint64_t b = src[w];
+                    while (b) {
+                        const uint64_t y = w * 64 + (uint64_t)__builtin_ctzll(b);
+                        b &= b - 1;
+                        const uint64_t col = (uint64_t)t * n + y;
+                        o[col >> 6] |= 1ull << (col & 63);
+                    }
+                }
+            }
+        }
+    }
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Path extraction (Sec. 3.2, Listing 2), on the host.
+// ---------------------------------------------------------------------------
+// getPaths(vs, vf, N) follows product paths of M3 from (q0_N, vs) to (f, vf),
+// f final in N's box; a product edge over a terminal is a graph edge, one over
+// a nonterminal N' with M2^{N'}[v, v'] = 1 expands into getPaths(v, v', N').
+// The sets are bounded by the number of graph edges (max_len) and computed as
+// the least fixpoint of these equations over keys (N, x, y, length), so that
+// recursion through nonterminals deriving the empty word terminates.
+namespace {
+
+struct PathCtx {
+    const HostRSM *r;
+    uint32_t n;
+    std::vector<uint32_t> es, el, ed;        // unique edges sorted by (src, label, dst)
+    std::vector<uint32_t> eoff;              // per source vertex
+    std::vector<std::vector<uint64_t>> m2;   // per box, n * wn words
+    size_t wn;
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, std::set<std::vector<uint32_t>>> memo;
+    size_t stored = 0, cap = 4000000;
+    bool over = false;
+
+    const std::set<std::vector<uint32_t>> &get(uint32_t N, uint32_t x, uint32_t y, uint32_t len) {
+        auto key = std::make_tuple(N, x, y, len);
+        auto it = memo.find(key);
+        if (it == memo.end()) it = memo.emplace(key, std::set<std::vector<uint32_t>>()).first;
+        return it->second;
+    }
+
+    // One evaluation of Paths(N, x, y, len) from the current memo values.
+    std::set<std::vector<uint32_t>> eval(uint32_t N, uint32_t x, uint32_t y, uint32_t len) {
+        using PSet = std::set<std::vector<uint32_t>>;
+        // layer[k]: map (state, vertex) -> paths of k edges from (q0, x)
+        std::vector<std::map<std::pair<uint32_t, uint32_t>, PSet>> layer(len + 1);
+        const uint32_t q0 = r->box_start[N];
+        layer[0][{q0, x}].insert(std::vector<uint32_t>());
+        for (uint32_t k = 0; k <= len; ++k) {
+            bool grew = true;
+            while (grew && !over) {
+                grew = false;
+                auto snapshot = layer[k];
+                for (auto &kv : snapshot) {
+                    const uint32_t s = kv.first.first, v = kv.first.second;
+                    const PSet &S = kv.second;
+                    for (const auto &t : r->tr) {
+                        if (t.from != s) continue;
+                        if (t.kind == 0) {
+                            if (k + 1 > len) continue;
+                            for (uint32_t e = eoff[v]; e < eoff[v + 1]; ++e) {
+                                if (el[e] != t.sym) continue;
+                                PSet &D = layer[k + 1][{t.to, ed[e]}];
+                                for (const auto &p : S) {
+                                    auto q = p;
+                                    q.push_back(e);
+                                    D.insert(std::move(q));
+                                }
+                            }
+                        } else {
+                            const uint64_t *row = m2[t.sym].data() + (size_t)v * wn;
+                            for (size_t w = 0; w < wn; ++w) {
+                                uint64_t b = row[w];
+                                while (b) {
+                                    const uint32_t v2 = (uint32_t)(w * 64 + (uint64_t)__builtin_ctzll(b));
+                                    b &= b - 1;
+                                    for (uint32_t j = 0; k + j <= len; ++j) {
+                                        const PSet &sub = get(t.sym, v, v2, j);
+                                        if (sub.empty()) continue;
+                                        PSet &D = layer[k + j][{t.to, v2}];
+                                        const size_t before = D.size();
+                                        for (const auto &p : S)
+                                            for (const auto &s2 : sub) {
+                                                auto q = p;
+                                                q.insert(q.end(), s2.begin(), s2.end());
+                                                D.insert(std::move(q));
+                                            }
+                                        if (j == 0 && D.size() != before) grew = true;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        PSet out;
+        for (uint32_t f = 0; f < r->Q; ++f) {
+            if (r->state_box[f] != N || !r->final_[f]) continue;
+            auto it = layer[len].find({f, y});
+            if (it != layer[len].end()) out.insert(it->second.begin(), it->second.end());
+        }
+        return out;
+    }
+
+    // Chaotic iteration to the least fixpoint over every key in the memo.
+    void solve() {
+        bool changed = true;
+        while (changed && !over) {
+            changed = false;
+            std::vector<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>> keys;
+            for (auto &kv : memo) keys.push_back(kv.first);
+            for (auto &k : keys) {
+                auto v = eval(std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k));
+                auto &cur = memo[k];
+                if (v.size() != cur.size()) {
+                    stored += v.size() - cur.size();
+                    cur = std::move(v);
+                    changed = true;
+                    if (stored > cap) over = true;
+                }
+            }
+            if (memo.size() != keys.size()) changed = true;
+        }
+    }
+};
+
+}  // namespace
+
+extern "C" int cfpq_extract_paths(cfpq_ctx *ctx, uint32_t box, uint32_t vs, uint32_t vf, uint32_t max_len,
+                                  size_t max_paths, uint32_t *edge_buf, size_t edge_cap, size_t *path_offsets,
+                                  size_t *n_paths, int *truncated) {
+    if (!ctx || !n_paths || !path_offsets) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (!ctx->has_result) return fail(ctx, CFPQ_ERR_NOT_READY, "no result");
+    QueryDev &q = ctx->query;
+    if (box >= q.B || vs >= q.n || vf >= q.n) return fail(ctx, CFPQ_ERR_INVALID_ARG, "box or vertex out of range");
+    if (int rc = set_device(ctx)) return rc;
+    PathCtx P;
+    P.r = &q.rsm;
+    P.n = q.n;
+    P.wn = (q.n + 63) / 64;
+    // host copies: unique terminal edges and M2 of every box
+    const GraphDev &g = ctx->graph;
+    std::vector<uint32_t> off((size_t)g.n_term * g.n + 1), col(std::max<size_t>(g.m_unique, 1));
+    CK(ctx, cudaMemcpy(off.data(), g.csr_off.p, off.size() * 4, cudaMemcpyDeviceToHost));
+    if (g.m_unique) CK(ctx, cudaMemcpy(col.data(), g.csr_col.p, g.m_unique * 4, cudaMemcpyDeviceToHost));
+    std::vector<std::tuple<uint32_t, uint32_t, uint32_t>> tri;
+    for (uint32_t l = 0; l < g.n_term; ++l)
+        for (uint32_t x = 0; x < g.n; ++x)
+            for (uint32_t e = off[(size_t)l * g.n + x]; e < off[(size_t)l * g.n + x + 1]; ++e)
+                tri.emplace_back(x, l, col[e]);
+    std::sort(tri.begin(), tri.end());
+    tri.erase(std::unique(tri.begin(), tri.end()), tri.end());
+    P.eoff.assign(g.n + 1, 0);
+    for (auto &t : tri) {
+        P.es.push_back(std::get<0>(t));
+        P.el.push_back(std::get<1>(t));
+        P.ed.push_back(std::get<2>(t));
+        P.eoff[std::get<0>(t) + 1]++;
+    }
+    for (uint32_t v = 0; v < g.n; ++v) P.eoff[v + 1] += P.eoff[v];
+    P.m2.resize(q.B);
+    for (uint32_t b = 0; b < q.B; ++b) {
+        P.m2[b].resize((size_t)q.n * P.wn);
+        if (int rc = bits_to_host(ctx, q.m2_ptr(b), q.n, q.W, P.m2[b].data())) return rc;
+    }
+    // Paths in order of length, then lexicographic (edge ids follow the triple order).
+    std::vector<std::vector<uint32_t>> result;
+    bool trunc = false;
+    const uint64_t *root = P.m2[box].data() + (size_t)vs * P.wn;
+    const bool reachable = (root[vf >> 6] >> (vf & 63)) & 1;
+    if (reachable) {
+        for (uint32_t len = 0; len <= max_len && !trunc; ++len) {
+            P.get(box, vs, vf, len);
+            P.solve();
+            if (P.over) return fail(ctx, CFPQ_ERR_UNSUPPORTED, "path enumeration exceeded its work cap");
+            const auto &S = P.memo[std::make_tuple(box, vs, vf, len)];
+            for (const auto &p : S) {
+                if (result.size() == max_paths) { trunc = true; break; }
+                result.push_back(p);
+            }
+        }
+    }
+    size_t need = 0;
+    for (auto &p : result) need += p.size();
+    *n_paths = result.size();
+    if (truncated) *truncated = trunc ? 1 : 0;
+    if (need > edge_cap || (need && !edge_buf)) return fail(ctx, CFPQ_ERR_BUFFER_TOO_SMALL, "edge buffer too small");
+    size_t k = 0;
+    path_offsets[0] = 0;
+    for (size_t i = 0; i < result.size(); ++i) {
+        for (uint32_t e : result[i]) {
+            edge_buf[3 * k] = P.es[e];
+            edge_buf[3 * k + 1] = P.el[e];
+            edge_buf[3 * k + 2] = P.ed[e];
+            ++k;
+        }
+        path_offsets[i + 1] = k;
+    }
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+// ---------------------------------------------------------------------------
+// Batched index creation.
+// ---------------------------------------------------------------------------
+extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_query *queries,
+                              cfpq_run_stats *per_query_stats, cfpq_run_stats *total_stats) {
+    if (!ctx || (n_queries && !queries)) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    const auto t0 = std::chrono::steady_clock::now();
+    if (int rc = set_device(ctx)) return rc;
+    ctx->has_batch = false;
+    ctx->bexec.qs.clear();
+    ctx->bexec.drop_graph();
+    ctx->bqueries.clear();
+    ctx->bgraphs.clear();
+    std::string e;
+    for (uint32_t i = 0; i < n_queries; ++i) {
+        const cfpq_query &qq = queries[i];
+        std::unique_ptr<GraphDev> g(new GraphDev());
+        int rc = stage_graph(g.get(), &ctx->A, ctx->stream, qq.n_vertices, qq.n_terminals, qq.n_edges, qq.src,
+                             qq.label, qq.dst, false, &e);
+        if (rc) return fail(ctx, rc, "query " + std::to_string(i) + ": " + e);
+        std::unique_ptr<QueryDev> q(new QueryDev());
+        rc = copy_rsm(qq.rsm, &q->rsm, &e);
+        if (rc) return fail(ctx, rc, "query " + std::to_string(i) + ": " + e);
+        q->g = g.get();
+        rc = q->prepare(&ctx->A, &e);
+        if (rc) return fail(ctx, rc, "query " + std::to_string(i) + ": " + e);
+        ctx->bgraphs.push_back(std::move(g));
+        ctx->bqueries.push_back(std::move(q));
+    }
+    for (auto &q : ctx->bqueries) ctx->bexec.qs.push_back(q.get());
+    int rc = ctx->bexec.assemble(&ctx->A, ctx->stream, &e);
+    if (rc) return fail(ctx, rc, e);
+    std::vector<QCtl> ctls;
+    uint32_t launches = 0;
+    if ((rc = run_executor(ctx, ctx->bexec, &ctls, &launches))) return rc;
+    ctx->has_batch = true;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    int worst = CFPQ_OK;
+    cfpq_run_stats tot;
+    memset(&tot, 0, sizeof(tot));
+    for (uint32_t i = 0; i < n_queries; ++i) {
+        cfpq_run_stats s;
+        fill_stats(&s, ctls[i], *ctx->bqueries[i], ms);
+        if (per_query_stats) per_query_stats[i] = s;
+        tot.iterations = std::max(tot.iterations, s.iterations);
+        tot.rounds = std::max(tot.rounds, s.rounds);
+        tot.edges_added += s.edges_added;
+        tot.row_ors += s.row_ors;
+        tot.tile_mmas += s.tile_mmas;
+        tot.closure_blocks += s.closure_blocks;
+        tot.device_bytes += s.device_bytes;
+        if (status_of(ctls[i])) worst = status_of(ctls[i]);
+    }
+    tot.ms_total = ms;
+    tot.gpu_launches = launches;
+    tot.status = worst ? (uint32_t)(-worst) : 0;
+    if (total_stats) *total_stats = tot;
+    if (worst) return fail(ctx, worst, "a query reached an iteration, round or pass cap");
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+extern "C" int cfpq_batch_get_reachable_bits(cfpq_ctx *ctx, uint32_t qi, uint32_t box, uint64_t *bits) {
+    if (!ctx || !bits) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (!ctx->has_batch) return fail(ctx, CFPQ_ERR_NOT_READY, "no batch result");
+    if (qi >= ctx->bqueries.size()) return fail(ctx, CFPQ_ERR_INVALID_ARG, "query index out of range");
+    QueryDev &q = *ctx->bqueries[qi];
+    if (box >= q.B) return fail(ctx, CFPQ_ERR_INVALID_ARG, "box out of range");
+    if (int rc = set_device(ctx)) return rc;
+    return bits_to_host(ctx, q.m2_ptr(box), q.n, q.W, bits);
+    API_CATCH(ctx)
+}

@@ -1,0 +1,101 @@
+// cfpq_dev.cuh -- device data structures of libcfpq (shared by host and kernels).
+//
+// Layout of one query on the device (Sec. 3.1, Listing 1; Kronecker index
+// state * n + vertex of Sec. 2.4):
+//   - the closure C3 is held as n x n state blocks C[s,t], one per pair of RSM
+//     states with t reachable from s by one or more RSM transitions (all other
+//     blocks of C3 are zero because M3's block (s,t) is OR_{l: s-l->t} M2^l);
+//     a block is n rows of W = n_pad/64 uint64 words, bit y of row x is
+//     word y/64, bit y%64; n_pad is n rounded up to 128 so that rows are
+//     16-byte aligned for 128-bit loads;
+//   - every block has a uint32 stamp per row (the closure pass that last
+//     changed the row) and one "last changed pass" word: the dirty flags;
+//   - terminal labels are CSR adjacency lists (static, deduplicated);
+//   - nonterminal labels are bit rows M2^b (all edges) and A2^b (edges new in
+//     this iteration, valid where the row's stamp equals the iteration).
+#pragma once
+#include <stdint.h>
+
+namespace cfpq {
+
+constexpr uint32_t kModeNew = 0;   // pass over the new edges of the iteration
+constexpr uint32_t kModeProp = 1;  // pass over dirty rows (all edges)
+constexpr uint32_t kPhaseRun = 0;
+constexpr uint32_t kPhaseDone = 1;
+constexpr uint32_t kStatusOk = 0;
+constexpr uint32_t kStatusIterCap = 1;
+constexpr uint32_t kStatusRoundCap = 2;
+constexpr uint32_t kStatusPassCap = 3;
+
+// Per-query loop state, in device memory.  Written only by the control
+// kernel (and the counters by atomics), read by every kernel of a pass.
+struct QCtl {
+    uint32_t g;               // id of the closure pass in progress (starts at 2)
+    uint32_t iter;            // fixpoint iteration, 1-based
+    uint32_t mode;            // kModeNew / kModeProp
+    uint32_t phase;           // kPhaseRun / kPhaseDone
+    uint32_t g_iter_start;    // pass id of the iteration's first pass
+    uint32_t rounds_in_iter;  // passes done in this iteration
+    uint32_t status;          // kStatus*
+    uint32_t max_iter;        // 0 = no cap
+    uint32_t max_rounds;      // 0 = no cap
+    uint32_t max_passes;      // hard cap on passes (safety)
+    uint32_t iters_done;      // completed iterations
+    uint32_t passes;          // passes done
+    unsigned long long changed_rows;  // rows changed by the pass in progress
+    unsigned long long new_edges;     // edges added by the extraction in progress
+    unsigned long long edges_total;   // edges added so far (epsilon edges included)
+    unsigned long long row_ors;       // source rows ORed (all passes)
+    unsigned long long tile_mmas;     // dense tiles multiplied (all passes)
+    unsigned long long rounds_total;
+};
+
+// One source of an output block C[s,t]: a transition s -l-> u with t = u or
+// t reachable from u.  Product edges (s,x) -> (u,y) for every edge (x,y) of
+// the graph matrix M2^l (the Kronecker product M1^l (x) M2^l, row by row).
+struct SrcDesc {
+    const uint32_t *csr_off;   // terminal l: CSR offsets [n+1]; else null
+    const uint32_t *csr_col;   // terminal l: CSR columns
+    const uint64_t *nt_all;    // nonterminal l = box b: M2^b rows
+    const uint64_t *nt_new;    // nonterminal: A2^b rows
+    const uint32_t *nt_new_it; // nonterminal: A2 row valid iff == iteration
+    const uint32_t *box_new_it;// nonterminal: box has new edges iff == iteration
+    const uint64_t *rblk;      // C[u,t] rows or null (u == t without a cycle)
+    const uint32_t *rstamp;    // row stamps of C[u,t]
+    const uint32_t *rlast;     // last pass that changed C[u,t]
+    uint32_t ident;            // u == t: the product edge itself lands in C[s,t]
+    uint32_t dense;            // label matrix handled by dense tiles (not here)
+};
+
+// Gather work item: rows [row0, row1) of one output block.
+struct GItem {
+    uint64_t *out;
+    uint32_t *out_stamp;
+    uint32_t *out_last;
+    QCtl *ctl;
+    uint32_t src0, nsrc;
+    uint32_t row0, row1;
+    uint32_t W;    // words per row
+    uint32_t lpr;  // lanes per row (power of two <= 32)
+};
+
+// Final-state block used by extraction: C[q0(b), f] with f final in box b.
+struct FDesc {
+    const uint64_t *blk;
+    const uint32_t *stamp;
+};
+
+// Extraction work item: rows [row0, row1) of box b's M2^b.
+struct XItem {
+    uint64_t *m2;
+    uint64_t *a2;
+    uint32_t *a2_it;
+    uint32_t *box_new_it;
+    QCtl *ctl;
+    uint32_t f0, nf;
+    uint32_t row0, row1;
+    uint32_t W;
+    uint32_t lpr;
+};
+
+}  // namespace cfpq

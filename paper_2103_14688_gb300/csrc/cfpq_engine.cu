@@ -1,0 +1,466 @@
+// cfpq_engine.cu -- host side of the index-creation engine: input staging,
+// per-query planning of the closure blocks, and the executor that drives the
+// fixpoint loop of Listing 1 (arXiv 2103.14688, Sec. 3.1) for one or many
+// queries, as a CUDA graph with a device-side while loop or as host-driven
+// passes.
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "cfpq_engine.cuh"
+
+namespace cfpq {
+
+#define ENG_CK(call)                                                                          \
+    do {                                                                                      \
+        cudaError_t _e = (call);                                                              \
+        if (_e != cudaSuccess) {                                                              \
+            if (err) *err = std::string(#call) + ": " + cudaGetErrorString(_e);               \
+            return CFPQ_ERR_CUDA;                                                             \
+        }                                                                                     \
+    } while (0)
+
+void *Allocator::get(size_t bytes, std::string *err) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (budget && in_use + bytes > budget) {
+        if (err) *err = "device memory budget exceeded (" + std::to_string(in_use + bytes) + " > " +
+                        std::to_string(budget) + " bytes)";
+        return nullptr;
+    }
+    void *p = nullptr;
+    if (alloc) {
+        p = alloc(bytes, stream, user);
+    } else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (!p) {
+        if (err) *err = "device allocation of " + std::to_string(bytes) + " bytes failed";
+        return nullptr;
+    }
+    in_use += bytes;
+    return p;
+}
+
+void Allocator::put(void *p, size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (free) free(p, bytes, stream, user);
+    else cudaFreeAsync(p, stream);
+    in_use -= std::min(in_use, bytes);
+}
+
+// ---------------------------------------------------------------------------
+// RSM validation (Sec. 2.3, Def. of an RSM).
+// ---------------------------------------------------------------------------
+int copy_rsm(const cfpq_rsm *r, HostRSM *out, std::string *err) {
+    if (!r) { *err = "rsm is NULL"; return CFPQ_ERR_INVALID_ARG; }
+    if (r->n_states == 0 || r->n_boxes == 0 || r->start_box >= r->n_boxes) {
+        *err = "rsm needs at least one state and one box, and start_box < n_boxes";
+        return CFPQ_ERR_INVALID_ARG;
+    }
+    if (!r->box_start || !r->state_box || !r->state_final || (r->n_trans && (!r->tr_from || !r->tr_kind ||
+                                                                              !r->tr_sym || !r->tr_to))) {
+        *err = "rsm has a NULL array";
+        return CFPQ_ERR_INVALID_ARG;
+    }
+    HostRSM h;
+    h.Q = r->n_states;
+    h.B = r->n_boxes;
+    h.start_box = r->start_box;
+    h.box_start.assign(r->box_start, r->box_start + h.B);
+    h.state_box.assign(r->state_box, r->state_box + h.Q);
+    h.final_.assign(r->state_final, r->state_final + h.Q);
+    for (uint32_t s = 0; s < h.Q; ++s)
+        if (h.state_box[s] >= h.B) { *err = "state_box out of range"; return CFPQ_ERR_INVALID_ARG; }
+    for (uint32_t b = 0; b < h.B; ++b)
+        if (h.box_start[b] >= h.Q || h.state_box[h.box_start[b]] != b) {
+            *err = "box_start[b] must be a state of box b";
+            return CFPQ_ERR_INVALID_ARG;
+        }
+    for (uint32_t k = 0; k < r->n_trans; ++k) {
+        HostRSM::Tr t{r->tr_from[k], r->tr_kind[k], r->tr_sym[k], r->tr_to[k]};
+        if (t.from >= h.Q || t.to >= h.Q || h.state_box[t.from] != h.state_box[t.to]) {
+            *err = "transition " + std::to_string(k) + " leaves its box or names a bad state";
+            return CFPQ_ERR_INVALID_ARG;
+        }
+        if (t.kind > 1 || (t.kind == 1 && t.sym >= h.B)) {
+            *err = "transition " + std::to_string(k) + " has a bad kind or box symbol";
+            return CFPQ_ERR_INVALID_ARG;
+        }
+        if (t.kind == 0) h.max_terminal_plus1 = std::max(h.max_terminal_plus1, t.sym + 1);
+        h.tr.push_back(t);
+    }
+    std::sort(h.tr.begin(), h.tr.end(), [](const HostRSM::Tr &a, const HostRSM::Tr &b) {
+        if (a.from != b.from) return a.from < b.from;
+        if (a.kind != b.kind) return a.kind < b.kind;
+        if (a.sym != b.sym) return a.sym < b.sym;
+        return a.to < b.to;
+    });
+    h.tr.erase(std::unique(h.tr.begin(), h.tr.end(),
+                           [](const HostRSM::Tr &a, const HostRSM::Tr &b) {
+                               return a.from == b.from && a.kind == b.kind && a.sym == b.sym && a.to == b.to;
+                           }),
+               h.tr.end());
+    *out = std::move(h);
+    return CFPQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Graph staging (edge list -> per-label deduplicated CSR), on the device.
+// ---------------------------------------------------------------------------
+int stage_graph(GraphDev *g, Allocator *A, cudaStream_t st, uint32_t n, uint32_t n_term, size_t m, const uint32_t *src,
+                const uint32_t *lbl, const uint32_t *dst, bool device_ptrs, std::string *err) {
+    if (n == 0 || n_term == 0) { *err = "graph needs n_vertices > 0 and n_terminals > 0"; return CFPQ_ERR_INVALID_ARG; }
+    if (m && (!src || !lbl || !dst)) { *err = "edge arrays are NULL"; return CFPQ_ERR_INVALID_ARG; }
+    if (m >= 0xffffffffull) { *err = "more than 2^32-1 edges"; return CFPQ_ERR_UNSUPPORTED; }
+    const uint32_t n_pad = (n + 127u) & ~127u, W = n_pad / 64u;
+    if (vpl_for_words(W) == 0) { *err = "graphs above 65536 vertices are not supported"; return CFPQ_ERR_UNSUPPORTED; }
+    const size_t rows = (size_t)n_term * n;
+    if (rows + 1 >= 0xffffffffull) { *err = "n_vertices * n_terminals too large"; return CFPQ_ERR_UNSUPPORTED; }
+    const size_t mm = m ? m : 1;
+    const bool realloc = !(g->csr_off.p && g->csr_off.bytes >= (rows + 1) * 4 && g->csr_col.bytes >= mm * 4);
+    const size_t nb = (rows + 4095) / 4096 + 2;
+    if (!g->csr_off.ensure(A, (rows + 1) * 4, err) || !g->csr_col.ensure(A, mm * 4, err) ||
+        !g->cnt.ensure(A, rows * 4, err) || !g->off.ensure(A, (rows + 1) * 4, err) || !g->col.ensure(A, mm * 4, err) ||
+        !g->ucnt.ensure(A, rows * 4, err) || !g->scan_tmp.ensure(A, nb * 4, err) ||
+        !g->label_map.ensure(A, (size_t)n_term * 4, err) || !g->err.ensure(A, 16, err))
+        return CFPQ_ERR_OUT_OF_MEMORY;
+    const uint32_t *s = src, *l = lbl, *d = dst;
+    if (!device_ptrs && m) {
+        if (!g->e_src.ensure(A, m * 4, err) || !g->e_lbl.ensure(A, m * 4, err) || !g->e_dst.ensure(A, m * 4, err))
+            return CFPQ_ERR_OUT_OF_MEMORY;
+        ENG_CK(cudaMemcpyAsync(g->e_src.p, src, m * 4, cudaMemcpyHostToDevice, st));
+        ENG_CK(cudaMemcpyAsync(g->e_lbl.p, lbl, m * 4, cudaMemcpyHostToDevice, st));
+        ENG_CK(cudaMemcpyAsync(g->e_dst.p, dst, m * 4, cudaMemcpyHostToDevice, st));
+        s = g->e_src.as<uint32_t>();
+        l = g->e_lbl.as<uint32_t>();
+        d = g->e_dst.as<uint32_t>();
+    }
+    if (g->n_term != n_term || realloc) {
+        std::vector<int32_t> lm(n_term);
+        for (uint32_t i = 0; i < n_term; ++i) lm[i] = (int32_t)i;
+        ENG_CK(cudaMemcpyAsync(g->label_map.p, lm.data(), n_term * 4, cudaMemcpyHostToDevice, st));
+        ENG_CK(cudaStreamSynchronize(st));
+    }
+    uint32_t *cnt = g->cnt.as<uint32_t>(), *off = g->off.as<uint32_t>(), *col = g->col.as<uint32_t>();
+    uint32_t *ucnt = g->ucnt.as<uint32_t>(), *tmp = g->scan_tmp.as<uint32_t>();
+    int *errf = g->err.as<int>();
+    ENG_CK(cudaMemsetAsync(cnt, 0, rows * 4, st));
+    ENG_CK(cudaMemsetAsync(errf, 0, 16, st));
+    ENG_CK(launch_stage_count(s, l, d, m, n, n_term, g->label_map.as<int32_t>(), cnt, errf, st));
+    ENG_CK(scan_exclusive(cnt, off, rows, tmp, st));
+    ENG_CK(cudaMemsetAsync(ucnt, 0, rows * 4, st));
+    ENG_CK(launch_stage_fill(s, l, d, m, n, n_term, g->label_map.as<int32_t>(), off, ucnt, col, st));
+    ENG_CK(launch_stage_unique(off, col, ucnt, rows, st));
+    ENG_CK(scan_exclusive(ucnt, g->csr_off.as<uint32_t>(), rows, tmp, st));
+    ENG_CK(launch_stage_compact(off, col, g->csr_off.as<uint32_t>(), g->csr_col.as<uint32_t>(), rows, st));
+    int herr = 0;
+    uint32_t total = 0;
+    ENG_CK(cudaMemcpyAsync(&herr, errf, 4, cudaMemcpyDeviceToHost, st));
+    ENG_CK(cudaMemcpyAsync(&total, g->csr_off.as<uint32_t>() + rows, 4, cudaMemcpyDeviceToHost, st));
+    ENG_CK(cudaStreamSynchronize(st));
+    if (herr) {
+        *err = "an edge names a vertex >= n_vertices or a label >= n_terminals";
+        g->n = 0;
+        return CFPQ_ERR_INVALID_ARG;
+    }
+    if (realloc || g->n != n || g->n_term != n_term) g->generation += 1;
+    g->n = n;
+    g->n_pad = n_pad;
+    g->W = W;
+    g->n_term = n_term;
+    g->m_in = m;
+    g->m_unique = total;
+    g->host_valid = false;
+    return CFPQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Query planning: which n x n state blocks of C3 can be nonzero.
+// ---------------------------------------------------------------------------
+static uint32_t next_pow2(uint32_t x) {
+    uint32_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+int QueryDev::prepare(Allocator *A, std::string *err) {
+    if (!g || g->n == 0) { *err = "no graph loaded"; return CFPQ_ERR_STATE; }
+    if (rsm.max_terminal_plus1 > g->n_term) {
+        *err = "the RSM reads a terminal >= the graph's n_terminals";
+        return CFPQ_ERR_INVALID_ARG;
+    }
+    const bool same = prepared && n == g->n && W == g->W && Q == rsm.Q && B == rsm.B;
+    n = g->n;
+    W = g->W;
+    Q = rsm.Q;
+    B = rsm.B;
+    vpl = (uint32_t)vpl_for_words(W);
+    if (!vpl) { *err = "unsupported row width"; return CFPQ_ERR_UNSUPPORTED; }
+    lpr = std::min<uint32_t>(32u, next_pow2(((W / 2) + vpl - 1) / vpl));
+    // reach[s][t]: t reachable from s by one or more RSM transitions (any
+    // symbol).  Block (s,t) of M3 is OR over transitions s -l-> t of M2^l, so
+    // block (s,t) of C3 = M3^+ can only be nonzero when reach[s][t].
+    std::vector<uint8_t> reach((size_t)Q * Q, 0);
+    for (const auto &t : rsm.tr) reach[(size_t)t.from * Q + t.to] = 1;
+    for (uint32_t k = 0; k < Q; ++k)
+        for (uint32_t i = 0; i < Q; ++i)
+            if (reach[(size_t)i * Q + k])
+                for (uint32_t j = 0; j < Q; ++j)
+                    if (reach[(size_t)k * Q + j]) reach[(size_t)i * Q + j] = 1;
+    blk_of.assign((size_t)Q * Q, -1);
+    blocks.clear();
+    for (uint32_t s = 0; s < Q; ++s)
+        for (uint32_t t = 0; t < Q; ++t)
+            if (reach[(size_t)s * Q + t]) {
+                blk_of[(size_t)s * Q + t] = (int32_t)blocks.size();
+                blocks.push_back({s, t});
+            }
+    // Sources of block (s,t): transitions s -l-> u with u == t or t reachable from u.
+    srcs.clear();
+    blk_src0.assign(blocks.size(), 0);
+    blk_nsrc.assign(blocks.size(), 0);
+    for (size_t b = 0; b < blocks.size(); ++b) {
+        const uint32_t s = blocks[b].first, t = blocks[b].second;
+        blk_src0[b] = (uint32_t)srcs.size();
+        for (const auto &tr : rsm.tr) {
+            if (tr.from != s) continue;
+            const uint32_t u = tr.to;
+            const bool ident = (u == t);
+            const int32_t rb = blk_of[(size_t)u * Q + t];
+            if (!ident && rb < 0) continue;
+            srcs.push_back({tr.kind, tr.sym, ident ? 1u : 0u, rb});
+        }
+        blk_nsrc[b] = (uint32_t)srcs.size() - blk_src0[b];
+    }
+    // Extraction blocks: (q0_b, f) for f final in box b.
+    fblocks.clear();
+    box_f0.assign(B, 0);
+    box_nf.assign(B, 0);
+    for (uint32_t b = 0; b < B; ++b) {
+        box_f0[b] = (uint32_t)fblocks.size();
+        const uint32_t q0 = rsm.box_start[b];
+        for (uint32_t f = 0; f < Q; ++f)
+            if (rsm.state_box[f] == b && rsm.final_[f] && blk_of[(size_t)q0 * Q + f] >= 0)
+                fblocks.push_back((uint32_t)blk_of[(size_t)q0 * Q + f]);
+        box_nf[b] = (uint32_t)fblocks.size() - box_f0[b];
+    }
+    const size_t nblk = blocks.size();
+    const size_t bw = (size_t)n * W * 8;
+    if (!blk_mem.ensure(A, std::max<size_t>(nblk, 1) * bw, err) ||
+        !stamp_mem.ensure(A, std::max<size_t>(nblk, 1) * n * 4, err) ||
+        !last_mem.ensure(A, std::max<size_t>(nblk, 1) * 4, err) || !m2_mem.ensure(A, (size_t)B * bw, err) ||
+        !a2_mem.ensure(A, (size_t)B * bw, err) || !a2it_mem.ensure(A, (size_t)B * n * 4, err) ||
+        !boxit_mem.ensure(A, (size_t)B * 4, err))
+        return CFPQ_ERR_OUT_OF_MEMORY;
+    device_bytes = blk_mem.bytes + stamp_mem.bytes + last_mem.bytes + m2_mem.bytes + a2_mem.bytes + a2it_mem.bytes +
+                   boxit_mem.bytes;
+    (void)same;
+    prepared = true;
+    graph_generation = g->generation;
+    return CFPQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Executor.
+// ---------------------------------------------------------------------------
+static int vpl_index(uint32_t vpl) {
+    switch (vpl) {
+        case 1: return 0;
+        case 2: return 1;
+        case 4: return 2;
+        case 8: return 3;
+        default: return 4;
+    }
+}
+static const int kVplOf[5] = {1, 2, 4, 8, 16};
+
+int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
+    const uint32_t nq = (uint32_t)qs.size();
+    if (!ctls.ensure(A, std::max<uint32_t>(nq, 1) * sizeof(QCtl), err) || !running.ensure(A, 16, err))
+        return CFPQ_ERR_OUT_OF_MEMORY;
+    QCtl *dctl = ctls.as<QCtl>();
+    std::vector<SrcDesc> hs;
+    std::vector<GItem> hi[5];
+    std::vector<FDesc> hf;
+    std::vector<XItem> hx[5];
+    std::vector<unsigned char> he;
+    const size_t esz = eps_desc_size();
+    n_eds = 0;
+    for (uint32_t qi = 0; qi < nq; ++qi) {
+        QueryDev &q = *qs[qi];
+        const GraphDev &g = *q.g;
+        QCtl *cp = dctl + qi;
+        const uint32_t base = (uint32_t)hs.size();
+        for (const auto &s : q.srcs) {
+            SrcDesc d;
+            memset(&d, 0, sizeof(d));
+            if (s.label_kind == 0) {
+                d.csr_off = g.csr_off.as<uint32_t>() + (size_t)s.label * q.n;
+                d.csr_col = g.csr_col.as<uint32_t>();
+            } else {
+                d.nt_all = q.m2_ptr(s.label);
+                d.nt_new = q.a2_ptr(s.label);
+                d.nt_new_it = q.a2it_mem.as<uint32_t>() + (size_t)s.label * q.n;
+                d.box_new_it = q.boxit_mem.as<uint32_t>() + s.label;
+            }
+            if (s.rblk >= 0) {
+                d.rblk = q.blk_ptr((uint32_t)s.rblk);
+                d.rstamp = q.stamp_ptr((uint32_t)s.rblk);
+                d.rlast = q.last_mem.as<uint32_t>() + s.rblk;
+            }
+            d.ident = s.ident;
+            d.dense = 0;
+            hs.push_back(d);
+        }
+        const int vi = vpl_index(q.vpl);
+        const uint32_t rows_per_step = 8u * (32u / q.lpr);
+        const uint32_t rpi = std::max<uint32_t>(64u, rows_per_step * 4u);
+        for (size_t b = 0; b < q.blocks.size(); ++b) {
+            if (q.blk_nsrc[b] == 0) continue;
+            for (uint32_t r0 = 0; r0 < q.n; r0 += rpi) {
+                GItem it;
+                it.out = q.blk_ptr((uint32_t)b);
+                it.out_stamp = q.stamp_ptr((uint32_t)b);
+                it.out_last = q.last_mem.as<uint32_t>() + b;
+                it.ctl = cp;
+                it.src0 = base + q.blk_src0[b];
+                it.nsrc = q.blk_nsrc[b];
+                it.row0 = r0;
+                it.row1 = std::min(q.n, r0 + rpi);
+                it.W = q.W;
+                it.lpr = q.lpr;
+                hi[vi].push_back(it);
+            }
+        }
+        const uint32_t fbase = (uint32_t)hf.size();
+        for (uint32_t fb : q.fblocks) hf.push_back(FDesc{q.blk_ptr(fb), q.stamp_ptr(fb)});
+        for (uint32_t b = 0; b < q.B; ++b) {
+            if (q.box_nf[b] == 0) continue;
+            for (uint32_t r0 = 0; r0 < q.n; r0 += rpi) {
+                XItem x;
+                x.m2 = q.m2_ptr(b);
+                x.a2 = q.a2_ptr(b);
+                x.a2_it = q.a2it_mem.as<uint32_t>() + (size_t)b * q.n;
+                x.box_new_it = q.boxit_mem.as<uint32_t>() + b;
+                x.ctl = cp;
+                x.f0 = fbase + q.box_f0[b];
+                x.nf = q.box_nf[b];
+                x.row0 = r0;
+                x.row1 = std::min(q.n, r0 + rpi);
+                x.W = q.W;
+                x.lpr = q.lpr;
+                hx[vi].push_back(x);
+            }
+        }
+        for (uint32_t b = 0; b < q.B; ++b) {
+            if (!q.rsm.final_[q.rsm.box_start[b]]) continue;
+            he.resize(he.size() + esz);
+            fill_eps_desc(he.data() + he.size() - esz, q.m2_ptr(b), q.a2_ptr(b),
+                          q.a2it_mem.as<uint32_t>() + (size_t)b * q.n, q.boxit_mem.as<uint32_t>() + b, cp, q.n, q.W);
+            ++n_eds;
+        }
+    }
+    auto upload = [&](DBuf &buf, const void *h, size_t bytes) -> int {
+        if (!buf.ensure(A, std::max<size_t>(bytes, 64), err)) return CFPQ_ERR_OUT_OF_MEMORY;
+        if (bytes) ENG_CK(cudaMemcpyAsync(buf.p, h, bytes, cudaMemcpyHostToDevice, st));
+        return CFPQ_OK;
+    };
+    int rc;
+    if ((rc = upload(srcs, hs.data(), hs.size() * sizeof(SrcDesc)))) return rc;
+    if ((rc = upload(fds, hf.data(), hf.size() * sizeof(FDesc)))) return rc;
+    if ((rc = upload(eds, he.data(), he.size()))) return rc;
+    for (int v = 0; v < 5; ++v) {
+        n_items[v] = (uint32_t)hi[v].size();
+        n_xitems[v] = (uint32_t)hx[v].size();
+        if ((rc = upload(items[v], hi[v].data(), hi[v].size() * sizeof(GItem)))) return rc;
+        if ((rc = upload(xitems[v], hx[v].data(), hx[v].size() * sizeof(XItem)))) return rc;
+    }
+    ENG_CK(cudaStreamSynchronize(st));
+    drop_graph();
+    built = true;
+    return CFPQ_OK;
+}
+
+int Executor::enqueue_prologue(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes) {
+    std::string *err = nullptr;
+    for (QueryDev *q : qs) {
+        const size_t nblk = q->blocks.size();
+        ENG_CK(cudaMemsetAsync(q->blk_mem.p, 0, nblk * (size_t)q->n * q->W * 8, st));
+        ENG_CK(cudaMemsetAsync(q->stamp_mem.p, 0, nblk * (size_t)q->n * 4, st));
+        ENG_CK(cudaMemsetAsync(q->last_mem.p, 0, std::max<size_t>(nblk, 1) * 4, st));
+        ENG_CK(cudaMemsetAsync(q->m2_mem.p, 0, (size_t)q->B * q->n * q->W * 8, st));
+        ENG_CK(cudaMemsetAsync(q->a2it_mem.p, 0, (size_t)q->B * q->n * 4, st));
+        ENG_CK(cudaMemsetAsync(q->boxit_mem.p, 0, (size_t)q->B * 4, st));
+    }
+    ENG_CK(launch_ctl_reset(ctls.as<QCtl>(), (uint32_t)qs.size(), max_iter, max_rounds, max_passes, st));
+    ENG_CK(launch_eps_init(eds.p, n_eds, 152, st));
+    return CFPQ_OK;
+}
+
+int Executor::enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int use_handle, int *running_out) {
+    std::string *err = nullptr;
+    for (int v = 0; v < 5; ++v)
+        ENG_CK(launch_gather(kVplOf[v], items[v].as<GItem>(), n_items[v], srcs.as<SrcDesc>(), st));
+    for (int v = 0; v < 5; ++v)
+        ENG_CK(launch_extract(kVplOf[v], xitems[v].as<XItem>(), n_xitems[v], fds.as<FDesc>(), st));
+    ENG_CK(launch_control(ctls.as<QCtl>(), (uint32_t)qs.size(), h, use_handle, running_out, st));
+    return CFPQ_OK;
+}
+
+int Executor::build_graph(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes,
+                          std::string *err) {
+    drop_graph();
+    if (!cap_stream) ENG_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+    // Everything the graph reads was uploaded on `st`; order the capture after it.
+    ENG_CK(cudaStreamSynchronize(st));
+    const cudaStream_t cs = cap_stream;
+    cudaGraph_t prologue = nullptr;
+    ENG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_prologue(cs, max_iter, max_rounds, max_passes);
+    cudaError_t ce = cudaStreamEndCapture(cs, &prologue);
+    if (rc || ce != cudaSuccess) {
+        if (prologue) cudaGraphDestroy(prologue);
+        if (err) *err = std::string("prologue capture failed: ") + cudaGetErrorString(ce);
+        return CFPQ_ERR_CUDA;
+    }
+    ENG_CK(cudaGraphCreate(&graph, 0));
+    cudaGraphNode_t pro_node, loop_node;
+    ce = cudaGraphAddChildGraphNode(&pro_node, graph, nullptr, 0, prologue);
+    cudaGraphDestroy(prologue);
+    ENG_CK(ce);
+    cudaGraphConditionalHandle handle;
+    ENG_CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+    // cudaGraphNodeParams holds a union with a deleted default constructor.
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    memset(cp_raw, 0, sizeof(cp_raw));
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    ENG_CK(cudaGraphAddNode(&loop_node, graph, &pro_node, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ENG_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue_pass(cs, handle, 1, nullptr);
+    cudaGraph_t body_out = body;
+    ce = cudaStreamEndCapture(cs, &body_out);
+    if (rc || ce != cudaSuccess) {
+        if (err) *err = std::string("loop body capture failed: ") + cudaGetErrorString(ce);
+        drop_graph();
+        return CFPQ_ERR_CUDA;
+    }
+    ENG_CK(cudaGraphInstantiate(&exec, graph, 0));
+    return CFPQ_OK;
+}
+
+int Executor::read_ctls(cudaStream_t st, std::vector<QCtl> *out) {
+    std::string *err = nullptr;
+    out->resize(qs.size());
+    if (qs.empty()) return CFPQ_OK;
+    ENG_CK(cudaMemcpyAsync(out->data(), ctls.p, qs.size() * sizeof(QCtl), cudaMemcpyDeviceToHost, st));
+    ENG_CK(cudaStreamSynchronize(st));
+    return CFPQ_OK;
+}
+
+}  // namespace cfpq

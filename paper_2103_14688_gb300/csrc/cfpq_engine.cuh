@@ -1,0 +1,159 @@
+// cfpq_engine.cuh -- host-side engine of libcfpq (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cfpq.h"
+#include "cfpq_dev.cuh"
+
+namespace cfpq {
+
+// ---- kernel launchers (cfpq_kernels.cu) ----
+int vpl_for_words(uint32_t W);
+cudaError_t launch_gather(int vpl, const GItem *items, uint32_t n_items, const SrcDesc *srcs, cudaStream_t st);
+cudaError_t launch_extract(int vpl, const XItem *items, uint32_t n_items, const FDesc *fds, cudaStream_t st);
+cudaError_t launch_control(QCtl *ctls, uint32_t nq, cudaGraphConditionalHandle h, int use_handle, int *running_out,
+                           cudaStream_t st);
+cudaError_t launch_ctl_reset(QCtl *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes,
+                             cudaStream_t st);
+cudaError_t launch_eps_init(const void *eds, uint32_t ned, uint32_t grid, cudaStream_t st);
+size_t eps_desc_size();
+void fill_eps_desc(void *dst, uint64_t *m2, uint64_t *a2, uint32_t *a2_it, uint32_t *box_new_it, QCtl *ctl, uint32_t n,
+                   uint32_t W);
+cudaError_t scan_exclusive(const uint32_t *in, uint32_t *out, size_t n, uint32_t *tmp, cudaStream_t st);
+cudaError_t launch_stage_count(const uint32_t *src, const uint32_t *lbl, const uint32_t *dst, size_t m, uint32_t n,
+                               uint32_t n_term, const int32_t *label_map, uint32_t *cnt, int *err, cudaStream_t st);
+cudaError_t launch_stage_fill(const uint32_t *src, const uint32_t *lbl, const uint32_t *dst, size_t m, uint32_t n,
+                              uint32_t n_term, const int32_t *label_map, const uint32_t *off, uint32_t *fill,
+                              uint32_t *col, cudaStream_t st);
+cudaError_t launch_stage_unique(const uint32_t *off, uint32_t *col, uint32_t *ucnt, size_t rows, cudaStream_t st);
+cudaError_t launch_stage_compact(const uint32_t *off, const uint32_t *col, const uint32_t *uoff, uint32_t *ucol,
+                                 size_t rows, cudaStream_t st);
+cudaError_t launch_popcount(const uint64_t *p, size_t nwords, unsigned long long *out, cudaStream_t st);
+cudaError_t launch_copy_rows(const uint64_t *const *ptrs, const uint32_t *rows, uint32_t njobs, uint32_t W,
+                             uint64_t *out, cudaStream_t st);
+
+// ---- device memory ----
+struct Allocator {
+    cfpq_alloc_fn alloc = nullptr;
+    cfpq_free_fn free = nullptr;
+    void *user = nullptr;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;
+    size_t in_use = 0;
+    void *get(size_t bytes, std::string *err);
+    void put(void *p, size_t bytes);
+};
+
+// An owned device buffer.
+struct DBuf {
+    Allocator *A = nullptr;
+    void *p = nullptr;
+    size_t bytes = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { reset(); }
+    void reset() {
+        if (p && A) A->put(p, bytes);
+        p = nullptr;
+        bytes = 0;
+    }
+    // (Re)allocate to at least `want` bytes; returns false on failure.
+    bool ensure(Allocator *a, size_t want, std::string *err) {
+        if (p && bytes >= want) return true;
+        reset();
+        A = a;
+        if (want == 0) want = 256;
+        p = a->get(want, err);
+        if (!p) return false;
+        bytes = want;
+        return true;
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+// Host copy of an RSM (validated).
+struct HostRSM {
+    uint32_t Q = 0, B = 0, start_box = 0;
+    std::vector<uint32_t> box_start, state_box;
+    std::vector<uint8_t> final_;
+    struct Tr { uint32_t from, kind, sym, to; };
+    std::vector<Tr> tr;  // deduplicated, sorted
+    uint32_t max_terminal_plus1 = 0;
+};
+int copy_rsm(const cfpq_rsm *r, HostRSM *out, std::string *err);
+
+// A staged graph on the device: per terminal label, deduplicated CSR rows.
+struct GraphDev {
+    uint32_t n = 0, n_pad = 0, W = 0, n_term = 0;
+    size_t m_in = 0, m_unique = 0;
+    DBuf csr_off;  // [n_term * n + 1]
+    DBuf csr_col;  // [m_unique]
+    // staging scratch
+    DBuf e_src, e_lbl, e_dst, cnt, off, col, ucnt, scan_tmp, label_map, err;
+    std::vector<uint32_t> h_off;  // host copies on demand (paths)
+    std::vector<uint32_t> h_col;
+    bool host_valid = false;
+    uint64_t generation = 0;
+};
+
+// Device state and descriptors of one query (graph + RSM).
+struct QueryDev {
+    GraphDev *g = nullptr;
+    HostRSM rsm;
+    uint32_t n = 0, W = 0, Q = 0, B = 0, vpl = 0, lpr = 0;
+    std::vector<int32_t> blk_of;  // Q*Q -> block or -1
+    std::vector<std::pair<uint32_t, uint32_t>> blocks;
+    DBuf blk_mem, stamp_mem, last_mem, m2_mem, a2_mem, a2it_mem, boxit_mem;
+    uint64_t device_bytes = 0;
+    // host descriptors (pointers filled once buffers exist; ctl set by the executor)
+    struct Src { uint32_t label_kind, label, ident; int32_t rblk; };
+    std::vector<uint32_t> blk_src0, blk_nsrc;  // per block
+    std::vector<Src> srcs;
+    std::vector<uint32_t> box_f0, box_nf;
+    std::vector<uint32_t> fblocks;  // per box list of block ids (q0, f)
+    bool prepared = false;
+    uint64_t graph_generation = 0;
+    int prepare(Allocator *A, std::string *err);  // plan + buffers
+    uint64_t *blk_ptr(uint32_t b) const { return blk_mem.as<uint64_t>() + (size_t)b * n * W; }
+    uint32_t *stamp_ptr(uint32_t b) const { return stamp_mem.as<uint32_t>() + (size_t)b * n; }
+    uint64_t *m2_ptr(uint32_t b) const { return m2_mem.as<uint64_t>() + (size_t)b * n * W; }
+    uint64_t *a2_ptr(uint32_t b) const { return a2_mem.as<uint64_t>() + (size_t)b * n * W; }
+};
+
+// Runs the fixpoint of a set of queries with shared launches.
+struct Executor {
+    std::vector<QueryDev *> qs;
+    DBuf ctls, items[5], xitems[5], srcs, fds, eds, running;
+    uint32_t n_items[5] = {0, 0, 0, 0, 0}, n_xitems[5] = {0, 0, 0, 0, 0};
+    uint32_t n_eds = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream: capture is not allowed on the legacy default stream
+    bool built = false;
+    ~Executor() {
+        drop_graph();
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+    void drop_graph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+    }
+    int assemble(Allocator *A, cudaStream_t st, std::string *err);
+    int enqueue_prologue(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes);
+    int enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int use_handle, int *running_out);
+    int build_graph(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes, std::string *err);
+    int read_ctls(cudaStream_t st, std::vector<QCtl> *out);
+};
+
+int stage_graph(GraphDev *g, Allocator *A, cudaStream_t st, uint32_t n, uint32_t n_term, size_t m, const uint32_t *src,
+                const uint32_t *lbl, const uint32_t *dst, bool device_ptrs, std::string *err);
+
+}  // namespace cfpq

@@ -1,0 +1,649 @@
+// cfpq_kernels.cu -- CUDA kernels of libcfpq for sm_103a.
+//
+// The index-creation loop of Listing 1 (arXiv 2103.14688, Sec. 3.1) runs as
+// passes of three kernels, all driven by per-query control words in device
+// memory (QCtl):
+//   k_gather   one closure pass.  For every output block C[s,t] and row x it
+//              ORs, over the product edges (s,x) -> (u,y) generated on the fly
+//              from the RSM transitions s -l-> u and the graph edges (x,y) of
+//              M2^l (the Kronecker product M1 (x) M2, never materialised), the
+//              row (I + C)[u,t][y].  The first pass of an iteration uses only
+//              the new edges A2 (left-distributivity, Sec. 3.1.1) with whole
+//              source rows; later passes use all edges but only source rows
+//              whose dirty stamp says they changed in the previous pass (the
+//              incremental closure of Sec. 3.1.1 recomputes only what the new
+//              edges reach).
+//   k_extract  after a pass that changed nothing: for every box b and final f
+//              of b, new = C[q0_b, f] & ~M2^b on the rows changed in this
+//              iteration; M2^b |= new; A2^b = new (Listing 1, extraction via
+//              getStates/getCoordinates).
+//   k_control  advances each query's loop state and sets the CUDA-graph
+//              conditional (Listing 1: "while M2 is changing").
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cfpq_dev.cuh"
+
+namespace cfpq {
+
+#define FULLMASK 0xffffffffu
+
+__device__ __forceinline__ bool nz4(const uint4 &v) { return (v.x | v.y | v.z | v.w) != 0u; }
+__device__ __forceinline__ void or4(uint4 &a, const uint4 &b) {
+    a.x |= b.x; a.y |= b.y; a.z |= b.z; a.w |= b.w;
+}
+__device__ __forceinline__ uint4 andnot4(const uint4 &a, const uint4 &b) {
+    return make_uint4(a.x & ~b.x, a.y & ~b.y, a.z & ~b.z, a.w & ~b.w);
+}
+__device__ __forceinline__ int popc4(const uint4 &v) {
+    return __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+}
+
+// Set bit `pos` (0..127) of a 128-bit vector.
+__device__ __forceinline__ void setbit4(uint4 &v, uint32_t pos) {
+    const uint32_t m = 1u << (pos & 31);
+    switch ((pos >> 5) & 3) {
+        case 0: v.x |= m; break;
+        case 1: v.y |= m; break;
+        case 2: v.z |= m; break;
+        default: v.w |= m; break;
+    }
+}
+
+// Lowest set bit of a 128-bit vector, -1 if none; clears it when `clear`.
+__device__ __forceinline__ int lowbit4(uint4 &v, bool clear) {
+    if (v.x) { int b = __ffs(v.x) - 1; if (clear) v.x &= v.x - 1; return b; }
+    if (v.y) { int b = __ffs(v.y) - 1; if (clear) v.y &= v.y - 1; return 32 + b; }
+    if (v.z) { int b = __ffs(v.z) - 1; if (clear) v.z &= v.z - 1; return 64 + b; }
+    if (v.w) { int b = __ffs(v.w) - 1; if (clear) v.w &= v.w - 1; return 96 + b; }
+    return -1;
+}
+
+__device__ __forceinline__ bool src_active(const SrcDesc &d, uint32_t mode, uint32_t iter, uint32_t g) {
+    if (d.dense) return false;
+    if (mode == kModeNew) {
+        if (d.csr_off) return iter == 1;
+        return *d.box_new_it == iter;
+    }
+    return d.rblk != nullptr && (*d.rlast + 1u >= g);
+}
+
+// --------------------------------------------------------------------------
+// Closure pass (bit-packed rows).  One CTA of 8 warps per work item; a row is
+// handled by a group of `lpr` lanes, each lane holding VPL 128-bit vectors
+// (words 2v, 2v+1 for v = lane_in_group + j * lpr).
+// --------------------------------------------------------------------------
+template <int VPL>
+__global__ void __launch_bounds__(256) k_gather(const GItem *__restrict__ items, const SrcDesc *__restrict__ srcs) {
+    const GItem it = items[blockIdx.x];
+    const QCtl *c = it.ctl;
+    if (c->phase != kPhaseRun) return;
+    const uint32_t g = c->g, iter = c->iter, mode = c->mode;
+
+    int act = 0;
+    for (uint32_t k = threadIdx.x; k < it.nsrc; k += blockDim.x) act |= src_active(srcs[it.src0 + k], mode, iter, g);
+    if (!__syncthreads_or(act)) return;
+
+    __shared__ unsigned long long s_changed, s_ors;
+    if (threadIdx.x == 0) { s_changed = 0; s_ors = 0; }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lpr = (int)it.lpr, grp = lane / lpr, gl = lane % lpr, rpw = 32 / lpr;
+    const unsigned gmask = (lpr == 32 ? FULLMASK : ((1u << lpr) - 1u)) << (grp * lpr);
+    const uint32_t W = it.W, nvec = W / 2;
+    uint32_t my_changed = 0, my_ors = 0;
+
+    for (uint32_t rbase = it.row0 + (uint32_t)(warp * rpw); rbase < it.row1; rbase += 8u * rpw) {
+        const uint32_t row = rbase + grp;
+        const bool valid = row < it.row1;
+        uint4 acc[VPL];
+#pragma unroll
+        for (int j = 0; j < VPL; ++j) acc[j] = make_uint4(0, 0, 0, 0);
+
+        for (uint32_t k = 0; k < it.nsrc; ++k) {
+            const SrcDesc d = srcs[it.src0 + k];
+            if (!src_active(d, mode, iter, g)) continue;
+            const bool use_ident = (mode == kModeNew) && d.ident;
+            if (!use_ident && d.rblk == nullptr) continue;
+            const bool check_dirty = (mode == kModeProp);
+
+            // OR of source row y of C[u,t] (and the product edge itself).
+            auto take = [&](uint32_t y) {
+                if (use_ident) {
+                    const uint32_t v = y >> 7;
+                    if ((int)(v % lpr) == gl) {
+                        const int j = (int)(v / lpr);
+#pragma unroll
+                        for (int jj = 0; jj < VPL; ++jj)
+                            if (jj == j) setbit4(acc[jj], y & 127u);
+                    }
+                }
+                if (d.rblk) {
+                    if (check_dirty && d.rstamp[y] + 1u < g) return;
+                    const uint4 *r = reinterpret_cast<const uint4 *>(d.rblk + (size_t)y * W);
+#pragma unroll
+                    for (int j = 0; j < VPL; ++j) {
+                        const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
+                        if (v < nvec) or4(acc[j], r[v]);
+                    }
+                    if (gl == 0) ++my_ors;
+                }
+            };
+
+            if (d.csr_off) {
+                const uint32_t e0 = valid ? d.csr_off[row] : 0u, e1 = valid ? d.csr_off[row + 1] : 0u;
+                for (uint32_t e = e0; e < e1; ++e) take(d.csr_col[e]);
+            } else {
+                const uint64_t *adj;
+                bool rowok;
+                if (mode == kModeNew) { adj = d.nt_new; rowok = valid && d.nt_new_it[row] == iter; }
+                else { adj = d.nt_all; rowok = valid; }
+                uint4 a[VPL];
+#pragma unroll
+                for (int j = 0; j < VPL; ++j) {
+                    const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
+                    a[j] = (rowok && v < nvec) ? reinterpret_cast<const uint4 *>(adj + (size_t)row * W)[v]
+                                               : make_uint4(0, 0, 0, 0);
+                }
+                // Enumerate the set bits of the adjacency row, lowest first,
+                // one per group per step (ballot picks the holding lane).
+                while (true) {
+                    bool mine_nz = false;
+#pragma unroll
+                    for (int j = 0; j < VPL; ++j) mine_nz |= nz4(a[j]);
+                    const unsigned b = __ballot_sync(FULLMASK, mine_nz);
+                    if (b == 0u) break;
+                    const unsigned gb = b & gmask;
+                    const int holder = gb ? (__ffs(gb) - 1) : lane;
+                    int ypos = -1;
+                    if (lane == holder && gb) {
+#pragma unroll
+                        for (int j = 0; j < VPL; ++j) {
+                            if (ypos < 0 && nz4(a[j])) {
+                                const int bit = lowbit4(a[j], true);
+                                ypos = (int)(((uint32_t)gl + (uint32_t)j * lpr) * 128u) + bit;
+                            }
+                        }
+                    }
+                    const int y = __shfl_sync(FULLMASK, ypos, holder);
+                    if (gb) take((uint32_t)y);
+                }
+            }
+        }
+
+        bool ch = false;
+        if (valid) {
+            uint4 *o = reinterpret_cast<uint4 *>(it.out + (size_t)row * W);
+#pragma unroll
+            for (int j = 0; j < VPL; ++j) {
+                const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
+                if (v < nvec && nz4(acc[j])) {
+                    const uint4 old = o[v];
+                    const uint4 nw = andnot4(acc[j], old);
+                    if (nz4(nw)) {
+                        uint4 m = old;
+                        or4(m, nw);
+                        o[v] = m;
+                        ch = true;
+                    }
+                }
+            }
+        }
+        const unsigned chb = __ballot_sync(FULLMASK, ch);
+        if ((chb & gmask) && gl == 0) {
+            it.out_stamp[row] = g;
+            ++my_changed;
+        }
+    }
+    if (my_changed) atomicAdd(&s_changed, (unsigned long long)my_changed);
+    if (my_ors) atomicAdd(&s_ors, (unsigned long long)my_ors);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        QCtl *cw = it.ctl;
+        if (s_changed) {
+            *it.out_last = g;
+            atomicAdd(&cw->changed_rows, s_changed);
+        }
+        if (s_ors) atomicAdd(&cw->row_ors, s_ors);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Extraction: runs for a query only after a pass that changed no row.
+// --------------------------------------------------------------------------
+template <int VPL>
+__global__ void __launch_bounds__(256) k_extract(const XItem *__restrict__ items, const FDesc *__restrict__ fds) {
+    const XItem it = items[blockIdx.x];
+    const QCtl *c = it.ctl;
+    if (c->phase != kPhaseRun || c->changed_rows != 0ull) return;
+    const uint32_t g0 = c->g_iter_start, iter = c->iter;
+    __shared__ unsigned long long s_new;
+    if (threadIdx.x == 0) s_new = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lpr = (int)it.lpr, grp = lane / lpr, gl = lane % lpr, rpw = 32 / lpr;
+    const unsigned gmask = (lpr == 32 ? FULLMASK : ((1u << lpr) - 1u)) << (grp * lpr);
+    const uint32_t W = it.W, nvec = W / 2;
+    uint32_t my_new = 0;
+    for (uint32_t rbase = it.row0 + (uint32_t)(warp * rpw); rbase < it.row1; rbase += 8u * rpw) {
+        const uint32_t row = rbase + grp;
+        const bool valid = row < it.row1;
+        uint4 acc[VPL];
+#pragma unroll
+        for (int j = 0; j < VPL; ++j) acc[j] = make_uint4(0, 0, 0, 0);
+        bool any = false;
+        for (uint32_t f = 0; f < it.nf; ++f) {
+            const FDesc fd = fds[it.f0 + f];
+            if (!valid || fd.stamp[row] < g0) continue;
+            any = true;
+            const uint4 *r = reinterpret_cast<const uint4 *>(fd.blk + (size_t)row * W);
+#pragma unroll
+            for (int j = 0; j < VPL; ++j) {
+                const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
+                if (v < nvec) or4(acc[j], r[v]);
+            }
+        }
+        bool has = false;
+        if (any) {
+            const uint4 *m = reinterpret_cast<const uint4 *>(it.m2 + (size_t)row * W);
+#pragma unroll
+            for (int j = 0; j < VPL; ++j) {
+                const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
+                if (v < nvec) {
+                    acc[j] = andnot4(acc[j], m[v]);
+                    if (nz4(acc[j])) has = true;
+                }
+            }
+        }
+        const unsigned hb = __ballot_sync(FULLMASK, has);
+        if (hb & gmask) {
+            uint4 *m = reinterpret_cast<uint4 *>(it.m2 + (size_t)row * W);
+            uint4 *a = reinterpret_cast<uint4 *>(it.a2 + (size_t)row * W);
+#pragma unroll
+            for (int j = 0; j < VPL; ++j) {
+                const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
+                if (v < nvec) {
+                    a[v] = acc[j];
+                    if (nz4(acc[j])) {
+                        uint4 mm = m[v];
+                        or4(mm, acc[j]);
+                        m[v] = mm;
+                        my_new += (uint32_t)popc4(acc[j]);
+                    }
+                }
+            }
+            if (gl == 0) it.a2_it[row] = iter + 1;
+        }
+    }
+    if (my_new) atomicAdd(&s_new, (unsigned long long)my_new);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_new) {
+        *it.box_new_it = iter + 1;
+        atomicAdd(&it.ctl->new_edges, s_new);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Loop control: one CTA for all queries.
+// --------------------------------------------------------------------------
+__global__ void k_control(QCtl *ctls, uint32_t nq, cudaGraphConditionalHandle handle, int use_handle,
+                          int *running_out) {
+    int running = 0;
+    for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
+        QCtl &c = ctls[q];
+        if (c.phase != kPhaseRun) continue;
+        c.passes += 1;
+        c.rounds_total += 1;
+        if (c.changed_rows == 0ull) {
+            c.iters_done = c.iter;
+            c.edges_total += c.new_edges;
+            if (c.new_edges == 0ull) {
+                c.phase = kPhaseDone;
+            } else if (c.max_iter && c.iter >= c.max_iter) {
+                c.status = kStatusIterCap;
+                c.phase = kPhaseDone;
+            } else {
+                c.iter += 1;
+                c.g += 1;
+                c.mode = kModeNew;
+                c.g_iter_start = c.g;
+                c.rounds_in_iter = 0;
+            }
+            c.new_edges = 0;
+        } else {
+            c.rounds_in_iter += 1;
+            c.g += 1;
+            c.mode = kModeProp;
+            if (c.max_rounds && c.rounds_in_iter >= c.max_rounds) {
+                c.status = kStatusRoundCap;
+                c.phase = kPhaseDone;
+            }
+        }
+        if (c.phase == kPhaseRun && c.passes >= c.max_passes) {
+            c.status = kStatusPassCap;
+            c.phase = kPhaseDone;
+        }
+        c.changed_rows = 0;
+        running |= (c.phase == kPhaseRun);
+    }
+    running = __syncthreads_or(running);
+    if (threadIdx.x == 0) {
+        if (use_handle) cudaGraphSetConditional(handle, running ? 1u : 0u);
+        if (running_out) *running_out = running;
+    }
+}
+
+// Reset the loop state of queries [0, nq) (start of a run).
+__global__ void k_ctl_reset(QCtl *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        QCtl c;
+        memset(&c, 0, sizeof(c));
+        c.g = 2;
+        c.iter = 1;
+        c.mode = kModeNew;
+        c.phase = kPhaseRun;
+        c.g_iter_start = 2;
+        c.max_iter = max_iter;
+        c.max_rounds = max_rounds;
+        c.max_passes = max_passes;
+        ctls[q] = c;
+    }
+}
+
+// Epsilon case of Listing 1: a box whose start state is final derives the
+// empty word, so M2^b[i,i] = 1 for every vertex i.  These edges are new edges
+// of the first iteration (A2^b rows = e_i), so that they take part in the
+// product like any other nonterminal edge.
+struct EpsDesc {
+    uint64_t *m2, *a2;
+    uint32_t *a2_it, *box_new_it;
+    QCtl *ctl;
+    uint32_t n, W;
+};
+__global__ void k_eps_init(const EpsDesc *__restrict__ eds, uint32_t ned) {
+    for (uint32_t e = 0; e < ned; ++e) {
+        const EpsDesc d = eds[e];
+        const size_t total = (size_t)d.n * d.W;
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+            const uint32_t row = (uint32_t)(i / d.W), w = (uint32_t)(i % d.W);
+            const uint64_t bit = (w == (row >> 6)) ? (1ull << (row & 63)) : 0ull;
+            d.a2[i] = bit;
+            if (bit) d.m2[i] |= bit;
+            if (w == 0) d.a2_it[row] = 1;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *d.box_new_it = 1;
+            atomicAdd(&d.ctl->edges_total, (unsigned long long)d.n);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Graph staging: edge list -> deduplicated CSR per used terminal label.
+// --------------------------------------------------------------------------
+__global__ void k_stage_count(const uint32_t *__restrict__ src, const uint32_t *__restrict__ lbl,
+                              const uint32_t *__restrict__ dst, size_t m, uint32_t n, uint32_t n_term,
+                              const int32_t *__restrict__ label_map, uint32_t *cnt, int *err) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t s = src[e], l = lbl[e], d = dst[e];
+        if (s >= n || d >= n || l >= n_term) { atomicOr(err, 1); continue; }
+        const int32_t li = label_map[l];
+        if (li >= 0) atomicAdd(&cnt[(size_t)li * n + s], 1u);
+    }
+}
+
+__global__ void k_stage_fill(const uint32_t *__restrict__ src, const uint32_t *__restrict__ lbl,
+                             const uint32_t *__restrict__ dst, size_t m, uint32_t n, uint32_t n_term,
+                             const int32_t *__restrict__ label_map, const uint32_t *__restrict__ off,
+                             uint32_t *fill, uint32_t *col) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t s = src[e], l = lbl[e], d = dst[e];
+        if (s >= n || d >= n || l >= n_term) continue;
+        const int32_t li = label_map[l];
+        if (li < 0) continue;
+        const size_t r = (size_t)li * n + s;
+        col[off[r] + atomicAdd(&fill[r], 1u)] = d;
+    }
+}
+
+// Sort each adjacency row and drop duplicates; ucnt[r] = distinct count.
+// Rows longer than kUniqueMax are left as they are: a repeated edge only
+// repeats an idempotent OR of the same source row, so duplicates cost time,
+// never correctness, and the per-row work stays bounded.
+constexpr uint32_t kUniqueMax = 256;
+__global__ void k_stage_unique(const uint32_t *__restrict__ off, uint32_t *col, uint32_t *ucnt, size_t rows) {
+    for (size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t a = off[r], b = off[r + 1];
+        if (b - a > kUniqueMax) { ucnt[r] = b - a; continue; }
+        for (uint32_t i = a + 1; i < b; ++i) {
+            const uint32_t v = col[i];
+            uint32_t j = i;
+            while (j > a && col[j - 1] > v) { col[j] = col[j - 1]; --j; }
+            col[j] = v;
+        }
+        uint32_t k = a;
+        for (uint32_t i = a; i < b; ++i)
+            if (i == a || col[i] != col[k - 1]) col[k++] = col[i];
+        ucnt[r] = k - a;
+    }
+}
+
+__global__ void k_stage_compact(const uint32_t *__restrict__ off, const uint32_t *__restrict__ col,
+                                const uint32_t *__restrict__ uoff, uint32_t *ucol, size_t rows) {
+    for (size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t a = off[r], u0 = uoff[r], k = uoff[r + 1] - u0;
+        for (uint32_t i = 0; i < k; ++i) ucol[u0 + i] = col[a + i];
+    }
+}
+
+// Exclusive scan of n uint32 (n < 2^32 total): out[0..n], out[n] = total.
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanChunk = kScanThreads * kScanPer;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t warp_sums[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULLMASK, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULLMASK, s, o);
+            if (lane >= o) s += t;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t base = wid ? warp_sums[wid - 1] : 0u;
+    if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_local(const uint32_t *__restrict__ in, uint32_t *out,
+                                                             uint32_t *block_sums, size_t n) {
+    const size_t base = (size_t)blockIdx.x * kScanChunk + (size_t)threadIdx.x * kScanPer;
+    uint32_t v[kScanPer], s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) { v[i] = (base + i < n) ? in[base + i] : 0u; s += v[i]; }
+    uint32_t tot;
+    uint32_t ex = block_exclusive_scan(s, &tot);
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        if (base + i < n) out[base + i] = ex;
+        ex += v[i];
+    }
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(uint32_t *block_sums, uint32_t nb, uint32_t *total_out) {
+    // nb <= kScanChunk
+    const uint32_t base = threadIdx.x * kScanPer;
+    uint32_t v[kScanPer], s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) { v[i] = (base + i < nb) ? block_sums[base + i] : 0u; s += v[i]; }
+    uint32_t tot;
+    uint32_t ex = block_exclusive_scan(s, &tot);
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        if (base + i < nb) block_sums[base + i] = ex;
+        ex += v[i];
+    }
+    if (threadIdx.x == 0) *total_out = tot;
+}
+
+__global__ void k_scan_add(uint32_t *out, const uint32_t *__restrict__ block_sums, size_t n, const uint32_t *total,
+                           uint32_t *out_total) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += block_sums[i / kScanChunk];
+    if (i == 0) *out_total = *total;
+}
+
+// --------------------------------------------------------------------------
+// Result helpers.
+// --------------------------------------------------------------------------
+__global__ void k_popcount(const uint64_t *__restrict__ p, size_t nwords, unsigned long long *out) {
+    unsigned long long s = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += (size_t)gridDim.x * blockDim.x)
+        s += (unsigned long long)__popcll(p[i]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_down_sync(FULLMASK, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+// Copy rows of several blocks into a dense staging buffer:
+// job k copies row rows[k] of block ptrs[k] (W words) to out + k * W.
+__global__ void k_copy_rows(const uint64_t *const *__restrict__ ptrs, const uint32_t *__restrict__ rows, uint32_t njobs,
+                            uint32_t W, uint64_t *out) {
+    for (uint32_t k = blockIdx.x; k < njobs; k += gridDim.x) {
+        const uint64_t *p = ptrs[k];
+        for (uint32_t w = threadIdx.x; w < W; w += blockDim.x) out[(size_t)k * W + w] = p ? p[(size_t)rows[k] * W + w] : 0ull;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------
+int vpl_for_words(uint32_t W) {
+    if (W <= 64) return 1;
+    if (W <= 128) return 2;
+    if (W <= 256) return 4;
+    if (W <= 512) return 8;
+    if (W <= 1024) return 16;
+    return 0;
+}
+
+cudaError_t launch_gather(int vpl, const GItem *items, uint32_t n_items, const SrcDesc *srcs, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    switch (vpl) {
+        case 1: k_gather<1><<<n_items, 256, 0, st>>>(items, srcs); break;
+        case 2: k_gather<2><<<n_items, 256, 0, st>>>(items, srcs); break;
+        case 4: k_gather<4><<<n_items, 256, 0, st>>>(items, srcs); break;
+        case 8: k_gather<8><<<n_items, 256, 0, st>>>(items, srcs); break;
+        case 16: k_gather<16><<<n_items, 256, 0, st>>>(items, srcs); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract(int vpl, const XItem *items, uint32_t n_items, const FDesc *fds, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    switch (vpl) {
+        case 1: k_extract<1><<<n_items, 256, 0, st>>>(items, fds); break;
+        case 2: k_extract<2><<<n_items, 256, 0, st>>>(items, fds); break;
+        case 4: k_extract<4><<<n_items, 256, 0, st>>>(items, fds); break;
+        case 8: k_extract<8><<<n_items, 256, 0, st>>>(items, fds); break;
+        case 16: k_extract<16><<<n_items, 256, 0, st>>>(items, fds); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_control(QCtl *ctls, uint32_t nq, cudaGraphConditionalHandle h, int use_handle, int *running_out,
+                           cudaStream_t st) {
+    k_control<<<1, 256, 0, st>>>(ctls, nq, h, use_handle, running_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ctl_reset(QCtl *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes,
+                             cudaStream_t st) {
+    k_ctl_reset<<<(nq + 255) / 256, 256, 0, st>>>(ctls, nq, max_iter, max_rounds, max_passes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eps_init(const void *eds, uint32_t ned, uint32_t grid, cudaStream_t st) {
+    if (ned == 0) return cudaSuccess;
+    k_eps_init<<<grid, 256, 0, st>>>(static_cast<const EpsDesc *>(eds), ned);
+    return cudaGetLastError();
+}
+
+size_t eps_desc_size() { return sizeof(EpsDesc); }
+void fill_eps_desc(void *dst, uint64_t *m2, uint64_t *a2, uint32_t *a2_it, uint32_t *box_new_it, QCtl *ctl, uint32_t n,
+                   uint32_t W) {
+    EpsDesc d{m2, a2, a2_it, box_new_it, ctl, n, W};
+    memcpy(dst, &d, sizeof(d));
+}
+
+static uint32_t grid_for(size_t work, uint32_t threads, uint32_t cap = 4096) {
+    size_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (uint32_t)g;
+}
+
+// Exclusive scan with total: out has n+1 entries.  tmp needs
+// ceil(n / kScanChunk) + 1 words.
+cudaError_t scan_exclusive(const uint32_t *in, uint32_t *out, size_t n, uint32_t *tmp, cudaStream_t st) {
+    const size_t nb = (n + kScanChunk - 1) / kScanChunk;
+    if (nb > (size_t)kScanChunk) return cudaErrorInvalidValue;
+    if (n == 0) return cudaMemsetAsync(out, 0, sizeof(uint32_t), st);
+    k_scan_local<<<(uint32_t)nb, kScanThreads, 0, st>>>(in, out, tmp, n);
+    k_scan_sums<<<1, kScanThreads, 0, st>>>(tmp, (uint32_t)nb, tmp + nb);
+    k_scan_add<<<(uint32_t)((n + 255) / 256), 256, 0, st>>>(out, tmp, n, tmp + nb, out + n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage_count(const uint32_t *src, const uint32_t *lbl, const uint32_t *dst, size_t m, uint32_t n,
+                               uint32_t n_term, const int32_t *label_map, uint32_t *cnt, int *err, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_stage_count<<<grid_for(m, 256), 256, 0, st>>>(src, lbl, dst, m, n, n_term, label_map, cnt, err);
+    return cudaGetLastError();
+}
+cudaError_t launch_stage_fill(const uint32_t *src, const uint32_t *lbl, const uint32_t *dst, size_t m, uint32_t n,
+                              uint32_t n_term, const int32_t *label_map, const uint32_t *off, uint32_t *fill,
+                              uint32_t *col, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_stage_fill<<<grid_for(m, 256), 256, 0, st>>>(src, lbl, dst, m, n, n_term, label_map, off, fill, col);
+    return cudaGetLastError();
+}
+cudaError_t launch_stage_unique(const uint32_t *off, uint32_t *col, uint32_t *ucnt, size_t rows, cudaStream_t st) {
+    if (rows == 0) return cudaSuccess;
+    k_stage_unique<<<grid_for(rows, 128), 128, 0, st>>>(off, col, ucnt, rows);
+    return cudaGetLastError();
+}
+cudaError_t launch_stage_compact(const uint32_t *off, const uint32_t *col, const uint32_t *uoff, uint32_t *ucol,
+                                 size_t rows, cudaStream_t st) {
+    if (rows == 0) return cudaSuccess;
+    k_stage_compact<<<grid_for(rows, 128), 128, 0, st>>>(off, col, uoff, ucol, rows);
+    return cudaGetLastError();
+}
+cudaError_t launch_popcount(const uint64_t *p, size_t nwords, unsigned long long *out, cudaStream_t st) {
+    if (nwords == 0) return cudaSuccess;
+    k_popcount<<<grid_for(nwords, 256, 2048), 256, 0, st>>>(p, nwords, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_copy_rows(const uint64_t *const *ptrs, const uint32_t *rows, uint32_t njobs, uint32_t W,
+                             uint64_t *out, cudaStream_t st) {
+    if (njobs == 0) return cudaSuccess;
+    k_copy_rows<<<njobs < 4096 ? njobs : 4096, 128, 0, st>>>(ptrs, rows, njobs, W, out);
+    return cudaGetLastError();
+}
+
+}  // namespace cfpq

@@ -1,0 +1,49 @@
+"""The C-ABI library builds for sm_103a and exports every declared symbol.
+No compute call is made here (no GPU is needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2103_14688_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        names += re.findall(r"^\s*(?:int|const char \*)\s*(cfpq_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ["cfpq_create", "cfpq_destroy", "cfpq_load_graph", "cfpq_load_rsm", "cfpq_run",
+                 "cfpq_get_reachable", "cfpq_extract_paths", "cfpq_status_string"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(B.build())
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu():
+    lib = ctypes.CDLL(B.build())
+    lib.cfpq_status_string.restype = ctypes.c_char_p
+    assert lib.cfpq_status_string(0) == b"ok"
+    assert lib.cfpq_status_string(-4).startswith(b"iteration")
+    assert lib.cfpq_status_string(12345) == b"unknown status"
+
+
+def test_binding_names_match_the_header():
+    from paper_2103_14688_gb300 import cfpq
+    src = open(cfpq.__file__).read()
+    for n in _declared():
+        assert f'"{n}"' in src, n
