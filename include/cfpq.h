@@ -75,6 +75,8 @@ typedef struct {
     uint32_t max_rounds;     /* closure passes per iteration cap; 0 = no cap */
     uint32_t closure_mode;   /* CFPQ_CLOSURE_* */
     uint32_t loop_mode;      /* CFPQ_LOOP_* */
+    uint32_t profile;        /* 1 = time every closure-pass launch with CUDA events on the
+                                context's stream (needs CFPQ_LOOP_HOST); see cfpq_run_stats */
     size_t memory_budget;    /* bytes of device memory a context may hold; 0 = no limit */
     cfpq_alloc_fn alloc;     /* NULL = cudaMallocAsync */
     cfpq_free_fn free;
@@ -114,10 +116,15 @@ typedef struct {
     uint64_t closure_bits;     /* nnz(C3) at the fixpoint (counted on request, else 0) */
     uint64_t m3_bits;          /* nnz(M3) at the fixpoint (counted on request, else 0) */
     uint64_t row_ors;          /* bit-packed source-row ORs issued by the closure */
+    uint64_t rows_changed;     /* output rows of C3 changed, summed over passes */
+    uint64_t row_bytes;        /* bytes of one bit-packed row (n rounded up to 128 bits, / 8) */
     uint64_t tile_mmas;        /* dense tensor-core tile products issued */
     uint64_t closure_blocks;   /* n x n state blocks of C3 held on the device */
     uint64_t device_bytes;     /* device memory held by the query */
     double ms_total;           /* wall time of the call (host clock) */
+    double ms_closure;         /* summed CUDA-event time of the closure-pass launches (profile = 1) */
+    uint32_t closure_launches; /* closure-pass launches timed (profile = 1) */
+    uint32_t pad_;
 } cfpq_run_stats;
 
 /* ---- context ---------------------------------------------------------------- */

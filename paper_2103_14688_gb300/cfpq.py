@@ -43,7 +43,7 @@ cfpq_free_fn = CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
 class cfpq_options(Structure):
     _fields_ = [("struct_size", c_uint32), ("device", c_int32), ("max_iterations", c_uint32),
                 ("max_rounds", c_uint32), ("closure_mode", c_uint32), ("loop_mode", c_uint32),
-                ("memory_budget", c_size_t), ("alloc", cfpq_alloc_fn), ("free", cfpq_free_fn),
+                ("profile", c_uint32), ("memory_budget", c_size_t), ("alloc", cfpq_alloc_fn), ("free", cfpq_free_fn),
                 ("alloc_user", c_void_p)]
 
 
@@ -57,8 +57,10 @@ class cfpq_rsm(Structure):
 class cfpq_run_stats(Structure):
     _fields_ = [("iterations", c_uint32), ("rounds", c_uint32), ("status", c_uint32), ("gpu_launches", c_uint32),
                 ("edges_added", c_uint64), ("closure_bits", c_uint64), ("m3_bits", c_uint64),
-                ("row_ors", c_uint64), ("tile_mmas", c_uint64), ("closure_blocks", c_uint64),
-                ("device_bytes", c_uint64), ("ms_total", c_double)]
+                ("row_ors", c_uint64), ("rows_changed", c_uint64), ("row_bytes", c_uint64),
+                ("tile_mmas", c_uint64), ("closure_blocks", c_uint64),
+                ("device_bytes", c_uint64), ("ms_total", c_double), ("ms_closure", c_double),
+                ("closure_launches", c_uint32), ("pad_", c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

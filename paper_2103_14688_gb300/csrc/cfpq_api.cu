@@ -78,6 +78,8 @@ uint32_t pass_cap(const cfpq_options &o) { return kDefaultPassCap; }
 
 void fill_stats(cfpq_run_stats *s, const QCtl &c, const QueryDev &q, double ms) {
     memset(s, 0, sizeof(*s));
+    s->rows_changed = c.rows_changed_total;
+    s->row_bytes = (uint64_t)q.W * 8;
     s->iterations = c.iters_done;
     s->rounds = (uint32_t)c.rounds_total;
     s->status = c.status == kStatusOk ? 0 : (uint32_t)(-CFPQ_ERR_TIMEOUT);
@@ -92,7 +94,8 @@ void fill_stats(cfpq_run_stats *s, const QCtl &c, const QueryDev &q, double ms) 
 int status_of(const QCtl &c) { return c.status == kStatusOk ? CFPQ_OK : CFPQ_ERR_TIMEOUT; }
 
 // Run the executor's queries to their fixpoint.
-int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t *launches) {
+int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t *launches,
+                 double *ms_closure = nullptr, uint32_t *closure_launches = nullptr) {
     const cudaStream_t st = ctx->stream;
     const uint32_t mi = ctx->opt.max_iterations, mr = ctx->opt.max_rounds, mp = pass_cap(ctx->opt);
     uint32_t n_gather = 0, n_extract = 0;
@@ -105,12 +108,33 @@ int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t 
         if (ex.enqueue_prologue(st, mi, mr, mp)) return fail(ctx, CFPQ_ERR_CUDA, "prologue launch failed");
         int running = 1;
         uint32_t passes = 0;
+        const bool prof = ctx->opt.profile != 0;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (prof) {
+            CK(ctx, cudaEventCreate(&e0));
+            CK(ctx, cudaEventCreate(&e1));
+        }
+        double tot = 0.0;
         while (running) {
-            if (ex.enqueue_pass(st, 0, 0, ex.running.as<int>()))
+            if (ex.enqueue_pass(st, 0, 0, ex.running.as<int>(), e0, e1)) {
+                if (e0) cudaEventDestroy(e0);
+                if (e1) cudaEventDestroy(e1);
                 return fail(ctx, CFPQ_ERR_CUDA, "pass launch failed");
+            }
             CK(ctx, cudaMemcpyAsync(&running, ex.running.p, sizeof(int), cudaMemcpyDeviceToHost, st));
             CK(ctx, cudaStreamSynchronize(st));
+            if (prof) {
+                float ms = 0.f;
+                CK(ctx, cudaEventElapsedTime(&ms, e0, e1));
+                tot += ms;
+            }
             ++passes;
+        }
+        if (prof) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (ms_closure) *ms_closure = tot;
+            if (closure_launches) *closure_launches = passes * n_gather;
         }
         if (launches) *launches = passes * per_pass + 2;
     } else {
@@ -198,6 +222,7 @@ int cfpq_create(cfpq_ctx **out, const cfpq_options *opt, void *stream) {
         cfpq_default_options(&c->opt);
     }
     if (c->opt.loop_mode > CFPQ_LOOP_HOST || c->opt.closure_mode > CFPQ_CLOSURE_TC_I8) return CFPQ_ERR_INVALID_ARG;
+    if (c->opt.profile && c->opt.loop_mode != CFPQ_LOOP_HOST) return CFPQ_ERR_INVALID_ARG;
     if ((c->opt.alloc == nullptr) != (c->opt.free == nullptr)) return CFPQ_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || c->opt.device < 0 || c->opt.device >= ndev) {
@@ -279,13 +304,16 @@ int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats) {
     if (int rc = set_device(ctx)) return rc;
     if (int rc = ensure_query(ctx)) return rc;
     std::vector<QCtl> ctls;
-    uint32_t launches = 0;
-    if (int rc = run_executor(ctx, ctx->exec, &ctls, &launches)) return rc;
+    uint32_t launches = 0, claunch = 0;
+    double ms_cl = 0.0;
+    if (int rc = run_executor(ctx, ctx->exec, &ctls, &launches, &ms_cl, &claunch)) return rc;
     ctx->has_result = true;
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (stats) {
         fill_stats(stats, ctls[0], ctx->query, ms);
         stats->gpu_launches = launches;
+        stats->ms_closure = ms_cl;
+        stats->closure_launches = claunch;
     }
     const int st = status_of(ctls[0]);
     if (st) return fail(ctx, st, "iteration, round or pass cap reached before the fixpoint");

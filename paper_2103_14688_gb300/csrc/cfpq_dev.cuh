@@ -48,6 +48,7 @@ struct QCtl {
     unsigned long long row_ors;       // source rows ORed (all passes)
     unsigned long long tile_mmas;     // dense tiles multiplied (all passes)
     unsigned long long rounds_total;
+    unsigned long long rows_changed_total;  // summed over passes
 };
 
 // One source of an output block C[s,t]: a transition s -l-> u with t = u or

@@ -398,10 +398,13 @@ int Executor::enqueue_prologue(cudaStream_t st, uint32_t max_iter, uint32_t max_
     return CFPQ_OK;
 }
 
-int Executor::enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int use_handle, int *running_out) {
+int Executor::enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int use_handle, int *running_out,
+                           cudaEvent_t ev_before, cudaEvent_t ev_after) {
     std::string *err = nullptr;
+    if (ev_before) ENG_CK(cudaEventRecord(ev_before, st));
     for (int v = 0; v < 5; ++v)
         ENG_CK(launch_gather(kVplOf[v], items[v].as<GItem>(), n_items[v], srcs.as<SrcDesc>(), st));
+    if (ev_after) ENG_CK(cudaEventRecord(ev_after, st));
     for (int v = 0; v < 5; ++v)
         ENG_CK(launch_extract(kVplOf[v], xitems[v].as<XItem>(), n_xitems[v], fds.as<FDesc>(), st));
     ENG_CK(launch_control(ctls.as<QCtl>(), (uint32_t)qs.size(), h, use_handle, running_out, st));

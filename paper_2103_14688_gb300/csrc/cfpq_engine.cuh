@@ -148,7 +148,8 @@ struct Executor {
     }
     int assemble(Allocator *A, cudaStream_t st, std::string *err);
     int enqueue_prologue(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes);
-    int enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int use_handle, int *running_out);
+    int enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int use_handle, int *running_out,
+                     cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);
     int build_graph(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes, std::string *err);
     int read_ctls(cudaStream_t st, std::vector<QCtl> *out);
 };

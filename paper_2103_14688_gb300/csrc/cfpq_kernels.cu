@@ -295,6 +295,7 @@ __global__ void k_control(QCtl *ctls, uint32_t nq, cudaGraphConditionalHandle ha
         if (c.phase != kPhaseRun) continue;
         c.passes += 1;
         c.rounds_total += 1;
+        c.rows_changed_total += c.changed_rows;
         if (c.changed_rows == 0ull) {
             c.iters_done = c.iter;
             c.edges_total += c.new_edges;
