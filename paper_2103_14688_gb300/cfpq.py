@@ -364,3 +364,78 @@ class Context:
         self._check(self.lib.cfpq_batch_get_reachable_bits(self.h, q, box, c_void_p(out.ctypes.data)),
                     "cfpq_batch_get_reachable_bits")
         return np.unpackbits(out.reshape(n, wn).view(np.uint8), axis=1, bitorder="little")[:, :n].astype(bool)
+
+
+class Server:
+    """A cfpq_server: resident graph, continuously batched RSM queries."""
+
+    def __init__(self, g, device: int = 0, use_torch: bool = True, stream=None, **options):
+        self.lib = load()
+        self._alloc = None
+        o = default_options(device=device, **options)
+        if use_torch:
+            import torch
+            torch.cuda.init()
+            self._alloc = _TorchAllocator(device)
+            o.alloc = self._alloc.alloc
+            o.free = self._alloc.free
+            if stream is None:
+                with torch.cuda.device(device):
+                    stream = torch.cuda.current_stream().cuda_stream
+        s, l, d = _u32(g.src), _u32(g.lbl), _u32(g.dst)
+        h = c_void_p()
+        rc = self.lib.cfpq_server_create(ctypes.byref(h), ctypes.byref(o), c_void_p(stream or 0), g.n, g.n_terminals,
+                                         len(s), _u32p(s), _u32p(l), _u32p(d))
+        if rc != CFPQ_OK:
+            raise CfpqError(rc, "cfpq_server_create: " + status_string(rc))
+        self.h = h
+        self.n = g.n
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cfpq_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, r) -> int:
+        ra = RSMArgs(r)
+        t = c_uint64()
+        rc = self.lib.cfpq_submit(self.h, ctypes.byref(ra.c), ctypes.byref(t))
+        if rc != CFPQ_OK:
+            raise CfpqError(rc, "cfpq_submit: " + status_string(rc))
+        self._keep[t.value] = (ra, r.n_boxes)
+        return t.value
+
+    def step(self) -> Tuple[int, int]:
+        a, b = c_uint32(), c_uint32()
+        rc = self.lib.cfpq_server_step(self.h, ctypes.byref(a), ctypes.byref(b))
+        if rc != CFPQ_OK:
+            raise CfpqError(rc, "cfpq_server_step: " + status_string(rc))
+        return a.value, b.value
+
+    def poll(self, ticket: int) -> bool:
+        d = c_int()
+        rc = self.lib.cfpq_poll(self.h, ticket, ctypes.byref(d))
+        if rc != CFPQ_OK:
+            raise CfpqError(rc, "cfpq_poll: " + status_string(rc))
+        return bool(d.value)
+
+    def result_bits(self, ticket: int, box: int = 0) -> np.ndarray:
+        wn = (self.n + 63) // 64
+        out = np.zeros(self.n * wn, dtype=np.uint64)
+        rc = self.lib.cfpq_result_reachable_bits(self.h, ticket, box, c_void_p(out.ctypes.data))
+        if rc != CFPQ_OK:
+            raise CfpqError(rc, "cfpq_result_reachable_bits: " + status_string(rc))
+        return np.unpackbits(out.reshape(self.n, wn).view(np.uint8), axis=1, bitorder="little")[:, : self.n].astype(bool)
+
+    def release(self, ticket: int):
+        rc = self.lib.cfpq_release(self.h, ticket)
+        if rc != CFPQ_OK:
+            raise CfpqError(rc, "cfpq_release: " + status_string(rc))
+        self._keep.pop(ticket, None)

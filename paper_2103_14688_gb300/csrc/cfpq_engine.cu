@@ -184,13 +184,12 @@ static uint32_t next_pow2(uint32_t x) {
     return p;
 }
 
-int QueryDev::prepare(Allocator *A, std::string *err) {
+int QueryDev::plan(std::string *err) {
     if (!g || g->n == 0) { *err = "no graph loaded"; return CFPQ_ERR_STATE; }
     if (rsm.max_terminal_plus1 > g->n_term) {
         *err = "the RSM reads a terminal >= the graph's n_terminals";
         return CFPQ_ERR_INVALID_ARG;
     }
-    const bool same = prepared && n == g->n && W == g->W && Q == rsm.Q && B == rsm.B;
     n = g->n;
     W = g->W;
     Q = rsm.Q;
@@ -245,19 +244,61 @@ int QueryDev::prepare(Allocator *A, std::string *err) {
                 fblocks.push_back((uint32_t)blk_of[(size_t)q0 * Q + f]);
         box_nf[b] = (uint32_t)fblocks.size() - box_f0[b];
     }
+    n_eps = 0;
+    for (uint32_t b = 0; b < B; ++b) n_eps += rsm.final_[rsm.box_start[b]] ? 1u : 0u;
+    return CFPQ_OK;
+}
+
+uint64_t QueryDev::footprint() const {
+    const uint64_t nblk = std::max<uint64_t>(blocks.size(), 1), bw = (uint64_t)n * W * 8;
+    return nblk * bw + nblk * n * 4 + nblk * 4 + 2ull * B * bw + (uint64_t)B * n * 4 + B * 4 + 4096;
+}
+
+int QueryDev::prepare(Allocator *A, std::string *err) {
+    int rc = plan(err);
+    if (rc) return rc;
     const size_t nblk = blocks.size();
     const size_t bw = (size_t)n * W * 8;
     if (!blk_mem.ensure(A, std::max<size_t>(nblk, 1) * bw, err) ||
         !stamp_mem.ensure(A, std::max<size_t>(nblk, 1) * n * 4, err) ||
         !last_mem.ensure(A, std::max<size_t>(nblk, 1) * 4, err) || !m2_mem.ensure(A, (size_t)B * bw, err) ||
         !a2_mem.ensure(A, (size_t)B * bw, err) || !a2it_mem.ensure(A, (size_t)B * n * 4, err) ||
-        !boxit_mem.ensure(A, (size_t)B * 4, err))
+        !boxit_mem.ensure(A, (size_t)B * 4, err) || !ctl_mem.ensure(A, sizeof(QCtl), err) ||
+        !ctl_ptr_mem.ensure(A, sizeof(QCtl *), err) ||
+        !eps_mem.ensure(A, std::max<size_t>(n_eps, 1) * eps_desc_size(), err))
         return CFPQ_ERR_OUT_OF_MEMORY;
     device_bytes = blk_mem.bytes + stamp_mem.bytes + last_mem.bytes + m2_mem.bytes + a2_mem.bytes + a2it_mem.bytes +
                    boxit_mem.bytes;
-    (void)same;
+    std::vector<unsigned char> he(std::max<size_t>(n_eps, 1) * eps_desc_size());
+    uint32_t k = 0;
+    for (uint32_t b = 0; b < B; ++b) {
+        if (!rsm.final_[rsm.box_start[b]]) continue;
+        fill_eps_desc(he.data() + (size_t)k * eps_desc_size(), m2_ptr(b), a2_ptr(b),
+                      a2it_mem.as<uint32_t>() + (size_t)b * n, boxit_mem.as<uint32_t>() + b, ctl(), n, W);
+        ++k;
+    }
+    QCtl *cp = ctl();
+    ENG_CK(cudaMemcpyAsync(eps_mem.p, he.data(), he.size(), cudaMemcpyHostToDevice, A->stream));
+    ENG_CK(cudaMemcpyAsync(ctl_ptr_mem.p, &cp, sizeof(cp), cudaMemcpyHostToDevice, A->stream));
+    ENG_CK(cudaStreamSynchronize(A->stream));
     prepared = true;
     graph_generation = g->generation;
+    return CFPQ_OK;
+}
+
+int QueryDev::enqueue_init(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes) {
+    std::string *err = nullptr;
+    const size_t nblk = blocks.size();
+    if (nblk) {
+        ENG_CK(cudaMemsetAsync(blk_mem.p, 0, nblk * (size_t)n * W * 8, st));
+        ENG_CK(cudaMemsetAsync(stamp_mem.p, 0, nblk * (size_t)n * 4, st));
+        ENG_CK(cudaMemsetAsync(last_mem.p, 0, nblk * 4, st));
+    }
+    ENG_CK(cudaMemsetAsync(m2_mem.p, 0, (size_t)B * n * W * 8, st));
+    ENG_CK(cudaMemsetAsync(a2it_mem.p, 0, (size_t)B * n * 4, st));
+    ENG_CK(cudaMemsetAsync(boxit_mem.p, 0, (size_t)B * 4, st));
+    ENG_CK(launch_ctl_reset(ctl_ptr_mem.as<QCtl *>(), 1, max_iter, max_rounds, max_passes, st));
+    ENG_CK(launch_eps_init(eps_mem.p, n_eps, 152, st));
     return CFPQ_OK;
 }
 
@@ -277,20 +318,19 @@ static const int kVplOf[5] = {1, 2, 4, 8, 16};
 
 int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     const uint32_t nq = (uint32_t)qs.size();
-    if (!ctls.ensure(A, std::max<uint32_t>(nq, 1) * sizeof(QCtl), err) || !running.ensure(A, 16, err))
+    if (!ctl_ptrs.ensure(A, std::max<uint32_t>(nq, 1) * sizeof(QCtl *), err) ||
+        !mirror.ensure(A, std::max<uint32_t>(nq, 1) * sizeof(QCtl), err) || !running.ensure(A, 16, err))
         return CFPQ_ERR_OUT_OF_MEMORY;
-    QCtl *dctl = ctls.as<QCtl>();
+    std::vector<QCtl *> hp;
     std::vector<SrcDesc> hs;
     std::vector<GItem> hi[5];
     std::vector<FDesc> hf;
     std::vector<XItem> hx[5];
-    std::vector<unsigned char> he;
-    const size_t esz = eps_desc_size();
-    n_eds = 0;
     for (uint32_t qi = 0; qi < nq; ++qi) {
         QueryDev &q = *qs[qi];
         const GraphDev &g = *q.g;
-        QCtl *cp = dctl + qi;
+        QCtl *cp = q.ctl();
+        hp.push_back(cp);
         const uint32_t base = (uint32_t)hs.size();
         for (const auto &s : q.srcs) {
             SrcDesc d;
@@ -353,13 +393,6 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                 hx[vi].push_back(x);
             }
         }
-        for (uint32_t b = 0; b < q.B; ++b) {
-            if (!q.rsm.final_[q.rsm.box_start[b]]) continue;
-            he.resize(he.size() + esz);
-            fill_eps_desc(he.data() + he.size() - esz, q.m2_ptr(b), q.a2_ptr(b),
-                          q.a2it_mem.as<uint32_t>() + (size_t)b * q.n, q.boxit_mem.as<uint32_t>() + b, cp, q.n, q.W);
-            ++n_eds;
-        }
     }
     auto upload = [&](DBuf &buf, const void *h, size_t bytes) -> int {
         if (!buf.ensure(A, std::max<size_t>(bytes, 64), err)) return CFPQ_ERR_OUT_OF_MEMORY;
@@ -367,9 +400,9 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
         return CFPQ_OK;
     };
     int rc;
+    if ((rc = upload(ctl_ptrs, hp.data(), hp.size() * sizeof(QCtl *)))) return rc;
     if ((rc = upload(srcs, hs.data(), hs.size() * sizeof(SrcDesc)))) return rc;
     if ((rc = upload(fds, hf.data(), hf.size() * sizeof(FDesc)))) return rc;
-    if ((rc = upload(eds, he.data(), he.size()))) return rc;
     for (int v = 0; v < 5; ++v) {
         n_items[v] = (uint32_t)hi[v].size();
         n_xitems[v] = (uint32_t)hx[v].size();
@@ -383,18 +416,8 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
 }
 
 int Executor::enqueue_prologue(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes) {
-    std::string *err = nullptr;
-    for (QueryDev *q : qs) {
-        const size_t nblk = q->blocks.size();
-        ENG_CK(cudaMemsetAsync(q->blk_mem.p, 0, nblk * (size_t)q->n * q->W * 8, st));
-        ENG_CK(cudaMemsetAsync(q->stamp_mem.p, 0, nblk * (size_t)q->n * 4, st));
-        ENG_CK(cudaMemsetAsync(q->last_mem.p, 0, std::max<size_t>(nblk, 1) * 4, st));
-        ENG_CK(cudaMemsetAsync(q->m2_mem.p, 0, (size_t)q->B * q->n * q->W * 8, st));
-        ENG_CK(cudaMemsetAsync(q->a2it_mem.p, 0, (size_t)q->B * q->n * 4, st));
-        ENG_CK(cudaMemsetAsync(q->boxit_mem.p, 0, (size_t)q->B * 4, st));
-    }
-    ENG_CK(launch_ctl_reset(ctls.as<QCtl>(), (uint32_t)qs.size(), max_iter, max_rounds, max_passes, st));
-    ENG_CK(launch_eps_init(eds.p, n_eds, 152, st));
+    for (QueryDev *q : qs)
+        if (int rc = q->enqueue_init(st, max_iter, max_rounds, max_passes)) return rc;
     return CFPQ_OK;
 }
 
@@ -407,7 +430,8 @@ int Executor::enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int us
     if (ev_after) ENG_CK(cudaEventRecord(ev_after, st));
     for (int v = 0; v < 5; ++v)
         ENG_CK(launch_extract(kVplOf[v], xitems[v].as<XItem>(), n_xitems[v], fds.as<FDesc>(), st));
-    ENG_CK(launch_control(ctls.as<QCtl>(), (uint32_t)qs.size(), h, use_handle, running_out, st));
+    ENG_CK(launch_control(ctl_ptrs.as<QCtl *>(), (uint32_t)qs.size(), mirror.as<QCtl>(), h, use_handle, running_out,
+                          st));
     return CFPQ_OK;
 }
 
@@ -461,7 +485,7 @@ int Executor::read_ctls(cudaStream_t st, std::vector<QCtl> *out) {
     std::string *err = nullptr;
     out->resize(qs.size());
     if (qs.empty()) return CFPQ_OK;
-    ENG_CK(cudaMemcpyAsync(out->data(), ctls.p, qs.size() * sizeof(QCtl), cudaMemcpyDeviceToHost, st));
+    ENG_CK(cudaMemcpyAsync(out->data(), mirror.p, qs.size() * sizeof(QCtl), cudaMemcpyDeviceToHost, st));
     ENG_CK(cudaStreamSynchronize(st));
     return CFPQ_OK;
 }

@@ -15,10 +15,10 @@ namespace cfpq {
 int vpl_for_words(uint32_t W);
 cudaError_t launch_gather(int vpl, const GItem *items, uint32_t n_items, const SrcDesc *srcs, cudaStream_t st);
 cudaError_t launch_extract(int vpl, const XItem *items, uint32_t n_items, const FDesc *fds, cudaStream_t st);
-cudaError_t launch_control(QCtl *ctls, uint32_t nq, cudaGraphConditionalHandle h, int use_handle, int *running_out,
-                           cudaStream_t st);
-cudaError_t launch_ctl_reset(QCtl *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes,
-                             cudaStream_t st);
+cudaError_t launch_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGraphConditionalHandle h, int use_handle,
+                           int *running_out, cudaStream_t st);
+cudaError_t launch_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds,
+                             uint32_t max_passes, cudaStream_t st);
 cudaError_t launch_eps_init(const void *eds, uint32_t ned, uint32_t grid, cudaStream_t st);
 size_t eps_desc_size();
 void fill_eps_desc(void *dst, uint64_t *m2, uint64_t *a2, uint32_t *a2_it, uint32_t *box_new_it, QCtl *ctl, uint32_t n,
@@ -109,7 +109,8 @@ struct QueryDev {
     uint32_t n = 0, W = 0, Q = 0, B = 0, vpl = 0, lpr = 0;
     std::vector<int32_t> blk_of;  // Q*Q -> block or -1
     std::vector<std::pair<uint32_t, uint32_t>> blocks;
-    DBuf blk_mem, stamp_mem, last_mem, m2_mem, a2_mem, a2it_mem, boxit_mem;
+    DBuf blk_mem, stamp_mem, last_mem, m2_mem, a2_mem, a2it_mem, boxit_mem, ctl_mem, eps_mem, ctl_ptr_mem;
+    uint32_t n_eps = 0;
     uint64_t device_bytes = 0;
     // host descriptors (pointers filled once buffers exist; ctl set by the executor)
     struct Src { uint32_t label_kind, label, ident; int32_t rblk; };
@@ -119,7 +120,12 @@ struct QueryDev {
     std::vector<uint32_t> fblocks;  // per box list of block ids (q0, f)
     bool prepared = false;
     uint64_t graph_generation = 0;
+    int plan(std::string *err);                    // blocks, sources, extraction lists (host only)
+    uint64_t footprint() const;                    // device bytes prepare() will hold
     int prepare(Allocator *A, std::string *err);  // plan + buffers
+    // Reset this query's device state and loop control (start of its fixpoint).
+    int enqueue_init(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes);
+    QCtl *ctl() const { return ctl_mem.as<QCtl>(); }
     uint64_t *blk_ptr(uint32_t b) const { return blk_mem.as<uint64_t>() + (size_t)b * n * W; }
     uint32_t *stamp_ptr(uint32_t b) const { return stamp_mem.as<uint32_t>() + (size_t)b * n; }
     uint64_t *m2_ptr(uint32_t b) const { return m2_mem.as<uint64_t>() + (size_t)b * n * W; }
@@ -129,9 +135,8 @@ struct QueryDev {
 // Runs the fixpoint of a set of queries with shared launches.
 struct Executor {
     std::vector<QueryDev *> qs;
-    DBuf ctls, items[5], xitems[5], srcs, fds, eds, running;
+    DBuf ctl_ptrs, mirror, items[5], xitems[5], srcs, fds, running;
     uint32_t n_items[5] = {0, 0, 0, 0, 0}, n_xitems[5] = {0, 0, 0, 0, 0};
-    uint32_t n_eds = 0;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream: capture is not allowed on the legacy default stream

@@ -287,12 +287,15 @@ __global__ void __launch_bounds__(256) k_extract(const XItem *__restrict__ items
 // --------------------------------------------------------------------------
 // Loop control: one CTA for all queries.
 // --------------------------------------------------------------------------
-__global__ void k_control(QCtl *ctls, uint32_t nq, cudaGraphConditionalHandle handle, int use_handle,
-                          int *running_out) {
+__global__ void k_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGraphConditionalHandle handle,
+                          int use_handle, int *running_out) {
     int running = 0;
     for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
-        QCtl &c = ctls[q];
-        if (c.phase != kPhaseRun) continue;
+        QCtl &c = *ctls[q];
+        if (c.phase != kPhaseRun) {
+            mirror[q] = c;
+            continue;
+        }
         c.passes += 1;
         c.rounds_total += 1;
         c.rows_changed_total += c.changed_rows;
@@ -327,6 +330,7 @@ __global__ void k_control(QCtl *ctls, uint32_t nq, cudaGraphConditionalHandle ha
         }
         c.changed_rows = 0;
         running |= (c.phase == kPhaseRun);
+        mirror[q] = c;
     }
     running = __syncthreads_or(running);
     if (threadIdx.x == 0) {
@@ -336,7 +340,8 @@ __global__ void k_control(QCtl *ctls, uint32_t nq, cudaGraphConditionalHandle ha
 }
 
 // Reset the loop state of queries [0, nq) (start of a run).
-__global__ void k_ctl_reset(QCtl *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes) {
+__global__ void k_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds,
+                            uint32_t max_passes) {
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
         QCtl c;
         memset(&c, 0, sizeof(c));
@@ -348,7 +353,7 @@ __global__ void k_ctl_reset(QCtl *ctls, uint32_t nq, uint32_t max_iter, uint32_t
         c.max_iter = max_iter;
         c.max_rounds = max_rounds;
         c.max_passes = max_passes;
-        ctls[q] = c;
+        *ctls[q] = c;
     }
 }
 
@@ -567,14 +572,14 @@ cudaError_t launch_extract(int vpl, const XItem *items, uint32_t n_items, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_control(QCtl *ctls, uint32_t nq, cudaGraphConditionalHandle h, int use_handle, int *running_out,
-                           cudaStream_t st) {
-    k_control<<<1, 256, 0, st>>>(ctls, nq, h, use_handle, running_out);
+cudaError_t launch_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGraphConditionalHandle h, int use_handle,
+                           int *running_out, cudaStream_t st) {
+    k_control<<<1, 256, 0, st>>>(ctls, nq, mirror, h, use_handle, running_out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ctl_reset(QCtl *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes,
-                             cudaStream_t st) {
+cudaError_t launch_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds,
+                             uint32_t max_passes, cudaStream_t st) {
     k_ctl_reset<<<(nq + 255) / 256, 256, 0, st>>>(ctls, nq, max_iter, max_rounds, max_passes);
     return cudaGetLastError();
 }
