@@ -18,8 +18,16 @@
 
 namespace cfpq {
 
-constexpr uint32_t kModeNew = 0;   // pass over the new edges of the iteration
-constexpr uint32_t kModeProp = 1;  // pass over dirty rows (all edges)
+// Passes are scheduled by level: the RSM's states are grouped into strongly
+// connected components, a component's level is one more than the highest
+// level among the components it has transitions into, and block C[s,t]
+// takes the level of s.  C[s,t] depends only on blocks C[u,t] of successors
+// u of s, so on lower levels or (inside a cyclic component) its own level.
+// Every iteration processes the levels in increasing order; a level gets one
+// FIRST pass, and a level whose component has a cycle repeats (REPEAT) until
+// a pass changes no row.
+constexpr uint32_t kModeNew = 0;   // FIRST pass of a level
+constexpr uint32_t kModeProp = 1;  // REPEAT pass of a cyclic level
 constexpr uint32_t kPhaseRun = 0;
 constexpr uint32_t kPhaseDone = 1;
 constexpr uint32_t kStatusOk = 0;
@@ -42,6 +50,9 @@ struct QCtl {
     uint32_t max_passes;      // hard cap on passes (safety)
     uint32_t iters_done;      // completed iterations
     uint32_t passes;          // passes done
+    uint32_t level;           // level being processed
+    uint32_t n_levels;        // levels of this query (>= 1)
+    unsigned long long cyclic_mask;   // bit L: level L has a cycle (REPEAT passes)
     unsigned long long changed_rows;  // rows changed by the pass in progress
     unsigned long long new_edges;     // edges added by the extraction in progress
     unsigned long long edges_total;   // edges added so far (epsilon edges included)
@@ -65,7 +76,9 @@ struct SrcDesc {
     const uint32_t *rstamp;    // row stamps of C[u,t]
     const uint32_t *rlast;     // last pass that changed C[u,t]
     uint32_t ident;            // u == t: the product edge itself lands in C[s,t]
+    uint32_t same_level;       // C[u,t] is on the level of C[s,t] (same cyclic component)
     uint32_t dense;            // label matrix handled by dense tiles (not here)
+    uint32_t pad;
 };
 
 // Gather work item: rows [row0, row1) of one output block.
@@ -78,6 +91,8 @@ struct GItem {
     uint32_t row0, row1;
     uint32_t W;    // words per row
     uint32_t lpr;  // lanes per row (power of two <= 32)
+    uint32_t level;
+    uint32_t pad;
 };
 
 // Final-state block used by extraction: C[q0(b), f] with f final in box b.

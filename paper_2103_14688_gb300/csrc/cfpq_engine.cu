@@ -215,6 +215,43 @@ int QueryDev::plan(std::string *err) {
                 blk_of[(size_t)s * Q + t] = (int32_t)blocks.size();
                 blocks.push_back({s, t});
             }
+    // Levels (see cfpq_dev.cuh): strongly connected components of the state
+    // graph, level = 1 + max level of the components a component has
+    // transitions into; levels without blocks are dropped.
+    std::vector<uint32_t> comp(Q);
+    for (uint32_t s = 0; s < Q; ++s) {
+        comp[s] = s;
+        for (uint32_t t = 0; t < s; ++t)
+            if (reach[(size_t)s * Q + t] && reach[(size_t)t * Q + s]) { comp[s] = comp[t]; break; }
+    }
+    std::vector<int32_t> clevel(Q, -1);
+    // components in an order where every successor component comes first:
+    // repeat relaxation (Q is small)
+    bool changed_lv = true;
+    for (uint32_t s = 0; s < Q; ++s) clevel[comp[s]] = 0;
+    while (changed_lv) {
+        changed_lv = false;
+        for (const auto &t : rsm.tr) {
+            const uint32_t a = comp[t.from], b = comp[t.to];
+            if (a == b) continue;
+            if (clevel[a] < clevel[b] + 1) { clevel[a] = clevel[b] + 1; changed_lv = true; }
+        }
+    }
+    std::vector<int32_t> used(Q + 1, 0);
+    for (const auto &bk : blocks) used[clevel[comp[bk.first]]] = 1;
+    std::vector<int32_t> remap(Q + 1, -1);
+    n_levels = 0;
+    for (uint32_t L = 0; L <= Q; ++L)
+        if (used[L]) remap[L] = (int32_t)n_levels++;
+    if (n_levels == 0) n_levels = 1;
+    if (n_levels > 64) { *err = "more than 64 block levels"; return CFPQ_ERR_UNSUPPORTED; }
+    blk_level.assign(blocks.size(), 0);
+    cyclic_mask = 0;
+    for (size_t b = 0; b < blocks.size(); ++b) {
+        const uint32_t s = blocks[b].first;
+        blk_level[b] = (uint32_t)remap[clevel[comp[s]]];
+        if (reach[(size_t)s * Q + s]) cyclic_mask |= 1ull << blk_level[b];
+    }
     // Sources of block (s,t): transitions s -l-> u with u == t or t reachable from u.
     srcs.clear();
     blk_src0.assign(blocks.size(), 0);
@@ -228,7 +265,8 @@ int QueryDev::plan(std::string *err) {
             const bool ident = (u == t);
             const int32_t rb = blk_of[(size_t)u * Q + t];
             if (!ident && rb < 0) continue;
-            srcs.push_back({tr.kind, tr.sym, ident ? 1u : 0u, rb});
+            const uint32_t same = (rb >= 0 && blk_level[(size_t)rb] == blk_level[b]) ? 1u : 0u;
+            srcs.push_back({tr.kind, tr.sym, ident ? 1u : 0u, rb, same});
         }
         blk_nsrc[b] = (uint32_t)srcs.size() - blk_src0[b];
     }
@@ -297,7 +335,7 @@ int QueryDev::enqueue_init(cudaStream_t st, uint32_t max_iter, uint32_t max_roun
     ENG_CK(cudaMemsetAsync(m2_mem.p, 0, (size_t)B * n * W * 8, st));
     ENG_CK(cudaMemsetAsync(a2it_mem.p, 0, (size_t)B * n * 4, st));
     ENG_CK(cudaMemsetAsync(boxit_mem.p, 0, (size_t)B * 4, st));
-    ENG_CK(launch_ctl_reset(ctl_ptr_mem.as<QCtl *>(), 1, max_iter, max_rounds, max_passes, st));
+    ENG_CK(launch_ctl_reset(ctl_ptr_mem.as<QCtl *>(), 1, max_iter, max_rounds, max_passes, n_levels, cyclic_mask, st));
     ENG_CK(launch_eps_init(eps_mem.p, n_eps, 152, st));
     return CFPQ_OK;
 }
@@ -350,6 +388,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                 d.rlast = q.last_mem.as<uint32_t>() + s.rblk;
             }
             d.ident = s.ident;
+            d.same_level = s.same_level;
             d.dense = 0;
             hs.push_back(d);
         }
@@ -370,6 +409,8 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                 it.row1 = std::min(q.n, r0 + rpi);
                 it.W = q.W;
                 it.lpr = q.lpr;
+                it.level = q.blk_level[b];
+                it.pad = 0;
                 hi[vi].push_back(it);
             }
         }

@@ -18,7 +18,7 @@ cudaError_t launch_extract(int vpl, const XItem *items, uint32_t n_items, const 
 cudaError_t launch_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGraphConditionalHandle h, int use_handle,
                            int *running_out, cudaStream_t st);
 cudaError_t launch_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds,
-                             uint32_t max_passes, cudaStream_t st);
+                             uint32_t max_passes, uint32_t n_levels, unsigned long long cyclic_mask, cudaStream_t st);
 cudaError_t launch_eps_init(const void *eds, uint32_t ned, uint32_t grid, cudaStream_t st);
 size_t eps_desc_size();
 void fill_eps_desc(void *dst, uint64_t *m2, uint64_t *a2, uint32_t *a2_it, uint32_t *box_new_it, QCtl *ctl, uint32_t n,
@@ -113,8 +113,11 @@ struct QueryDev {
     uint32_t n_eps = 0;
     uint64_t device_bytes = 0;
     // host descriptors (pointers filled once buffers exist; ctl set by the executor)
-    struct Src { uint32_t label_kind, label, ident; int32_t rblk; };
+    struct Src { uint32_t label_kind, label, ident; int32_t rblk; uint32_t same_level; };
     std::vector<uint32_t> blk_src0, blk_nsrc;  // per block
+    std::vector<uint32_t> blk_level;           // per block, 0..n_levels-1
+    uint32_t n_levels = 1;
+    uint64_t cyclic_mask = 0;
     std::vector<Src> srcs;
     std::vector<uint32_t> box_f0, box_nf;
     std::vector<uint32_t> fblocks;  // per box list of block ids (q0, f)

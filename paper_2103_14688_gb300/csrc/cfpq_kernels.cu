@@ -59,13 +59,25 @@ __device__ __forceinline__ int lowbit4(uint4 &v, bool clear) {
     return -1;
 }
 
-__device__ __forceinline__ bool src_active(const SrcDesc &d, uint32_t mode, uint32_t iter, uint32_t g) {
-    if (d.dense) return false;
+// Which edges of a source take part in this pass (bit mask):
+//   1  new edges of the iteration, whole source rows (FIRST pass): terminal
+//      edges in iteration 1, A2 rows afterwards (left-distributivity);
+//   2  all edges, source rows of a lower level changed in this iteration
+//      (FIRST pass; those levels are final for the iteration);
+//   4  all edges, source rows of this level changed in the previous pass
+//      (REPEAT pass of a cyclic level).
+__device__ __forceinline__ uint32_t src_channels(const SrcDesc &d, uint32_t mode, uint32_t iter, uint32_t g,
+                                                 uint32_t g0) {
+    if (d.dense) return 0u;
+    uint32_t ch = 0u;
     if (mode == kModeNew) {
-        if (d.csr_off) return iter == 1;
-        return *d.box_new_it == iter;
+        const bool term1 = d.csr_off != nullptr && iter == 1;
+        if (term1 || (d.csr_off == nullptr && *d.box_new_it == iter)) ch |= 1u;
+        if (d.rblk && !d.same_level && !term1 && *d.rlast >= g0) ch |= 2u;
+    } else {
+        if (d.rblk && d.same_level && *d.rlast + 1u >= g) ch |= 4u;
     }
-    return d.rblk != nullptr && (*d.rlast + 1u >= g);
+    return ch;
 }
 
 // --------------------------------------------------------------------------
@@ -77,11 +89,12 @@ template <int VPL>
 __global__ void __launch_bounds__(256) k_gather(const GItem *__restrict__ items, const SrcDesc *__restrict__ srcs) {
     const GItem it = items[blockIdx.x];
     const QCtl *c = it.ctl;
-    if (c->phase != kPhaseRun) return;
-    const uint32_t g = c->g, iter = c->iter, mode = c->mode;
+    if (c->phase != kPhaseRun || c->level != it.level) return;
+    const uint32_t g = c->g, iter = c->iter, mode = c->mode, g0 = c->g_iter_start;
 
     int act = 0;
-    for (uint32_t k = threadIdx.x; k < it.nsrc; k += blockDim.x) act |= src_active(srcs[it.src0 + k], mode, iter, g);
+    for (uint32_t k = threadIdx.x; k < it.nsrc; k += blockDim.x)
+        act |= src_channels(srcs[it.src0 + k], mode, iter, g, g0) != 0u;
     if (!__syncthreads_or(act)) return;
 
     __shared__ unsigned long long s_changed, s_ors;
@@ -103,71 +116,76 @@ __global__ void __launch_bounds__(256) k_gather(const GItem *__restrict__ items,
 
         for (uint32_t k = 0; k < it.nsrc; ++k) {
             const SrcDesc d = srcs[it.src0 + k];
-            if (!src_active(d, mode, iter, g)) continue;
-            const bool use_ident = (mode == kModeNew) && d.ident;
-            if (!use_ident && d.rblk == nullptr) continue;
-            const bool check_dirty = (mode == kModeProp);
+            const uint32_t chans = src_channels(d, mode, iter, g, g0);
+            for (uint32_t cbit = 1u; cbit <= 4u; cbit <<= 1) {
+                if (!(chans & cbit)) continue;
+                const bool new_edges = cbit == 1u;
+                const bool use_ident = new_edges && d.ident;
+                if (!use_ident && d.rblk == nullptr) continue;
+                // a source row takes part when its stamp is >= thr
+                const uint32_t thr = new_edges ? 0u : (cbit == 2u ? g0 : g - 1u);
 
-            // OR of source row y of C[u,t] (and the product edge itself).
-            auto take = [&](uint32_t y) {
-                if (use_ident) {
-                    const uint32_t v = y >> 7;
-                    if ((int)(v % lpr) == gl) {
-                        const int j = (int)(v / lpr);
+                // OR of source row y of C[u,t] (and the product edge itself).
+                auto take = [&](uint32_t y) {
+                    if (use_ident) {
+                        const uint32_t v = y >> 7;
+                        if ((int)(v % lpr) == gl) {
+                            const int j = (int)(v / lpr);
 #pragma unroll
-                        for (int jj = 0; jj < VPL; ++jj)
-                            if (jj == j) setbit4(acc[jj], y & 127u);
+                            for (int jj = 0; jj < VPL; ++jj)
+                                if (jj == j) setbit4(acc[jj], y & 127u);
+                        }
                     }
-                }
-                if (d.rblk) {
-                    if (check_dirty && d.rstamp[y] + 1u < g) return;
-                    const uint4 *r = reinterpret_cast<const uint4 *>(d.rblk + (size_t)y * W);
+                    if (d.rblk) {
+                        if (thr && d.rstamp[y] < thr) return;
+                        const uint4 *r = reinterpret_cast<const uint4 *>(d.rblk + (size_t)y * W);
+#pragma unroll
+                        for (int j = 0; j < VPL; ++j) {
+                            const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
+                            if (v < nvec) or4(acc[j], r[v]);
+                        }
+                        if (gl == 0) ++my_ors;
+                    }
+                };
+
+                if (d.csr_off) {
+                    const uint32_t e0 = valid ? d.csr_off[row] : 0u, e1 = valid ? d.csr_off[row + 1] : 0u;
+                    for (uint32_t e = e0; e < e1; ++e) take(d.csr_col[e]);
+                } else {
+                    const uint64_t *adj;
+                    bool rowok;
+                    if (new_edges) { adj = d.nt_new; rowok = valid && d.nt_new_it[row] == iter; }
+                    else { adj = d.nt_all; rowok = valid; }
+                    uint4 a[VPL];
 #pragma unroll
                     for (int j = 0; j < VPL; ++j) {
                         const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
-                        if (v < nvec) or4(acc[j], r[v]);
+                        a[j] = (rowok && v < nvec) ? reinterpret_cast<const uint4 *>(adj + (size_t)row * W)[v]
+                                                   : make_uint4(0, 0, 0, 0);
                     }
-                    if (gl == 0) ++my_ors;
-                }
-            };
-
-            if (d.csr_off) {
-                const uint32_t e0 = valid ? d.csr_off[row] : 0u, e1 = valid ? d.csr_off[row + 1] : 0u;
-                for (uint32_t e = e0; e < e1; ++e) take(d.csr_col[e]);
-            } else {
-                const uint64_t *adj;
-                bool rowok;
-                if (mode == kModeNew) { adj = d.nt_new; rowok = valid && d.nt_new_it[row] == iter; }
-                else { adj = d.nt_all; rowok = valid; }
-                uint4 a[VPL];
+                    // Enumerate the set bits of the adjacency row, lowest first,
+                    // one per group per step (ballot picks the holding lane).
+                    while (true) {
+                        bool mine_nz = false;
 #pragma unroll
-                for (int j = 0; j < VPL; ++j) {
-                    const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
-                    a[j] = (rowok && v < nvec) ? reinterpret_cast<const uint4 *>(adj + (size_t)row * W)[v]
-                                               : make_uint4(0, 0, 0, 0);
-                }
-                // Enumerate the set bits of the adjacency row, lowest first,
-                // one per group per step (ballot picks the holding lane).
-                while (true) {
-                    bool mine_nz = false;
+                        for (int j = 0; j < VPL; ++j) mine_nz |= nz4(a[j]);
+                        const unsigned b = __ballot_sync(FULLMASK, mine_nz);
+                        if (b == 0u) break;
+                        const unsigned gb = b & gmask;
+                        const int holder = gb ? (__ffs(gb) - 1) : lane;
+                        int ypos = -1;
+                        if (lane == holder && gb) {
 #pragma unroll
-                    for (int j = 0; j < VPL; ++j) mine_nz |= nz4(a[j]);
-                    const unsigned b = __ballot_sync(FULLMASK, mine_nz);
-                    if (b == 0u) break;
-                    const unsigned gb = b & gmask;
-                    const int holder = gb ? (__ffs(gb) - 1) : lane;
-                    int ypos = -1;
-                    if (lane == holder && gb) {
-#pragma unroll
-                        for (int j = 0; j < VPL; ++j) {
-                            if (ypos < 0 && nz4(a[j])) {
-                                const int bit = lowbit4(a[j], true);
-                                ypos = (int)(((uint32_t)gl + (uint32_t)j * lpr) * 128u) + bit;
+                            for (int j = 0; j < VPL; ++j) {
+                                if (ypos < 0 && nz4(a[j])) {
+                                    const int bit = lowbit4(a[j], true);
+                                    ypos = (int)(((uint32_t)gl + (uint32_t)j * lpr) * 128u) + bit;
+                                }
                             }
                         }
+                        const int y = __shfl_sync(FULLMASK, ypos, holder);
+                        if (gb) take((uint32_t)y);
                     }
-                    const int y = __shfl_sync(FULLMASK, ypos, holder);
-                    if (gb) take((uint32_t)y);
                 }
             }
         }
@@ -216,7 +234,11 @@ template <int VPL>
 __global__ void __launch_bounds__(256) k_extract(const XItem *__restrict__ items, const FDesc *__restrict__ fds) {
     const XItem it = items[blockIdx.x];
     const QCtl *c = it.ctl;
-    if (c->phase != kPhaseRun || c->changed_rows != 0ull) return;
+    if (c->phase != kPhaseRun) return;
+    // Extraction follows the last level's final pass: its FIRST pass when the
+    // level is acyclic, else the first pass that changed no row.
+    const bool cyc = (c->cyclic_mask >> c->level) & 1ull;
+    if (c->level + 1 != c->n_levels || (cyc && c->changed_rows != 0ull)) return;
     const uint32_t g0 = c->g_iter_start, iter = c->iter;
     __shared__ unsigned long long s_new;
     if (threadIdx.x == 0) s_new = 0;
@@ -299,7 +321,22 @@ __global__ void k_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGrap
         c.passes += 1;
         c.rounds_total += 1;
         c.rows_changed_total += c.changed_rows;
-        if (c.changed_rows == 0ull) {
+        c.rounds_in_iter += 1;
+        const bool cyc = (c.cyclic_mask >> c.level) & 1ull;
+        if (cyc && c.changed_rows != 0ull) {
+            // a cyclic level repeats until a pass changes nothing
+            c.g += 1;
+            c.mode = kModeProp;
+            if (c.max_rounds && c.rounds_in_iter >= c.max_rounds) {
+                c.status = kStatusRoundCap;
+                c.phase = kPhaseDone;
+            }
+        } else if (c.level + 1 < c.n_levels) {
+            c.level += 1;
+            c.g += 1;
+            c.mode = kModeNew;
+        } else {
+            // extraction ran in this pass: the iteration is complete
             c.iters_done = c.iter;
             c.edges_total += c.new_edges;
             if (c.new_edges == 0ull) {
@@ -310,19 +347,12 @@ __global__ void k_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGrap
             } else {
                 c.iter += 1;
                 c.g += 1;
+                c.level = 0;
                 c.mode = kModeNew;
                 c.g_iter_start = c.g;
                 c.rounds_in_iter = 0;
             }
             c.new_edges = 0;
-        } else {
-            c.rounds_in_iter += 1;
-            c.g += 1;
-            c.mode = kModeProp;
-            if (c.max_rounds && c.rounds_in_iter >= c.max_rounds) {
-                c.status = kStatusRoundCap;
-                c.phase = kPhaseDone;
-            }
         }
         if (c.phase == kPhaseRun && c.passes >= c.max_passes) {
             c.status = kStatusPassCap;
@@ -341,7 +371,7 @@ __global__ void k_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGrap
 
 // Reset the loop state of queries [0, nq) (start of a run).
 __global__ void k_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds,
-                            uint32_t max_passes) {
+                            uint32_t max_passes, uint32_t n_levels, unsigned long long cyclic_mask) {
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
         QCtl c;
         memset(&c, 0, sizeof(c));
@@ -353,6 +383,9 @@ __global__ void k_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, u
         c.max_iter = max_iter;
         c.max_rounds = max_rounds;
         c.max_passes = max_passes;
+        c.level = 0;
+        c.n_levels = n_levels;
+        c.cyclic_mask = cyclic_mask;
         *ctls[q] = c;
     }
 }
@@ -579,8 +612,8 @@ cudaError_t launch_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGra
 }
 
 cudaError_t launch_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds,
-                             uint32_t max_passes, cudaStream_t st) {
-    k_ctl_reset<<<(nq + 255) / 256, 256, 0, st>>>(ctls, nq, max_iter, max_rounds, max_passes);
+                             uint32_t max_passes, uint32_t n_levels, unsigned long long cyclic_mask, cudaStream_t st) {
+    k_ctl_reset<<<(nq + 255) / 256, 256, 0, st>>>(ctls, nq, max_iter, max_rounds, max_passes, n_levels, cyclic_mask);
     return cudaGetLastError();
 }
 
