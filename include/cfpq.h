@@ -267,6 +267,34 @@ int cfpq_result_reachable_bits(cfpq_server *srv, uint64_t ticket, uint32_t box, 
 /* Free a finished query's device state and forget the ticket. */
 int cfpq_release(cfpq_server *srv, uint64_t ticket);
 
+/* ---- staging without device allocation ------------------------------------------------ */
+
+/* The paper has no counterpart to this call: it serves callers that must not
+ * have the library allocate device memory, such as a service that keeps all
+ * device memory in its own fixed pool and swaps in new graph snapshots, or a
+ * process whose remaining GPU memory belongs to another framework.
+ *
+ * Same result as cfpq_load_graph_device (edge list in device memory, read on
+ * the context's stream; duplicates merged; range errors -> INVALID_ARG), but
+ * the staging temporaries (counts, offsets, an unsorted edge copy, the scan
+ * workspace, the error flag) live in one fixed array of about 16 MiB compiled
+ * into the library, which every GPU that loads the library holds until the
+ * process exits.  The output goes into the adjacency buffers the context
+ * already owns; they must come from an earlier cfpq_load_graph or
+ * cfpq_load_graph_device of a graph at least as large (same or larger
+ * n_terminals * n_vertices + 1 offsets and n_edges columns), else
+ * CFPQ_ERR_BUFFER_TOO_SMALL.  Limits: n_terminals * n_vertices <= 524288 and
+ * n_edges <= 2097152, else CFPQ_ERR_UNSUPPORTED.  No cudaMalloc, cudaFree or
+ * other allocating routine is called.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (each call
+ * clears what must start at zero); calls that overlap on the GPU race, so run
+ * them one at a time.  Synchronises the context's stream once. */
+int cfpq_load_graph_device_noalloc(cfpq_ctx *ctx, uint32_t n_vertices, uint32_t n_terminals, size_t n_edges,
+                                   const uint32_t *d_src, const uint32_t *d_label, const uint32_t *d_dst);
+
 /* ---- diagnostics ----------------------------------------------------------------------- */
 
 const char *cfpq_status_string(int status);

@@ -111,6 +111,7 @@ def _declare(lib):
         "cfpq_destroy": (c_int, [P]),
         "cfpq_load_graph": (c_int, [P, c_uint32, c_uint32, c_size_t, u32p, u32p, u32p]),
         "cfpq_load_graph_device": (c_int, [P, c_uint32, c_uint32, c_size_t, P, P, P]),
+        "cfpq_load_graph_device_noalloc": (c_int, [P, c_uint32, c_uint32, c_size_t, P, P, P]),
         "cfpq_load_rsm": (c_int, [P, POINTER(cfpq_rsm)]),
         "cfpq_run": (c_int, [P, POINTER(cfpq_run_stats)]),
         "cfpq_count_index": (c_int, [P, u64p, u64p]),
