@@ -62,7 +62,7 @@ typedef void (*cfpq_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
 #define CFPQ_CLOSURE_AUTO 0      /* bit-packed rows; tensor-core tiles where a label matrix is dense */
 #define CFPQ_CLOSURE_BITPACKED 1 /* bit-packed uint64 rows only */
 #define CFPQ_CLOSURE_TC_FP8 2    /* dense tiles as 0/1 FP8-E4M3 tcgen05 products, FP32 accumulate, > 0 */
-#define CFPQ_CLOSURE_TC_I8 3     /* dense tiles as 0/1 INT8 tcgen05 products, INT32 accumulate, > 0 */
+#define CFPQ_CLOSURE_TC_I8 3     /* 0/1 INT8 tcgen05 products: CFPQ_ERR_UNSUPPORTED on sm_103a (no kind::i8) */
 
 /* Fixpoint loop driver (Listing 1, "while M2 is changing"). */
 #define CFPQ_LOOP_DEVICE 0 /* one CUDA-graph launch; device-side convergence flags */
@@ -266,6 +266,19 @@ int cfpq_result_reachable_bits(cfpq_server *srv, uint64_t ticket, uint32_t box, 
 
 /* Free a finished query's device state and forget the ticket. */
 int cfpq_release(cfpq_server *srv, uint64_t ticket);
+
+/* ---- building block: dense Boolean product on the tensor cores ---------------------- */
+
+/* c = a * b over the Boolean semiring for n x n bit matrices (host buffers,
+ * row x = ceil(n/64) uint64 words, bit y of a row = word y/64, bit y%64),
+ * computed by the closure's tcgen05 tile kernel: 0/1 operands as FP8-E4M3
+ * with FP32 accumulation, a count > 0 giving a 1.  Exact for n <= 65536
+ * (counts < 2^24).  use_int8 = 1 (0/1 INT8 with INT32 accumulation) returns
+ * CFPQ_ERR_UNSUPPORTED: sm_103a has no tcgen05 kind::i8 MMA.  The closure's dense tiles (Sec. 3.1, Listing 1) use the
+ * same kernel; this call exposes it for testing and reuse.  Allocates and
+ * frees its device buffers on `stream` (a cudaStream_t) and synchronises it.
+ * CFPQ_ERR_TIMEOUT if a bounded wait inside the kernel gave up. */
+int cfpq_tc_bool_product(uint32_t n, int use_int8, const uint64_t *a, const uint64_t *b, uint64_t *c, void *stream);
 
 /* ---- staging without device allocation ------------------------------------------------ */
 

@@ -132,6 +132,7 @@ def _declare(lib):
         "cfpq_poll": (c_int, [P, c_uint64, POINTER(c_int)]),
         "cfpq_result_reachable_bits": (c_int, [P, c_uint64, c_uint32, P]),
         "cfpq_release": (c_int, [P, c_uint64]),
+        "cfpq_tc_bool_product": (c_int, [c_uint32, c_int, P, P, P, P]),
         "cfpq_status_string": (c_char_p, [c_int]),
         "cfpq_last_error": (c_char_p, [P]),
     }
@@ -440,3 +441,23 @@ class Server:
         if rc != CFPQ_OK:
             raise CfpqError(rc, "cfpq_release: " + status_string(rc))
         self._keep.pop(ticket, None)
+
+
+def tc_bool_product(a: np.ndarray, b: np.ndarray, use_int8: bool = False, stream=None) -> np.ndarray:
+    """Boolean product of two n x n bool matrices on the tensor cores."""
+    lib = load()
+    n = a.shape[0]
+    wn = (n + 63) // 64
+
+    def pack(m):
+        pad = np.zeros((n, wn * 64), dtype=bool)
+        pad[:, :n] = m
+        return np.ascontiguousarray(np.packbits(pad, axis=1, bitorder="little").view(np.uint64))
+
+    pa, pb = pack(a), pack(b)
+    out = np.zeros((n, wn), dtype=np.uint64)
+    rc = lib.cfpq_tc_bool_product(n, 1 if use_int8 else 0, c_void_p(pa.ctypes.data), c_void_p(pb.ctypes.data),
+                                  c_void_p(out.ctypes.data), c_void_p(stream or 0))
+    if rc != CFPQ_OK:
+        raise CfpqError(rc, "cfpq_tc_bool_product: " + status_string(rc))
+    return np.unpackbits(out.view(np.uint8), axis=1, bitorder="little")[:, :n].astype(bool)

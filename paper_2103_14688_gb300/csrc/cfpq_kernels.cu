@@ -125,32 +125,97 @@ __global__ void __launch_bounds__(256) k_gather(const GItem *__restrict__ items,
                 // a source row takes part when its stamp is >= thr
                 const uint32_t thr = new_edges ? 0u : (cbit == 2u ? g0 : g - 1u);
 
-                // OR of source row y of C[u,t] (and the product edge itself).
-                auto take = [&](uint32_t y) {
-                    if (use_ident) {
-                        const uint32_t v = y >> 7;
-                        if ((int)(v % lpr) == gl) {
-                            const int j = (int)(v / lpr);
+                // Every lane proposes one candidate edge (x, y) of its group's
+                // row (y_l, has_l).  The group keeps those whose source row is
+                // dirty, then ORs their rows U at a time: all U rows are loaded
+                // before any is combined, so several 128-bit loads per lane are
+                // in flight.
+                constexpr int U = VPL >= 8 ? 1 : 8 / VPL;
+                auto take_batch = [&](uint32_t y_l, bool has_l) {
+                    const bool keep = has_l && (d.rblk == nullptr || thr == 0u || d.rstamp[y_l] >= thr);
+                    const unsigned bal = __ballot_sync(FULLMASK, keep);
+                    unsigned mine = (bal & gmask) >> (grp * lpr);
+                    while (__any_sync(FULLMASK, mine != 0u)) {
+                        uint32_t ys[U];
+                        bool hs[U];
 #pragma unroll
-                            for (int jj = 0; jj < VPL; ++jj)
-                                if (jj == j) setbit4(acc[jj], y & 127u);
+                        for (int u = 0; u < U; ++u) {
+                            hs[u] = mine != 0u;
+                            const int p = hs[u] ? __ffs(mine) - 1 : 0;
+                            if (hs[u]) mine &= mine - 1u;
+                            ys[u] = __shfl_sync(FULLMASK, y_l, p, lpr);
                         }
-                    }
-                    if (d.rblk) {
-                        if (thr && d.rstamp[y] < thr) return;
-                        const uint4 *r = reinterpret_cast<const uint4 *>(d.rblk + (size_t)y * W);
+                        if (use_ident) {
 #pragma unroll
-                        for (int j = 0; j < VPL; ++j) {
-                            const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
-                            if (v < nvec) or4(acc[j], r[v]);
+                            for (int u = 0; u < U; ++u) {
+                                if (!hs[u]) continue;
+                                const uint32_t v = ys[u] >> 7;
+                                if ((int)(v % lpr) == gl) {
+                                    const int j = (int)(v / lpr);
+#pragma unroll
+                                    for (int jj = 0; jj < VPL; ++jj)
+                                        if (jj == j) setbit4(acc[jj], ys[u] & 127u);
+                                }
+                            }
                         }
-                        if (gl == 0) ++my_ors;
+                        if (d.rblk) {
+                            uint4 rv[U][VPL];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const uint4 *r = reinterpret_cast<const uint4 *>(d.rblk + (size_t)ys[u] * W);
+#pragma unroll
+                                for (int j = 0; j < VPL; ++j) {
+                                    const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
+                                    rv[u][j] = (hs[u] && v < nvec) ? r[v] : make_uint4(0, 0, 0, 0);
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                                for (int j = 0; j < VPL; ++j) or4(acc[j], rv[u][j]);
+                                if (gl == 0 && hs[u]) ++my_ors;
+                            }
+                        }
                     }
                 };
 
                 if (d.csr_off) {
                     const uint32_t e0 = valid ? d.csr_off[row] : 0u, e1 = valid ? d.csr_off[row + 1] : 0u;
-                    for (uint32_t e = e0; e < e1; ++e) take(d.csr_col[e]);
+                    const uint32_t cnt = e1 - e0;
+                    const uint32_t maxcnt = __reduce_max_sync(FULLMASK, cnt);
+                    if (maxcnt <= 8u) {
+                        // short adjacency rows (the common case on sparse graphs):
+                        // one edge at a time, no ballot overhead
+                        for (uint32_t e = e0; e < e1; ++e) {
+                            const uint32_t y = d.csr_col[e];
+                            if (use_ident) {
+                                const uint32_t v = y >> 7;
+                                if ((int)(v % lpr) == gl) {
+                                    const int j = (int)(v / lpr);
+#pragma unroll
+                                    for (int jj = 0; jj < VPL; ++jj)
+                                        if (jj == j) setbit4(acc[jj], y & 127u);
+                                }
+                            }
+                            if (d.rblk) {
+                                if (thr && d.rstamp[y] < thr) continue;
+                                const uint4 *r = reinterpret_cast<const uint4 *>(d.rblk + (size_t)y * W);
+#pragma unroll
+                                for (int j = 0; j < VPL; ++j) {
+                                    const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
+                                    if (v < nvec) or4(acc[j], r[v]);
+                                }
+                                if (gl == 0) ++my_ors;
+                            }
+                        }
+                    } else {
+                        for (uint32_t base = 0; base < maxcnt; base += (uint32_t)lpr) {
+                            const uint32_t k2 = base + (uint32_t)gl;
+                            const bool has = k2 < cnt;
+                            const uint32_t y = has ? d.csr_col[e0 + k2] : 0u;
+                            take_batch(y, has);
+                        }
+                    }
                 } else {
                     const uint64_t *adj;
                     bool rowok;
@@ -163,28 +228,21 @@ __global__ void __launch_bounds__(256) k_gather(const GItem *__restrict__ items,
                         a[j] = (rowok && v < nvec) ? reinterpret_cast<const uint4 *>(adj + (size_t)row * W)[v]
                                                    : make_uint4(0, 0, 0, 0);
                     }
-                    // Enumerate the set bits of the adjacency row, lowest first,
-                    // one per group per step (ballot picks the holding lane).
+                    // Each lane proposes the lowest set bit of its part of the
+                    // adjacency row per step (ballot/ffs enumeration).
                     while (true) {
-                        bool mine_nz = false;
+                        bool has = false;
+                        uint32_t y = 0u;
 #pragma unroll
-                        for (int j = 0; j < VPL; ++j) mine_nz |= nz4(a[j]);
-                        const unsigned b = __ballot_sync(FULLMASK, mine_nz);
-                        if (b == 0u) break;
-                        const unsigned gb = b & gmask;
-                        const int holder = gb ? (__ffs(gb) - 1) : lane;
-                        int ypos = -1;
-                        if (lane == holder && gb) {
-#pragma unroll
-                            for (int j = 0; j < VPL; ++j) {
-                                if (ypos < 0 && nz4(a[j])) {
-                                    const int bit = lowbit4(a[j], true);
-                                    ypos = (int)(((uint32_t)gl + (uint32_t)j * lpr) * 128u) + bit;
-                                }
+                        for (int j = 0; j < VPL; ++j) {
+                            if (!has && nz4(a[j])) {
+                                const int bit = lowbit4(a[j], true);
+                                y = ((uint32_t)gl + (uint32_t)j * lpr) * 128u + (uint32_t)bit;
+                                has = true;
                             }
                         }
-                        const int y = __shfl_sync(FULLMASK, ypos, holder);
-                        if (gb) take((uint32_t)y);
+                        if (!__any_sync(FULLMASK, has)) break;
+                        take_batch(y, has);
                     }
                 }
             }

@@ -1,0 +1,476 @@
+// cfpq_tc.cu -- dense Boolean matrix products on the 5th-generation tensor
+// cores (tcgen05, sm_103a) for the closure of Listing 1 (arXiv 2103.14688,
+// Sec. 3.1): out[x, z] |= OR_y A[x, y] AND B[y, z] for 0/1 matrices held as
+// bit rows.
+//
+// The Boolean product is computed exactly as an integer count: operands are
+// 0/1 FP8-E4M3 (1.0 = 0x38) with FP32 accumulation, or 0/1 unsigned INT8 with
+// INT32 accumulation, and a count > 0 sets the output bit.  Counts never
+// exceed the inner dimension (<= 65536 < 2^24), so FP32 represents them
+// exactly and the result equals the bit-packed product bit for bit.
+//
+// Tile: 128 output rows x 256 output columns per CTA, K in stages of 128.
+// Per stage the CTA loads the A bits (128 rows x 128 bits) and B bits (128
+// rows x 256 bits, rows filtered by a dirty stamp), expands them to bytes in
+// shared memory in the canonical no-swizzle K-major layout (8-row x 16-byte
+// core matrices), B through a 32 x 32 bit transpose done with warp shuffles,
+// and one thread issues four 128x256x32 MMAs into a TMEM accumulator (256
+// columns of FP32/INT32).  Two shared-memory buffers alternate; an mbarrier
+// signalled by tcgen05.commit says when the tensor core has finished reading
+// a buffer.  Stages whose A or B tile is all zero are skipped (dirty tiles).
+// The epilogue reads the accumulator with tcgen05.ld, thresholds it, ORs the
+// bits into the output rows and stamps the rows that changed.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "cfpq_dev.cuh"
+
+namespace cfpq {
+
+namespace tc {
+
+constexpr int kBM = 128, kBN = 256, kBK = 128;       // tile (K in bytes = elements)
+constexpr int kKG = kBK / 16;                         // 16-byte core-matrix columns per stage
+constexpr int kStageA = kBM * kBK;                    // bytes
+constexpr int kStageB = kBN * kBK;
+constexpr int kStageBytes = kStageA + kStageB;        // 48 KiB
+constexpr int kThreads = 256;
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kWaitLimit = 1u << 26;             // bounded spin on mbarriers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading (K) and
+// stride (M/N) byte offsets between core matrices, descriptor version 1,
+// no swizzle.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor: D format (1 = F32, 2 = S32), A/B format 0 (E4M3 for
+// kind::f8f6f4, unsigned 8-bit for kind::i8), both K-major, N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t dfmt, uint32_t M, uint32_t N) {
+    return (dfmt << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(bool int8, uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                    uint32_t accum) {
+    // kind::i8 is not available on sm_103a (ptxas: "Feature '.kind::i8' not
+    // supported on .target 'sm_103a'"); the 0/1 operands use FP8-E4M3.
+    (void)int8;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+// Bounded wait; returns false if the limit was reached.
+__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity) {
+    for (uint32_t i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(m, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 32 TMEM lanes x 32 consecutive 32-bit columns; lane i of the warp gets its
+// lane's 32 values.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// 4 bits -> 4 bytes of 0/1 (bit i -> byte i).
+__device__ __forceinline__ uint32_t spread4(uint32_t b) { return ((b & 0xFu) * 0x00204081u) & 0x01010101u; }
+
+// 16 bits -> 16 bytes, each 0 or `one`.
+__device__ __forceinline__ uint4 expand16(uint32_t b, uint32_t one) {
+    return make_uint4(spread4(b) * one, spread4(b >> 4) * one, spread4(b >> 8) * one, spread4(b >> 12) * one);
+}
+
+// Byte offset of element (row r, k byte) in a K-major no-swizzle tile whose
+// rows are grouped by 8 and whose K is split into kKG 16-byte columns.
+__device__ __forceinline__ uint32_t core_off(uint32_t r, uint32_t kg) {
+    return ((r >> 3) * kKG + kg) * 128u + (r & 7u) * 16u;
+}
+
+// Transpose a 32 x 32 bit block across a warp: lane i holds row i on entry,
+// column i (bit j = row j) on exit.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+    const uint32_t masks[5] = {0xFFFF0000u, 0xFF00FF00u, 0xF0F0F0F0u, 0xCCCCCCCCu, 0xAAAAAAAAu};
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int s = 16 >> i;
+        const uint32_t M = masks[i];
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, s);
+        x = (lane & s) ? ((x & M) | ((y & M) >> s)) : ((x & ~M) | ((y & ~M) << s));
+    }
+    return x;
+}
+
+}  // namespace tc
+
+// One dense product job: out |= A * B over the square n x n state block,
+// with A rows optionally valid only in one iteration (A2 semantics) and B
+// rows taking part only when their stamp is >= thr.
+struct TcJob {
+    uint64_t *out;
+    uint32_t *out_stamp;
+    uint32_t *out_last;
+    const uint64_t *A;
+    const uint32_t *a_it;      // if set: A row x is used only when a_it[x] == iter
+    const uint64_t *B;
+    const uint32_t *b_stamp;   // stamps of B rows (null: all rows)
+    QCtl *ctl;                 // null: standalone product (iter = 0, thr = 0, g = 0)
+    uint32_t n, W;
+    uint32_t ident;            // also OR the A rows themselves into out (product edge u == t)
+    uint32_t chan;             // 1, 2 or 4 (see src_channels); 0 = always, thr 0
+    uint32_t level, same_level;
+    const uint32_t *box_new_it;
+    const uint32_t *rlast;
+    uint32_t tiles_m, tiles_n;  // tiles of this job
+    uint32_t tile0;             // first global tile index of this job
+    uint32_t pad;
+};
+
+// Decide whether the job takes part in this pass and with which threshold.
+__device__ __forceinline__ bool tc_job_active(const TcJob &j, uint32_t *thr, uint32_t *iter, uint32_t *g) {
+    if (!j.ctl) {
+        *thr = 0;
+        *iter = 0;
+        *g = 0;
+        return true;
+    }
+    const QCtl *c = j.ctl;
+    if (c->phase != kPhaseRun || c->level != j.level) return false;
+    *iter = c->iter;
+    *g = c->g;
+    const uint32_t g0 = c->g_iter_start;
+    if (j.chan == 1u) {
+        if (c->mode != kModeNew) return false;
+        if (j.box_new_it && *j.box_new_it != c->iter) return false;
+        if (!j.box_new_it && c->iter != 1) return false;
+        *thr = 0;
+        return true;
+    }
+    if (j.chan == 2u) {
+        if (c->mode != kModeNew || j.same_level || !j.rlast || *j.rlast < g0) return false;
+        if (!j.box_new_it && c->iter == 1) return false;  // terminals: iteration 1 is covered by channel 1
+        *thr = g0;
+        return true;
+    }
+    if (j.chan == 4u) {
+        if (c->mode != kModeProp || !j.same_level || !j.rlast || *j.rlast + 1u < c->g) return false;
+        *thr = c->g - 1u;
+        return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(tc::kThreads, 1)
+    k_tc_product(const TcJob *__restrict__ jobs, uint32_t n_jobs, int *err_flag) {
+    constexpr bool INT8 = false;
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ uint32_t s_changed_rows;
+    __shared__ uint8_t s_row_changed[kBM];
+
+    // locate the job of this tile
+    uint32_t jb = 0;
+    {
+        uint32_t lo = 0, hi = n_jobs;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) / 2;
+            if (jobs[mid].tile0 <= blockIdx.x) lo = mid;
+            else hi = mid;
+        }
+        jb = lo;
+    }
+    const TcJob &J = jobs[jb];
+    uint32_t thr, iter, g;
+    if (!tc_job_active(J, &thr, &iter, &g)) return;
+    const uint32_t t = blockIdx.x - J.tile0;
+    if (t >= J.tiles_m * J.tiles_n) return;
+    const uint32_t m0 = (t / J.tiles_n) * kBM, n0 = (t % J.tiles_n) * kBN;
+    const uint32_t n = J.n, W = J.W;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t one = INT8 ? 0x01u : 0x38u;
+
+    unsigned char *stage[2] = {smem_raw, smem_raw + kStageBytes};
+    if (warp == 0) tmem_alloc(&tmem_base, kTmemCols);
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        s_changed_rows = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < kBM) s_row_changed[tid] = 0;
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = tmem_base;
+
+    constexpr uint32_t idesc = INT8 ? make_idesc(2, kBM, kBN) : make_idesc(1, kBM, kBN);
+    bool inflight[2] = {false, false};
+    uint32_t parity[2] = {0u, 0u};
+    bool started = false, timed_out = false;
+    int buf = 0;
+    const uint32_t ksteps = (n + kBK - 1) / kBK;
+
+    for (uint32_t ks = 0; ks < ksteps && !timed_out; ++ks) {
+        const uint32_t k0 = ks * kBK;  // bits of A's columns / B's rows
+        // ---- load this stage's bits into registers ----
+        // A: 256 threads x (half a row: 64 bits) of the 128 x 128-bit tile
+        const uint32_t ar = (uint32_t)tid >> 1, ah = (uint32_t)tid & 1u;
+        uint64_t abits = 0;
+        {
+            const uint32_t x = m0 + ar, w = (k0 >> 6) + ah;
+            if (x < n && w < W && (!J.a_it || J.a_it[x] == iter)) abits = J.A[(size_t)x * W + w];
+        }
+        // B: 32 blocks of 32 (rows) x 32 (columns) bits; warp w owns 4 blocks:
+        // rows k0 + 32 * (w / 2) + lane, columns n0 + 128 * (w % 2) + 32 * b
+        uint32_t bword[4];
+        {
+            const uint32_t y = k0 + 32u * ((uint32_t)warp >> 1) + (uint32_t)lane;
+            const bool rok = y < n && (!J.b_stamp || thr == 0u || J.b_stamp[y] >= thr);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t zc = n0 + 128u * ((uint32_t)warp & 1u) + 32u * (uint32_t)b;  // first column
+                uint32_t v = 0;
+                if (rok && zc < (W << 6)) {
+                    const uint64_t wv = J.B[(size_t)y * W + (zc >> 6)];
+                    v = (uint32_t)(wv >> (zc & 63u));
+                }
+                bword[b] = v;
+            }
+        }
+        const int anyA = __syncthreads_or(abits != 0ull);
+        const int anyB = __syncthreads_or((bword[0] | bword[1] | bword[2] | bword[3]) != 0u);
+        if (!anyA || !anyB) continue;  // dirty-tile skip: this stage adds nothing
+
+        // ---- the buffer must be free: wait for the MMAs that read it ----
+        if (inflight[buf]) {
+            if (!mbar_wait(&mbar[buf], parity[buf])) timed_out = true;
+            parity[buf] ^= 1u;
+            inflight[buf] = false;
+        }
+        if (__syncthreads_or(timed_out)) { timed_out = true; break; }
+        unsigned char *sa = stage[buf], *sb = stage[buf] + kStageA;
+        // ---- expand A: row ar, k bits [64 ah, 64 ah + 64) -> 4 core-matrix rows ----
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t kg = ah * 4u + (uint32_t)q;
+            *reinterpret_cast<uint4 *>(sa + core_off(ar, kg)) = expand16((uint32_t)(abits >> (16 * q)) & 0xFFFFu, one);
+        }
+        // ---- expand B transposed: column z gets the bits of rows y as bytes ----
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t col = transpose32(bword[b], lane);  // bit i = row (32 * (warp/2) + i)
+            const uint32_t z = 128u * ((uint32_t)warp & 1u) + 32u * (uint32_t)b + (uint32_t)lane;
+            const uint32_t kg = 2u * ((uint32_t)warp >> 1);
+            *reinterpret_cast<uint4 *>(sb + core_off(z, kg)) = expand16(col & 0xFFFFu, one);
+            *reinterpret_cast<uint4 *>(sb + core_off(z, kg + 1u)) = expand16(col >> 16, one);
+        }
+        fence_async_smem();
+        tc_before();
+        __syncthreads();
+        tc_after();
+        if (tid == 0) {
+            const uint32_t abase = smem_u32(sa), bbase = smem_u32(sb);
+#pragma unroll
+            for (int kk = 0; kk < kBK / 32; ++kk) {
+                const uint64_t ad = make_desc(abase + (uint32_t)kk * 256u, 128u, kKG * 128u);
+                const uint64_t bd = make_desc(bbase + (uint32_t)kk * 256u, 128u, kKG * 128u);
+                tc::mma(INT8, tmem, ad, bd, idesc, (started || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(&mbar[buf]);
+        }
+        started = true;
+        inflight[buf] = true;
+        buf ^= 1;
+    }
+    // ---- drain ----
+    for (int b = 0; b < 2; ++b) {
+        if (inflight[b]) {
+            if (!mbar_wait(&mbar[b], parity[b])) timed_out = true;
+            parity[b] ^= 1u;
+            inflight[b] = false;
+        }
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const bool bad = __syncthreads_or(timed_out) != 0;
+    if (bad && tid == 0) atomicOr(err_flag, 1);
+
+    // ---- epilogue: warps 0-3 columns [0,128), warps 4-7 columns [128,256) ----
+    if (!bad && (started || J.ident)) {
+        const uint32_t quarter = (uint32_t)warp & 3u, half = (uint32_t)warp >> 2;
+        const uint32_t r = quarter * 32u + (uint32_t)lane;  // tile row = TMEM lane
+        const uint32_t x = m0 + r;
+        uint32_t mask[4] = {0u, 0u, 0u, 0u};
+        if (started) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                uint32_t v[32];
+                const uint32_t col = half * 128u + 32u * (uint32_t)c;
+                tc::tmem_ld32(tmem + ((quarter * 32u) << 16) + col, v);
+                uint32_t mbits = 0u;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) mbits |= (v[i] != 0u ? 1u : 0u) << i;
+                mask[c] = mbits;
+            }
+        }
+        if (x < n) {
+            const uint32_t w0 = (n0 + half * 128u) >> 6;  // first output word of this half
+            bool ch = false;
+#pragma unroll
+            for (int wq = 0; wq < 2; ++wq) {
+                const uint32_t w = w0 + (uint32_t)wq;
+                if (w >= W) continue;
+                uint64_t add = (uint64_t)mask[2 * wq] | ((uint64_t)mask[2 * wq + 1] << 32);
+                if (J.ident && (!J.a_it || J.a_it[x] == iter)) add |= J.A[(size_t)x * W + w];
+                if (!add) continue;
+                // several jobs (sources) of one output block may share a launch
+                const uint64_t old =
+                    atomicOr(reinterpret_cast<unsigned long long *>(J.out + (size_t)x * W + w), (unsigned long long)add);
+                if (add & ~old) ch = true;
+            }
+            if (ch) s_row_changed[r] = 1;
+        }
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    if (tid < kBM && s_row_changed[tid]) {
+        if (J.out_stamp) J.out_stamp[m0 + tid] = g;
+        atomicAdd(&s_changed_rows, 1u);
+    }
+    __syncthreads();
+    if (tid == 0 && s_changed_rows) {
+        if (J.out_last) *J.out_last = g;
+        if (J.ctl) atomicAdd(&J.ctl->changed_rows, (unsigned long long)s_changed_rows);
+    }
+    if (tid == 0 && J.ctl && started) atomicAdd(&J.ctl->tile_mmas, 1ull);
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+int tc_smem_bytes() { return 2 * tc::kStageBytes; }
+
+cudaError_t launch_tc_product(bool int8, const TcJob *jobs, uint32_t n_jobs, uint32_t n_tiles, int *err_flag,
+                              cudaStream_t st) {
+    if (n_tiles == 0) return cudaSuccess;
+    if (int8) return cudaErrorNotSupported;
+    const int smem = tc_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_tc_product, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_tc_product<<<n_tiles, tc::kThreads, smem, st>>>(jobs, n_jobs, err_flag);
+    return cudaGetLastError();
+}
+
+size_t tc_job_size() { return sizeof(TcJob); }
+
+}  // namespace cfpq
+
+// ---------------------------------------------------------------------------
+// Standalone product (building block, testable on its own).
+// ---------------------------------------------------------------------------
+#include "../../include/cfpq.h"
+
+extern "C" int cfpq_tc_bool_product(uint32_t n, int use_int8, const uint64_t *a, const uint64_t *b, uint64_t *c,
+                                    void *stream) {
+    using namespace cfpq;
+    if (n == 0 || !a || !b || !c || n > 65536) return CFPQ_ERR_INVALID_ARG;
+    if (use_int8) return CFPQ_ERR_UNSUPPORTED;  // no kind::i8 tensor-core MMA on sm_103a
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint32_t n_pad = (n + 127u) & ~127u, W = n_pad / 64u;
+    const size_t wn = (n + 63) / 64, bytes = (size_t)n * W * 8;
+    uint64_t *dA = nullptr, *dB = nullptr, *dC = nullptr;
+    TcJob *dJ = nullptr;
+    int *dErr = nullptr;
+    int rc = CFPQ_OK;
+    auto ck = [&](cudaError_t e) {
+        if (e != cudaSuccess && rc == CFPQ_OK) rc = CFPQ_ERR_CUDA;
+        return e == cudaSuccess;
+    };
+    if (ck(cudaMallocAsync((void **)&dA, bytes, st)) && ck(cudaMallocAsync((void **)&dB, bytes, st)) &&
+        ck(cudaMallocAsync((void **)&dC, bytes, st)) && ck(cudaMallocAsync((void **)&dJ, sizeof(TcJob), st)) &&
+        ck(cudaMallocAsync((void **)&dErr, sizeof(int), st))) {
+        ck(cudaMemsetAsync(dA, 0, bytes, st));
+        ck(cudaMemsetAsync(dB, 0, bytes, st));
+        ck(cudaMemsetAsync(dC, 0, bytes, st));
+        ck(cudaMemsetAsync(dErr, 0, sizeof(int), st));
+        ck(cudaMemcpy2DAsync(dA, W * 8, a, wn * 8, wn * 8, n, cudaMemcpyHostToDevice, st));
+        ck(cudaMemcpy2DAsync(dB, W * 8, b, wn * 8, wn * 8, n, cudaMemcpyHostToDevice, st));
+        TcJob j;
+        memset(&j, 0, sizeof(j));
+        j.out = dC;
+        j.A = dA;
+        j.B = dB;
+        j.n = n;
+        j.W = W;
+        j.tiles_m = (n + 127) / 128;
+        j.tiles_n = (n_pad + 255) / 256;
+        j.tile0 = 0;
+        ck(cudaMemcpyAsync(dJ, &j, sizeof(j), cudaMemcpyHostToDevice, st));
+        ck(launch_tc_product(use_int8 != 0, dJ, 1, j.tiles_m * j.tiles_n, dErr, st));
+        int herr = 0;
+        ck(cudaMemcpyAsync(&herr, dErr, sizeof(int), cudaMemcpyDeviceToHost, st));
+        ck(cudaMemcpy2DAsync(c, wn * 8, dC, W * 8, wn * 8, n, cudaMemcpyDeviceToHost, st));
+        ck(cudaStreamSynchronize(st));
+        if (rc == CFPQ_OK && herr) rc = CFPQ_ERR_TIMEOUT;
+    }
+    if (dA) cudaFreeAsync(dA, st);
+    if (dB) cudaFreeAsync(dB, st);
+    if (dC) cudaFreeAsync(dC, st);
+    if (dJ) cudaFreeAsync(dJ, st);
+    if (dErr) cudaFreeAsync(dErr, st);
+    cudaStreamSynchronize(st);
+    return rc;
+}
