@@ -123,6 +123,8 @@ typedef struct {
     uint64_t device_bytes;     /* device memory held by the query */
     double ms_total;           /* wall time of the call (host clock) */
     double ms_closure;         /* summed CUDA-event time of the closure-pass launches (profile = 1) */
+    double ms_setup;           /* host clock: staging, planning, buffer and work-list set-up of the call */
+    double ms_loop;            /* host clock: the fixpoint loop (launch to completion) */
     uint32_t closure_launches; /* closure-pass launches timed (profile = 1) */
     uint32_t pad_;
 } cfpq_run_stats;

@@ -60,6 +60,7 @@ class cfpq_run_stats(Structure):
                 ("row_ors", c_uint64), ("rows_changed", c_uint64), ("row_bytes", c_uint64),
                 ("tile_mmas", c_uint64), ("closure_blocks", c_uint64),
                 ("device_bytes", c_uint64), ("ms_total", c_double), ("ms_closure", c_double),
+                ("ms_setup", c_double), ("ms_loop", c_double),
                 ("closure_launches", c_uint32), ("pad_", c_uint32)]
 
     def as_dict(self):

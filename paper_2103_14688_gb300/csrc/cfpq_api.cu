@@ -73,11 +73,11 @@ int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t 
     const cudaStream_t st = ctx->stream;
     const uint32_t mi = ctx->opt.max_iterations, mr = ctx->opt.max_rounds, mp = pass_cap(ctx->opt);
     uint32_t n_gather = 0, n_extract = 0;
-    for (int v = 0; v < 5; ++v) {
+    for (int v = 0; v < kClasses; ++v) {
         n_gather += ex.n_items[v] ? 1 : 0;
         n_extract += ex.n_xitems[v] ? 1 : 0;
     }
-    const uint32_t per_pass = n_gather + n_extract + 1;
+    const uint32_t per_pass = n_gather + n_extract + (ex.n_tcjobs ? 1 : 0) + 1;
     if (ctx->opt.loop_mode == CFPQ_LOOP_HOST) {
         if (ex.enqueue_prologue(st, mi, mr, mp)) return fail(ctx, CFPQ_ERR_CUDA, "prologue launch failed");
         int running = 1;
@@ -118,8 +118,9 @@ int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t 
         }
         CK(ctx, cudaGraphLaunch(ex.exec, st));
     }
-    std::string e;
-    if (ex.read_ctls(st, ctls)) return fail(ctx, CFPQ_ERR_CUDA, "reading loop state failed");
+    int tc_error = 0;
+    if (ex.read_ctls(st, ctls, &tc_error)) return fail(ctx, CFPQ_ERR_CUDA, "reading loop state failed");
+    if (tc_error) return fail(ctx, CFPQ_ERR_TIMEOUT, "a tensor-core tile gave up waiting for its MMAs");
     if (ctx->opt.loop_mode != CFPQ_LOOP_HOST && launches) {
         uint32_t passes = 0;
         for (const auto &c : *ctls) passes = std::max(passes, c.passes);
@@ -134,6 +135,7 @@ int ensure_query(cfpq_ctx *ctx) {
     if (!ctx->has_rsm) return fail(ctx, CFPQ_ERR_STATE, "no RSM loaded");
     QueryDev &q = ctx->query;
     q.g = &ctx->graph;
+    q.closure_mode = ctx->opt.closure_mode;
     if (!q.prepared || q.graph_generation != ctx->graph.generation || ctx->exec_dirty) {
         std::string e;
         int rc = q.prepare(&ctx->A, &e);
@@ -196,6 +198,7 @@ int cfpq_create(cfpq_ctx **out, const cfpq_options *opt, void *stream) {
         cfpq_default_options(&c->opt);
     }
     if (c->opt.loop_mode > CFPQ_LOOP_HOST || c->opt.closure_mode > CFPQ_CLOSURE_TC_I8) return CFPQ_ERR_INVALID_ARG;
+    if (c->opt.closure_mode == CFPQ_CLOSURE_TC_I8) return CFPQ_ERR_UNSUPPORTED;  // no kind::i8 MMA on sm_103a
     if (c->opt.profile && c->opt.loop_mode != CFPQ_LOOP_HOST) return CFPQ_ERR_INVALID_ARG;
     if ((c->opt.alloc == nullptr) != (c->opt.free == nullptr)) return CFPQ_ERR_INVALID_ARG;
     int ndev = 0;
@@ -238,8 +241,8 @@ static int load_graph_impl(cfpq_ctx *ctx, uint32_t n, uint32_t nt, size_t m, con
         return fail(ctx, rc, e);
     }
     ctx->has_graph = true;
-    if (ctx->has_rsm && ctx->query.rsm.max_terminal_plus1 > nt)
-        return fail(ctx, CFPQ_ERR_INVALID_ARG, "the loaded RSM reads a terminal >= n_terminals");
+    // an RSM reading more terminals than this graph has is reported by
+    // cfpq_run (the caller may be about to load a matching RSM)
     return CFPQ_OK;
     API_CATCH(ctx)
 }
@@ -277,17 +280,21 @@ int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats) {
     const auto t0 = std::chrono::steady_clock::now();
     if (int rc = set_device(ctx)) return rc;
     if (int rc = ensure_query(ctx)) return rc;
+    const auto t1 = std::chrono::steady_clock::now();
     std::vector<QCtl> ctls;
     uint32_t launches = 0, claunch = 0;
     double ms_cl = 0.0;
     if (int rc = run_executor(ctx, ctx->exec, &ctls, &launches, &ms_cl, &claunch)) return rc;
     ctx->has_result = true;
-    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const auto t2 = std::chrono::steady_clock::now();
+    const double ms = std::chrono::duration<double, std::milli>(t2 - t0).count();
     if (stats) {
         fill_stats(stats, ctls[0], ctx->query, ms);
         stats->gpu_launches = launches;
         stats->ms_closure = ms_cl;
         stats->closure_launches = claunch;
+        stats->ms_setup = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        stats->ms_loop = std::chrono::duration<double, std::milli>(t2 - t1).count();
     }
     const int st = status_of(ctls[0]);
     if (st) return fail(ctx, st, "iteration, round or pass cap reached before the fixpoint");
@@ -675,6 +682,7 @@ extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_quer
                              qq.label, qq.dst, false, &e);
         if (rc) return fail(ctx, rc, "query " + std::to_string(i) + ": " + e);
         std::unique_ptr<QueryDev> q(new QueryDev());
+        q->closure_mode = ctx->opt.closure_mode;
         rc = copy_rsm(qq.rsm, &q->rsm, &e);
         if (rc) return fail(ctx, rc, "query " + std::to_string(i) + ": " + e);
         q->g = g.get();
@@ -686,11 +694,13 @@ extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_quer
     for (auto &q : ctx->bqueries) ctx->bexec.qs.push_back(q.get());
     int rc = ctx->bexec.assemble(&ctx->A, ctx->stream, &e);
     if (rc) return fail(ctx, rc, e);
+    const auto t1 = std::chrono::steady_clock::now();
     std::vector<QCtl> ctls;
     uint32_t launches = 0;
     if ((rc = run_executor(ctx, ctx->bexec, &ctls, &launches))) return rc;
     ctx->has_batch = true;
-    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const auto t2 = std::chrono::steady_clock::now();
+    const double ms = std::chrono::duration<double, std::milli>(t2 - t0).count();
     int worst = CFPQ_OK;
     cfpq_run_stats tot;
     memset(&tot, 0, sizeof(tot));
@@ -708,6 +718,8 @@ extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_quer
         if (status_of(ctls[i])) worst = status_of(ctls[i]);
     }
     tot.ms_total = ms;
+    tot.ms_setup = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    tot.ms_loop = std::chrono::duration<double, std::milli>(t2 - t1).count();
     tot.gpu_launches = launches;
     tot.status = worst ? (uint32_t)(-worst) : 0;
     if (total_stats) *total_stats = tot;

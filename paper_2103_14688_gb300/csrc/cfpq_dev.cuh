@@ -114,4 +114,68 @@ struct XItem {
     uint32_t lpr;
 };
 
+// One dense product job: out |= A * B over the square n x n state block,
+// with A rows optionally valid only in one iteration (A2 semantics) and B
+// rows taking part only when their stamp is >= thr.
+struct TcJob {
+    uint64_t *out;
+    uint32_t *out_stamp;
+    uint32_t *out_last;
+    const uint64_t *A;
+    const uint32_t *a_it;      // if set: A row x is used only when a_it[x] == iter
+    const uint64_t *B;
+    const uint32_t *b_stamp;   // stamps of B rows (null: all rows)
+    QCtl *ctl;                 // null: standalone product (iter = 0, thr = 0, g = 0)
+    uint32_t n, W;
+    uint32_t ident;            // also OR the A rows themselves into out (product edge u == t)
+    uint32_t chan;             // 1, 2 or 4 (see src_channels); 0 = always, thr 0
+    uint32_t level, same_level;
+    const uint32_t *box_new_it;
+    const uint32_t *rlast;
+    uint32_t tiles_m, tiles_n;  // tiles of this job
+    uint32_t tile0;             // first global tile index of this job
+    uint32_t pad;
+};
+
+// Per-executor work tables.  Items of each kind are sorted by (query, level);
+// the static tables give, for query q and level L, the first item of that
+// level (entry L = n_levels gives the end).  Before every pass the control
+// kernel writes, for each running query, the range of items of its current
+// level and an exclusive prefix over queries, so that persistent kernels walk
+// only the live items.
+constexpr int kVplClasses = 5;
+// Item classes: row width class (VPL 1, 2, 4, 8, 16) x whether the block has
+// sources over nonterminal (bit-row) adjacency: class = 2 * vpl_index + nt.
+constexpr int kClasses = 2 * kVplClasses;
+struct ExecTables {
+    uint32_t nq;
+    uint32_t maxL1;                          // max levels over queries + 1
+    const uint32_t *g_lvl[kClasses];         // [nq * maxL1] gather items per (q, level)
+    const uint32_t *x_rng[kClasses];         // [nq + 1] extraction items per query
+    const uint32_t *t_lvl;                   // [nq * maxL1] TC jobs per (q, level)
+    const uint32_t *t_lvl_tiles;             // [nq * maxL1] TC tiles of the jobs at (q, level)
+    // written by the control kernel for the next pass
+    uint32_t *g_total;                       // [kClasses]
+    uint32_t *g_pre[kClasses];               // [nq] exclusive prefix of live items
+    uint32_t *g_beg[kClasses];               // [nq] first live item
+    uint32_t *x_total;                       // [kClasses]
+    uint32_t *x_pre[kClasses];
+    uint32_t *x_beg[kClasses];
+    uint32_t *t_total;                       // [1] live TC tiles
+    uint32_t *t_pre;                         // [nq] prefix of live tiles
+    uint32_t *t_job_beg;                     // [nq]
+    uint32_t *t_job_end;                     // [nq]
+};
+
+// Find q with pre[q] <= i < pre[q+1] (pre exclusive, non-decreasing).
+__host__ __device__ inline uint32_t find_owner(const uint32_t *pre, uint32_t nq, uint32_t i) {
+    uint32_t lo = 0, hi = nq;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pre[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 }  // namespace cfpq

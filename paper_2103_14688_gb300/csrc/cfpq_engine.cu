@@ -175,6 +175,17 @@ int stage_graph(GraphDev *g, Allocator *A, cudaStream_t st, uint32_t n, uint32_t
     return CFPQ_OK;
 }
 
+int GraphDev::ensure_term_bits(Allocator *A, cudaStream_t st, std::string *err) {
+    if (term_bits.p && term_bits_generation == generation && term_bits_m == m_unique) return CFPQ_OK;
+    const size_t rows = (size_t)n_term * n;
+    if (!term_bits.ensure(A, rows * W * 8, err)) return CFPQ_ERR_OUT_OF_MEMORY;
+    ENG_CK(cudaMemsetAsync(term_bits.p, 0, rows * W * 8, st));
+    ENG_CK(launch_csr_to_bits(csr_off.as<uint32_t>(), csr_col.as<uint32_t>(), rows, W, term_bits.as<uint64_t>(), st));
+    term_bits_generation = generation;
+    term_bits_m = m_unique;
+    return CFPQ_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Query planning: which n x n state blocks of C3 can be nonzero.
 // ---------------------------------------------------------------------------
@@ -266,7 +277,11 @@ int QueryDev::plan(std::string *err) {
             const int32_t rb = blk_of[(size_t)u * Q + t];
             if (!ident && rb < 0) continue;
             const uint32_t same = (rb >= 0 && blk_level[(size_t)rb] == blk_level[b]) ? 1u : 0u;
-            srcs.push_back({tr.kind, tr.sym, ident ? 1u : 0u, rb, same});
+            // tensor-core mode: every source that reads a closure block is a
+            // dense product job; sources that only add the product edges
+            // themselves (u == t on an acyclic state) stay bit-packed
+            const uint32_t dense = (closure_mode == CFPQ_CLOSURE_TC_FP8 && rb >= 0) ? 1u : 0u;
+            srcs.push_back({tr.kind, tr.sym, ident ? 1u : 0u, rb, same, dense});
         }
         blk_nsrc[b] = (uint32_t)srcs.size() - blk_src0[b];
     }
@@ -357,65 +372,151 @@ static const int kVplOf[5] = {1, 2, 4, 8, 16};
 int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     const uint32_t nq = (uint32_t)qs.size();
     if (!ctl_ptrs.ensure(A, std::max<uint32_t>(nq, 1) * sizeof(QCtl *), err) ||
-        !mirror.ensure(A, std::max<uint32_t>(nq, 1) * sizeof(QCtl), err) || !running.ensure(A, 16, err))
+        !mirror.ensure(A, std::max<uint32_t>(nq, 1) * sizeof(QCtl), err) || !running.ensure(A, 16, err) ||
+        !tc_err.ensure(A, 16, err))
         return CFPQ_ERR_OUT_OF_MEMORY;
+    uint32_t maxL1 = 2;
+    for (QueryDev *q : qs) maxL1 = std::max(maxL1, q->n_levels + 1);
     std::vector<QCtl *> hp;
     std::vector<SrcDesc> hs;
-    std::vector<GItem> hi[5];
+    std::vector<GItem> hi[kClasses];
     std::vector<FDesc> hf;
-    std::vector<XItem> hx[5];
+    std::vector<XItem> hx[kClasses];
+    std::vector<TcJob> hj;
+    // static tables
+    std::vector<uint32_t> g_lvl[kClasses], x_rng[kClasses];
+    for (int v = 0; v < kClasses; ++v) {
+        g_lvl[v].assign((size_t)nq * maxL1, 0);
+        x_rng[v].assign((size_t)nq + 1, 0);
+    }
+    std::vector<uint32_t> t_lvl((size_t)nq * maxL1, 0), t_lvl_tiles((size_t)nq * maxL1, 0);
+    max_tc_tiles = 0;
+    uint32_t live_bound[kClasses] = {0};
     for (uint32_t qi = 0; qi < nq; ++qi) {
         QueryDev &q = *qs[qi];
-        const GraphDev &g = *q.g;
+        GraphDev &g = *q.g;
         QCtl *cp = q.ctl();
         hp.push_back(cp);
+        bool need_term_bits = false;
+        for (const auto &sdesc : q.srcs) need_term_bits |= (sdesc.dense && sdesc.label_kind == 0);
+        if (need_term_bits) {
+            int rc = g.ensure_term_bits(A, st, err);
+            if (rc) return rc;
+        }
         const uint32_t base = (uint32_t)hs.size();
-        for (const auto &s : q.srcs) {
+        for (const auto &sd : q.srcs) {
             SrcDesc d;
             memset(&d, 0, sizeof(d));
-            if (s.label_kind == 0) {
-                d.csr_off = g.csr_off.as<uint32_t>() + (size_t)s.label * q.n;
+            if (sd.label_kind == 0) {
+                d.csr_off = g.csr_off.as<uint32_t>() + (size_t)sd.label * q.n;
                 d.csr_col = g.csr_col.as<uint32_t>();
             } else {
-                d.nt_all = q.m2_ptr(s.label);
-                d.nt_new = q.a2_ptr(s.label);
-                d.nt_new_it = q.a2it_mem.as<uint32_t>() + (size_t)s.label * q.n;
-                d.box_new_it = q.boxit_mem.as<uint32_t>() + s.label;
+                d.nt_all = q.m2_ptr(sd.label);
+                d.nt_new = q.a2_ptr(sd.label);
+                d.nt_new_it = q.a2it_mem.as<uint32_t>() + (size_t)sd.label * q.n;
+                d.box_new_it = q.boxit_mem.as<uint32_t>() + sd.label;
             }
-            if (s.rblk >= 0) {
-                d.rblk = q.blk_ptr((uint32_t)s.rblk);
-                d.rstamp = q.stamp_ptr((uint32_t)s.rblk);
-                d.rlast = q.last_mem.as<uint32_t>() + s.rblk;
+            if (sd.rblk >= 0) {
+                d.rblk = q.blk_ptr((uint32_t)sd.rblk);
+                d.rstamp = q.stamp_ptr((uint32_t)sd.rblk);
+                d.rlast = q.last_mem.as<uint32_t>() + sd.rblk;
             }
-            d.ident = s.ident;
-            d.same_level = s.same_level;
-            d.dense = 0;
+            d.ident = sd.ident;
+            d.same_level = sd.same_level;
+            d.dense = sd.dense;
             hs.push_back(d);
         }
         const int vi = vpl_index(q.vpl);
         const uint32_t rows_per_step = 8u * (32u / q.lpr);
         const uint32_t rpi = std::max<uint32_t>(64u, rows_per_step * 4u);
-        for (size_t b = 0; b < q.blocks.size(); ++b) {
-            if (q.blk_nsrc[b] == 0) continue;
-            for (uint32_t r0 = 0; r0 < q.n; r0 += rpi) {
-                GItem it;
-                it.out = q.blk_ptr((uint32_t)b);
-                it.out_stamp = q.stamp_ptr((uint32_t)b);
-                it.out_last = q.last_mem.as<uint32_t>() + b;
-                it.ctl = cp;
-                it.src0 = base + q.blk_src0[b];
-                it.nsrc = q.blk_nsrc[b];
-                it.row0 = r0;
-                it.row1 = std::min(q.n, r0 + rpi);
-                it.W = q.W;
-                it.lpr = q.lpr;
-                it.level = q.blk_level[b];
-                it.pad = 0;
-                hi[vi].push_back(it);
+        const uint32_t tiles_m = (q.n + 127u) / 128u, tiles_n = (q.n + 255u) / 256u;
+        for (uint32_t L = 0; L <= q.n_levels; ++L) {
+            for (int v = 0; v < kClasses; ++v) g_lvl[v][(size_t)qi * maxL1 + L] = (uint32_t)hi[v].size();
+            t_lvl[(size_t)qi * maxL1 + L] = (uint32_t)hj.size();
+            if (L == q.n_levels) break;
+            uint32_t lvl_tiles = 0;
+            for (size_t b = 0; b < q.blocks.size(); ++b) {
+                if (q.blk_level[b] != L || q.blk_nsrc[b] == 0) continue;
+                bool has_nt = false;
+                for (uint32_t k = 0; k < q.blk_nsrc[b]; ++k) {
+                    const auto &sd = q.srcs[q.blk_src0[b] + k];
+                    has_nt |= (sd.label_kind != 0 && !sd.dense);
+                }
+                const int cls = 2 * vi + (has_nt ? 1 : 0);
+                for (uint32_t r0 = 0; r0 < q.n; r0 += rpi) {
+                    GItem it;
+                    it.out = q.blk_ptr((uint32_t)b);
+                    it.out_stamp = q.stamp_ptr((uint32_t)b);
+                    it.out_last = q.last_mem.as<uint32_t>() + b;
+                    it.ctl = cp;
+                    it.src0 = base + q.blk_src0[b];
+                    it.nsrc = q.blk_nsrc[b];
+                    it.row0 = r0;
+                    it.row1 = std::min(q.n, r0 + rpi);
+                    it.W = q.W;
+                    it.lpr = q.lpr;
+                    it.level = L;
+                    it.pad = 0;
+                    hi[cls].push_back(it);
+                }
+                // dense sources of this block: one product job per channel
+                for (uint32_t k = 0; k < q.blk_nsrc[b]; ++k) {
+                    const auto &sd = q.srcs[q.blk_src0[b] + k];
+                    if (!sd.dense) continue;
+                    const SrcDesc &d = hs[base + q.blk_src0[b] + k];
+                    const uint32_t chans[2] = {1u, sd.same_level ? 4u : 2u};
+                    for (uint32_t ch : chans) {
+                        TcJob j;
+                        memset(&j, 0, sizeof(j));
+                        j.out = q.blk_ptr((uint32_t)b);
+                        j.out_stamp = q.stamp_ptr((uint32_t)b);
+                        j.out_last = q.last_mem.as<uint32_t>() + b;
+                        if (sd.label_kind == 0) {
+                            j.A = g.term_bits.as<uint64_t>() + (size_t)sd.label * q.n * q.W;
+                            j.a_it = nullptr;
+                            j.box_new_it = nullptr;
+                        } else {
+                            j.A = ch == 1u ? q.a2_ptr(sd.label) : q.m2_ptr(sd.label);
+                            j.a_it = ch == 1u ? d.nt_new_it : nullptr;
+                            j.box_new_it = d.box_new_it;
+                        }
+                        j.B = d.rblk;
+                        j.b_stamp = d.rstamp;
+                        j.rlast = d.rlast;
+                        j.ctl = cp;
+                        j.n = q.n;
+                        j.W = q.W;
+                        j.ident = (ch == 1u) ? sd.ident : 0u;
+                        j.chan = ch;
+                        j.level = L;
+                        j.same_level = sd.same_level;
+                        j.tiles_m = tiles_m;
+                        j.tiles_n = tiles_n;
+                        j.tile0 = lvl_tiles;
+                        lvl_tiles += tiles_m * tiles_n;
+                        hj.push_back(j);
+                    }
+                }
             }
+            t_lvl_tiles[(size_t)qi * maxL1 + L] = lvl_tiles;
+        }
+        for (uint32_t L = q.n_levels + 1; L < maxL1; ++L) {
+            for (int v = 0; v < kClasses; ++v)
+                g_lvl[v][(size_t)qi * maxL1 + L] = g_lvl[v][(size_t)qi * maxL1 + q.n_levels];
+            t_lvl[(size_t)qi * maxL1 + L] = t_lvl[(size_t)qi * maxL1 + q.n_levels];
+        }
+        uint32_t qtiles = 0;
+        for (uint32_t L = 0; L < q.n_levels; ++L) qtiles = std::max(qtiles, t_lvl_tiles[(size_t)qi * maxL1 + L]);
+        max_tc_tiles += qtiles;
+        for (int c = 0; c < kClasses; ++c) {
+            uint32_t mx = 0;
+            for (uint32_t L = 0; L < q.n_levels; ++L)
+                mx = std::max(mx, g_lvl[c][(size_t)qi * maxL1 + L + 1] - g_lvl[c][(size_t)qi * maxL1 + L]);
+            live_bound[c] += mx;
         }
         const uint32_t fbase = (uint32_t)hf.size();
         for (uint32_t fb : q.fblocks) hf.push_back(FDesc{q.blk_ptr(fb), q.stamp_ptr(fb)});
+        for (int v = 0; v < kClasses; ++v) x_rng[v][qi] = (uint32_t)hx[v].size();
         for (uint32_t b = 0; b < q.B; ++b) {
             if (q.box_nf[b] == 0) continue;
             for (uint32_t r0 = 0; r0 < q.n; r0 += rpi) {
@@ -431,10 +532,11 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                 x.row1 = std::min(q.n, r0 + rpi);
                 x.W = q.W;
                 x.lpr = q.lpr;
-                hx[vi].push_back(x);
+                hx[2 * vi].push_back(x);
             }
         }
     }
+    for (int v = 0; v < kClasses; ++v) x_rng[v][nq] = (uint32_t)hx[v].size();
     auto upload = [&](DBuf &buf, const void *h, size_t bytes) -> int {
         if (!buf.ensure(A, std::max<size_t>(bytes, 64), err)) return CFPQ_ERR_OUT_OF_MEMORY;
         if (bytes) ENG_CK(cudaMemcpyAsync(buf.p, h, bytes, cudaMemcpyHostToDevice, st));
@@ -444,12 +546,59 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     if ((rc = upload(ctl_ptrs, hp.data(), hp.size() * sizeof(QCtl *)))) return rc;
     if ((rc = upload(srcs, hs.data(), hs.size() * sizeof(SrcDesc)))) return rc;
     if ((rc = upload(fds, hf.data(), hf.size() * sizeof(FDesc)))) return rc;
-    for (int v = 0; v < 5; ++v) {
+    if ((rc = upload(tcjobs, hj.data(), hj.size() * sizeof(TcJob)))) return rc;
+    n_tcjobs = (uint32_t)hj.size();
+    for (int v = 0; v < kClasses; ++v) {
+        max_live[v] = live_bound[v];
         n_items[v] = (uint32_t)hi[v].size();
         n_xitems[v] = (uint32_t)hx[v].size();
         if ((rc = upload(items[v], hi[v].data(), hi[v].size() * sizeof(GItem)))) return rc;
         if ((rc = upload(xitems[v], hx[v].data(), hx[v].size() * sizeof(XItem)))) return rc;
     }
+    // tables: one buffer, static part then the per-pass part
+    const size_t nqa = std::max<uint32_t>(nq, 1), lv = nqa * maxL1;
+    const size_t words = kClasses * lv + kClasses * (nqa + 1) + 2 * lv  // static
+                         + kClasses + 2 * kClasses * nqa                  // gather lists
+                         + kClasses + 2 * kClasses * nqa                  // extraction lists
+                         + 1 + 3 * nqa;                                   // tensor-core lists
+    std::vector<uint32_t> ht(words, 0);
+    size_t o = 0;
+    memset(&T, 0, sizeof(T));
+    T.nq = nq;
+    T.maxL1 = maxL1;
+    uint32_t *dbase = nullptr;
+    if (!tables.ensure(A, words * 4, err)) return CFPQ_ERR_OUT_OF_MEMORY;
+    dbase = tables.as<uint32_t>();
+    auto take = [&](size_t cnt) {
+        uint32_t *p = dbase + o;
+        o += cnt;
+        return p;
+    };
+    for (int v = 0; v < kClasses; ++v) {
+        std::copy(g_lvl[v].begin(), g_lvl[v].end(), ht.begin() + o);
+        T.g_lvl[v] = take(lv);
+    }
+    for (int v = 0; v < kClasses; ++v) {
+        std::copy(x_rng[v].begin(), x_rng[v].end(), ht.begin() + o);
+        T.x_rng[v] = take(nqa + 1);
+    }
+    std::copy(t_lvl.begin(), t_lvl.end(), ht.begin() + o);
+    T.t_lvl = take(lv);
+    std::copy(t_lvl_tiles.begin(), t_lvl_tiles.end(), ht.begin() + o);
+    T.t_lvl_tiles = take(lv);
+    T.g_total = take(kClasses);
+    for (int v = 0; v < kClasses; ++v) T.g_pre[v] = take(nqa);
+    for (int v = 0; v < kClasses; ++v) T.g_beg[v] = take(nqa);
+    T.x_total = take(kClasses);
+    for (int v = 0; v < kClasses; ++v) T.x_pre[v] = take(nqa);
+    for (int v = 0; v < kClasses; ++v) T.x_beg[v] = take(nqa);
+    T.t_total = take(1);
+    T.t_pre = take(nqa);
+    T.t_job_beg = take(nqa);
+    T.t_job_end = take(nqa);
+    ENG_CK(cudaMemcpyAsync(dbase, ht.data(), words * 4, cudaMemcpyHostToDevice, st));
+    ENG_CK(cudaMemsetAsync(tc_err.p, 0, 16, st));
+    if (n_tcjobs) ENG_CK(prepare_tc_launch());
     ENG_CK(cudaStreamSynchronize(st));
     drop_graph();
     built = true;
@@ -459,6 +608,12 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
 int Executor::enqueue_prologue(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes) {
     for (QueryDev *q : qs)
         if (int rc = q->enqueue_init(st, max_iter, max_rounds, max_passes)) return rc;
+    return enqueue_lists(st);
+}
+
+int Executor::enqueue_lists(cudaStream_t st) {
+    std::string *err = nullptr;
+    ENG_CK(launch_control(ctl_ptrs.as<QCtl *>(), (uint32_t)qs.size(), mirror.as<QCtl>(), 0, 0, nullptr, T, 0, st));
     return CFPQ_OK;
 }
 
@@ -466,13 +621,15 @@ int Executor::enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int us
                            cudaEvent_t ev_before, cudaEvent_t ev_after) {
     std::string *err = nullptr;
     if (ev_before) ENG_CK(cudaEventRecord(ev_before, st));
-    for (int v = 0; v < 5; ++v)
-        ENG_CK(launch_gather(kVplOf[v], items[v].as<GItem>(), n_items[v], srcs.as<SrcDesc>(), st));
+    for (int c = 0; c < kClasses; ++c)
+        ENG_CK(launch_gather(kVplOf[c / 2], (c & 1) != 0, items[c].as<GItem>(), max_live[c], srcs.as<SrcDesc>(), T, c,
+                             st));
+    if (n_tcjobs) ENG_CK(launch_tc_product(false, tcjobs.as<TcJob>(), max_tc_tiles, T, tc_err.as<int>(), st));
     if (ev_after) ENG_CK(cudaEventRecord(ev_after, st));
-    for (int v = 0; v < 5; ++v)
-        ENG_CK(launch_extract(kVplOf[v], xitems[v].as<XItem>(), n_xitems[v], fds.as<FDesc>(), st));
-    ENG_CK(launch_control(ctl_ptrs.as<QCtl *>(), (uint32_t)qs.size(), mirror.as<QCtl>(), h, use_handle, running_out,
-                          st));
+    for (int c = 0; c < kClasses; c += 2)
+        ENG_CK(launch_extract(kVplOf[c / 2], xitems[c].as<XItem>(), n_xitems[c], fds.as<FDesc>(), T, c, st));
+    ENG_CK(launch_control(ctl_ptrs.as<QCtl *>(), (uint32_t)qs.size(), mirror.as<QCtl>(), h, use_handle, running_out, T,
+                          1, st));
     return CFPQ_OK;
 }
 
@@ -522,12 +679,15 @@ int Executor::build_graph(cudaStream_t st, uint32_t max_iter, uint32_t max_round
     return CFPQ_OK;
 }
 
-int Executor::read_ctls(cudaStream_t st, std::vector<QCtl> *out) {
+int Executor::read_ctls(cudaStream_t st, std::vector<QCtl> *out, int *tc_error) {
     std::string *err = nullptr;
     out->resize(qs.size());
     if (qs.empty()) return CFPQ_OK;
     ENG_CK(cudaMemcpyAsync(out->data(), mirror.p, qs.size() * sizeof(QCtl), cudaMemcpyDeviceToHost, st));
+    int te = 0;
+    if (tc_error && n_tcjobs) ENG_CK(cudaMemcpyAsync(&te, tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     ENG_CK(cudaStreamSynchronize(st));
+    if (tc_error) *tc_error = te;
     return CFPQ_OK;
 }
 

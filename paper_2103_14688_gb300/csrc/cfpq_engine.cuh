@@ -13,10 +13,17 @@ namespace cfpq {
 
 // ---- kernel launchers (cfpq_kernels.cu) ----
 int vpl_for_words(uint32_t W);
-cudaError_t launch_gather(int vpl, const GItem *items, uint32_t n_items, const SrcDesc *srcs, cudaStream_t st);
-cudaError_t launch_extract(int vpl, const XItem *items, uint32_t n_items, const FDesc *fds, cudaStream_t st);
+cudaError_t launch_gather(int vpl, bool nt, const GItem *items, uint32_t n_items, const SrcDesc *srcs,
+                          const ExecTables &T, int cls, cudaStream_t st);
+cudaError_t launch_extract(int vpl, const XItem *items, uint32_t n_items, const FDesc *fds, const ExecTables &T,
+                           int cls, cudaStream_t st);
 cudaError_t launch_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGraphConditionalHandle h, int use_handle,
-                           int *running_out, cudaStream_t st);
+                           int *running_out, const ExecTables &T, int advance, cudaStream_t st);
+cudaError_t launch_tc_product(bool int8, const TcJob *jobs, uint32_t max_tiles, const ExecTables &T, int *err_flag,
+                              cudaStream_t st);
+cudaError_t prepare_tc_launch();
+cudaError_t launch_csr_to_bits(const uint32_t *off, const uint32_t *col, size_t rows, uint32_t W, uint64_t *bits,
+                               cudaStream_t st);
 cudaError_t launch_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds,
                              uint32_t max_passes, uint32_t n_levels, unsigned long long cyclic_mask, cudaStream_t st);
 cudaError_t launch_eps_init(const void *eds, uint32_t ned, uint32_t grid, cudaStream_t st);
@@ -94,6 +101,10 @@ struct GraphDev {
     size_t m_in = 0, m_unique = 0;
     DBuf csr_off;  // [n_term * n + 1]
     DBuf csr_col;  // [m_unique]
+    DBuf term_bits;  // [n_term * n * W] bit rows of the terminal labels (tensor-core sources only)
+    uint64_t term_bits_generation = ~0ull;
+    size_t term_bits_m = 0;
+    int ensure_term_bits(Allocator *A, cudaStream_t st, std::string *err);
     // staging scratch
     DBuf e_src, e_lbl, e_dst, cnt, off, col, ucnt, scan_tmp, label_map, err;
     std::vector<uint32_t> h_off;  // host copies on demand (paths)
@@ -113,7 +124,8 @@ struct QueryDev {
     uint32_t n_eps = 0;
     uint64_t device_bytes = 0;
     // host descriptors (pointers filled once buffers exist; ctl set by the executor)
-    struct Src { uint32_t label_kind, label, ident; int32_t rblk; uint32_t same_level; };
+    uint32_t closure_mode = CFPQ_CLOSURE_AUTO;
+    struct Src { uint32_t label_kind, label, ident; int32_t rblk; uint32_t same_level, dense; };
     std::vector<uint32_t> blk_src0, blk_nsrc;  // per block
     std::vector<uint32_t> blk_level;           // per block, 0..n_levels-1
     uint32_t n_levels = 1;
@@ -138,8 +150,12 @@ struct QueryDev {
 // Runs the fixpoint of a set of queries with shared launches.
 struct Executor {
     std::vector<QueryDev *> qs;
-    DBuf ctl_ptrs, mirror, items[5], xitems[5], srcs, fds, running;
-    uint32_t n_items[5] = {0, 0, 0, 0, 0}, n_xitems[5] = {0, 0, 0, 0, 0};
+    DBuf ctl_ptrs, mirror, items[kClasses], xitems[kClasses], srcs, fds, running;
+    DBuf tcjobs, tables, tc_err;
+    ExecTables T;
+    uint32_t n_items[kClasses] = {0}, n_xitems[kClasses] = {0};
+    uint32_t max_live[kClasses] = {0};  // bound on live items of a pass: sum over queries of the largest level
+    uint32_t n_tcjobs = 0, max_tc_tiles = 0;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream: capture is not allowed on the legacy default stream
@@ -156,10 +172,11 @@ struct Executor {
     }
     int assemble(Allocator *A, cudaStream_t st, std::string *err);
     int enqueue_prologue(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes);
+    int enqueue_lists(cudaStream_t st);  // recompute the live lists without advancing any query
     int enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int use_handle, int *running_out,
                      cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);
     int build_graph(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes, std::string *err);
-    int read_ctls(cudaStream_t st, std::vector<QCtl> *out);
+    int read_ctls(cudaStream_t st, std::vector<QCtl> *out, int *tc_error = nullptr);
 };
 
 int stage_graph(GraphDev *g, Allocator *A, cudaStream_t st, uint32_t n, uint32_t n_term, size_t m, const uint32_t *src,

@@ -85,19 +85,32 @@ __device__ __forceinline__ uint32_t src_channels(const SrcDesc &d, uint32_t mode
 // handled by a group of `lpr` lanes, each lane holding VPL 128-bit vectors
 // (words 2v, 2v+1 for v = lane_in_group + j * lpr).
 // --------------------------------------------------------------------------
+// Occupancy target per row width: narrow rows keep 4 CTAs (32 warps) per SM.
 template <int VPL>
-__global__ void __launch_bounds__(256) k_gather(const GItem *__restrict__ items, const SrcDesc *__restrict__ srcs) {
-    const GItem it = items[blockIdx.x];
+struct GatherOcc {
+    static constexpr int value = VPL <= 2 ? 4 : (VPL == 4 ? 2 : 1);
+};
+
+template <int VPL, bool NT>
+__global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
+    k_gather(const GItem *__restrict__ items, const SrcDesc *__restrict__ srcs, ExecTables T, int cls) {
+    __shared__ unsigned long long s_changed, s_ors;
+    // one CTA per live item (the grid covers every item of the class; CTAs
+    // past the live count exit at once): a CTA that finishes early frees its
+    // slot for the next one, which a persistent loop would not.
+    const uint32_t total = T.g_total[cls];
+    for (uint32_t li = blockIdx.x; li < total; li += gridDim.x) {
+    const uint32_t q = find_owner(T.g_pre[cls], T.nq, li);
+    const GItem it = items[T.g_beg[cls][q] + (li - T.g_pre[cls][q])];
     const QCtl *c = it.ctl;
-    if (c->phase != kPhaseRun || c->level != it.level) return;
+    if (c->phase != kPhaseRun || c->level != it.level) continue;
     const uint32_t g = c->g, iter = c->iter, mode = c->mode, g0 = c->g_iter_start;
 
     int act = 0;
     for (uint32_t k = threadIdx.x; k < it.nsrc; k += blockDim.x)
         act |= src_channels(srcs[it.src0 + k], mode, iter, g, g0) != 0u;
-    if (!__syncthreads_or(act)) return;
+    if (!__syncthreads_or(act)) continue;
 
-    __shared__ unsigned long long s_changed, s_ors;
     if (threadIdx.x == 0) { s_changed = 0; s_ors = 0; }
     __syncthreads();
 
@@ -130,7 +143,7 @@ __global__ void __launch_bounds__(256) k_gather(const GItem *__restrict__ items,
                 // dirty, then ORs their rows U at a time: all U rows are loaded
                 // before any is combined, so several 128-bit loads per lane are
                 // in flight.
-                constexpr int U = VPL >= 8 ? 1 : 8 / VPL;
+                constexpr int U = VPL >= 4 ? 1 : 4 / VPL;
                 auto take_batch = [&](uint32_t y_l, bool has_l) {
                     const bool keep = has_l && (d.rblk == nullptr || thr == 0u || d.rstamp[y_l] >= thr);
                     const unsigned bal = __ballot_sync(FULLMASK, keep);
@@ -216,7 +229,7 @@ __global__ void __launch_bounds__(256) k_gather(const GItem *__restrict__ items,
                             take_batch(y, has);
                         }
                     }
-                } else {
+                } else if constexpr (NT) {
                     const uint64_t *adj;
                     bool rowok;
                     if (new_edges) { adj = d.nt_new; rowok = valid && d.nt_new_it[row] == iter; }
@@ -283,22 +296,28 @@ __global__ void __launch_bounds__(256) k_gather(const GItem *__restrict__ items,
         }
         if (s_ors) atomicAdd(&cw->row_ors, s_ors);
     }
+    __syncthreads();
+    }
 }
 
 // --------------------------------------------------------------------------
 // Extraction: runs for a query only after a pass that changed no row.
 // --------------------------------------------------------------------------
 template <int VPL>
-__global__ void __launch_bounds__(256) k_extract(const XItem *__restrict__ items, const FDesc *__restrict__ fds) {
-    const XItem it = items[blockIdx.x];
+__global__ void __launch_bounds__(256) k_extract(const XItem *__restrict__ items, const FDesc *__restrict__ fds,
+                                                 ExecTables T, int cls) {
+    __shared__ unsigned long long s_new;
+    const uint32_t total = T.x_total[cls];
+    for (uint32_t li = blockIdx.x; li < total; li += gridDim.x) {
+    const uint32_t q = find_owner(T.x_pre[cls], T.nq, li);
+    const XItem it = items[T.x_beg[cls][q] + (li - T.x_pre[cls][q])];
     const QCtl *c = it.ctl;
-    if (c->phase != kPhaseRun) return;
+    if (c->phase != kPhaseRun) continue;
     // Extraction follows the last level's final pass: its FIRST pass when the
     // level is acyclic, else the first pass that changed no row.
     const bool cyc = (c->cyclic_mask >> c->level) & 1ull;
-    if (c->level + 1 != c->n_levels || (cyc && c->changed_rows != 0ull)) return;
+    if (c->level + 1 != c->n_levels || (cyc && c->changed_rows != 0ull)) continue;
     const uint32_t g0 = c->g_iter_start, iter = c->iter;
-    __shared__ unsigned long long s_new;
     if (threadIdx.x == 0) s_new = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -362,17 +381,21 @@ __global__ void __launch_bounds__(256) k_extract(const XItem *__restrict__ items
         *it.box_new_it = iter + 1;
         atomicAdd(&it.ctl->new_edges, s_new);
     }
+    __syncthreads();
+    }
 }
 
 // --------------------------------------------------------------------------
 // Loop control: one CTA for all queries.
 // --------------------------------------------------------------------------
-__global__ void k_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGraphConditionalHandle handle,
-                          int use_handle, int *running_out) {
+__global__ void __launch_bounds__(1024) k_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror,
+                                                  cudaGraphConditionalHandle handle, int use_handle, int *running_out,
+                                                  ExecTables T, int advance) {
     int running = 0;
     for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
         QCtl &c = *ctls[q];
-        if (c.phase != kPhaseRun) {
+        if (c.phase != kPhaseRun || !advance) {
+            running |= (c.phase == kPhaseRun);
             mirror[q] = c;
             continue;
         }
@@ -421,6 +444,84 @@ __global__ void k_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGrap
         mirror[q] = c;
     }
     running = __syncthreads_or(running);
+    // Live work of the next pass: the items of the current level of every
+    // running query.  All 2 * kClasses + 1 counts of a query sit in registers
+    // and are scanned together across the CTA (warp shuffles, then the warp
+    // totals), one chunk of blockDim queries at a time.
+    constexpr int K = 2 * kClasses + 1;
+    __shared__ uint32_t s_wsum[32][K];
+    __shared__ uint32_t s_carry[K];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)((blockDim.x + 31) >> 5);
+    if (threadIdx.x < K) s_carry[threadIdx.x] = 0u;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < nq; c0 += blockDim.x) {
+        const uint32_t q = c0 + threadIdx.x;
+        uint32_t cnt[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) cnt[k] = 0u;
+        if (q < nq) {
+            const QCtl &c = *ctls[q];
+            const bool run = c.phase == kPhaseRun;
+            const uint32_t L = c.level, base = q * T.maxL1 + L;
+            const bool last = run && (L + 1 == c.n_levels);
+#pragma unroll
+            for (int v = 0; v < kClasses; ++v) {
+                const uint32_t gb = run ? T.g_lvl[v][base] : 0u, ge = run ? T.g_lvl[v][base + 1] : 0u;
+                T.g_beg[v][q] = gb;
+                cnt[v] = ge - gb;
+                const uint32_t xb = last ? T.x_rng[v][q] : 0u, xe = last ? T.x_rng[v][q + 1] : 0u;
+                T.x_beg[v][q] = xb;
+                cnt[kClasses + v] = xe - xb;
+            }
+            T.t_job_beg[q] = run ? T.t_lvl[base] : 0u;
+            T.t_job_end[q] = run ? T.t_lvl[base + 1] : 0u;
+            cnt[K - 1] = run ? T.t_lvl_tiles[base] : 0u;
+        }
+        uint32_t inc[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            uint32_t x = cnt[k];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            inc[k] = x;
+            if (lane == 31) s_wsum[wid][k] = x;
+        }
+        __syncthreads();
+        if (wid == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                uint32_t w = lane < nw ? s_wsum[lane][k] : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                    if (lane >= o) w += y;
+                }
+                if (lane < nw) s_wsum[lane][k] = w;  // inclusive prefix of warp totals
+            }
+        }
+        __syncthreads();
+        if (q < nq) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const uint32_t pre = s_carry[k] + (wid ? s_wsum[wid - 1][k] : 0u) + inc[k] - cnt[k];
+                if (k < kClasses) T.g_pre[k][q] = pre;
+                else if (k < 2 * kClasses) T.x_pre[k - kClasses][q] = pre;
+                else T.t_pre[q] = pre;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < K) s_carry[threadIdx.x] += s_wsum[nw - 1][threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x < K) {
+        const int k = threadIdx.x;
+        if (k < kClasses) T.g_total[k] = s_carry[k];
+        else if (k < 2 * kClasses) T.x_total[k - kClasses] = s_carry[k];
+        else *T.t_total = s_carry[k];
+    }
     if (threadIdx.x == 0) {
         if (use_handle) cudaGraphSetConditional(handle, running ? 1u : 0u);
         if (running_out) *running_out = running;
@@ -603,6 +704,19 @@ __global__ void k_scan_add(uint32_t *out, const uint32_t *__restrict__ block_sum
     if (i == 0) *out_total = *total;
 }
 
+// Terminal adjacency as bit rows (needed when terminal sources run on the
+// tensor cores): bits[l][x] has bit y for every CSR edge (x, l, y).
+__global__ void k_csr_to_bits(const uint32_t *__restrict__ off, const uint32_t *__restrict__ col, size_t rows,
+                              uint32_t W, uint64_t *bits) {
+    for (size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (size_t)gridDim.x * blockDim.x) {
+        uint64_t *row = bits + r * W;
+        for (uint32_t e = off[r]; e < off[r + 1]; ++e) {
+            const uint32_t y = col[e];
+            row[y >> 6] |= 1ull << (y & 63u);
+        }
+    }
+}
+
 // --------------------------------------------------------------------------
 // Result helpers.
 // --------------------------------------------------------------------------
@@ -637,35 +751,46 @@ int vpl_for_words(uint32_t W) {
     return 0;
 }
 
-cudaError_t launch_gather(int vpl, const GItem *items, uint32_t n_items, const SrcDesc *srcs, cudaStream_t st) {
+cudaError_t launch_gather(int vpl, bool nt, const GItem *items, uint32_t n_items, const SrcDesc *srcs,
+                          const ExecTables &T, int cls, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
+#define CFPQ_GATHER(V)                                                                         \
+    if (nt) k_gather<V, true><<<n_items, 256, 0, st>>>(items, srcs, T, cls);                   \
+    else k_gather<V, false><<<n_items, 256, 0, st>>>(items, srcs, T, cls);
     switch (vpl) {
-        case 1: k_gather<1><<<n_items, 256, 0, st>>>(items, srcs); break;
-        case 2: k_gather<2><<<n_items, 256, 0, st>>>(items, srcs); break;
-        case 4: k_gather<4><<<n_items, 256, 0, st>>>(items, srcs); break;
-        case 8: k_gather<8><<<n_items, 256, 0, st>>>(items, srcs); break;
-        case 16: k_gather<16><<<n_items, 256, 0, st>>>(items, srcs); break;
+        case 1: CFPQ_GATHER(1) break;
+        case 2: CFPQ_GATHER(2) break;
+        case 4: CFPQ_GATHER(4) break;
+        case 8: CFPQ_GATHER(8) break;
+        case 16: CFPQ_GATHER(16) break;
         default: return cudaErrorInvalidValue;
     }
+#undef CFPQ_GATHER
     return cudaGetLastError();
 }
 
-cudaError_t launch_extract(int vpl, const XItem *items, uint32_t n_items, const FDesc *fds, cudaStream_t st) {
+cudaError_t launch_extract(int vpl, const XItem *items, uint32_t n_items, const FDesc *fds, const ExecTables &T,
+                           int cls, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     switch (vpl) {
-        case 1: k_extract<1><<<n_items, 256, 0, st>>>(items, fds); break;
-        case 2: k_extract<2><<<n_items, 256, 0, st>>>(items, fds); break;
-        case 4: k_extract<4><<<n_items, 256, 0, st>>>(items, fds); break;
-        case 8: k_extract<8><<<n_items, 256, 0, st>>>(items, fds); break;
-        case 16: k_extract<16><<<n_items, 256, 0, st>>>(items, fds); break;
+        case 1: k_extract<1><<<n_items, 256, 0, st>>>(items, fds, T, cls); break;
+        case 2: k_extract<2><<<n_items, 256, 0, st>>>(items, fds, T, cls); break;
+        case 4: k_extract<4><<<n_items, 256, 0, st>>>(items, fds, T, cls); break;
+        case 8: k_extract<8><<<n_items, 256, 0, st>>>(items, fds, T, cls); break;
+        case 16: k_extract<16><<<n_items, 256, 0, st>>>(items, fds, T, cls); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGraphConditionalHandle h, int use_handle,
-                           int *running_out, cudaStream_t st) {
-    k_control<<<1, 256, 0, st>>>(ctls, nq, mirror, h, use_handle, running_out);
+                           int *running_out, const ExecTables &T, int advance, cudaStream_t st) {
+    // one thread per query up to 1024 (a single warp for small batches keeps
+    // the per-pass scans to shuffles)
+    uint32_t threads = ((nq + 31u) / 32u) * 32u;
+    if (threads < 32u) threads = 32u;
+    if (threads > 1024u) threads = 1024u;
+    k_control<<<1, threads, 0, st>>>(ctls, nq, mirror, h, use_handle, running_out, T, advance);
     return cudaGetLastError();
 }
 
@@ -729,6 +854,12 @@ cudaError_t launch_stage_compact(const uint32_t *off, const uint32_t *col, const
                                  size_t rows, cudaStream_t st) {
     if (rows == 0) return cudaSuccess;
     k_stage_compact<<<grid_for(rows, 128), 128, 0, st>>>(off, col, uoff, ucol, rows);
+    return cudaGetLastError();
+}
+cudaError_t launch_csr_to_bits(const uint32_t *off, const uint32_t *col, size_t rows, uint32_t W, uint64_t *bits,
+                               cudaStream_t st) {
+    if (rows == 0) return cudaSuccess;
+    k_csr_to_bits<<<grid_for(rows, 128), 128, 0, st>>>(off, col, rows, W, bits);
     return cudaGetLastError();
 }
 cudaError_t launch_popcount(const uint64_t *p, size_t nwords, unsigned long long *out, cudaStream_t st) {

@@ -114,6 +114,7 @@ int cfpq_submit(cfpq_server *s, const cfpq_rsm *rsm, uint64_t *ticket) {
     try {
         cfpq_server::Job j;
         j.q.reset(new QueryDev());
+        j.q->closure_mode = s->opt.closure_mode == CFPQ_CLOSURE_TC_FP8 ? CFPQ_CLOSURE_TC_FP8 : CFPQ_CLOSURE_BITPACKED;
         std::string e;
         int rc = copy_rsm(rsm, &j.q->rsm, &e);
         if (rc) return sfail(s, rc, e);
@@ -168,6 +169,7 @@ int cfpq_server_step(cfpq_server *s, uint32_t *n_running, uint32_t *n_waiting) {
                 for (uint64_t t : s->running) s->exec.qs.push_back(s->jobs[t].q.get());
                 int rc = s->exec.assemble(&s->A, s->stream, &e);
                 if (rc) return sfail(s, rc, e);
+                if (s->exec.enqueue_lists(s->stream)) return sfail(s, CFPQ_ERR_CUDA, "list launch failed");
                 s->exec_dirty = false;
             }
             for (uint32_t p = 0; p < kPassesPerStep; ++p)

@@ -154,29 +154,6 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 
 }  // namespace tc
 
-// One dense product job: out |= A * B over the square n x n state block,
-// with A rows optionally valid only in one iteration (A2 semantics) and B
-// rows taking part only when their stamp is >= thr.
-struct TcJob {
-    uint64_t *out;
-    uint32_t *out_stamp;
-    uint32_t *out_last;
-    const uint64_t *A;
-    const uint32_t *a_it;      // if set: A row x is used only when a_it[x] == iter
-    const uint64_t *B;
-    const uint32_t *b_stamp;   // stamps of B rows (null: all rows)
-    QCtl *ctl;                 // null: standalone product (iter = 0, thr = 0, g = 0)
-    uint32_t n, W;
-    uint32_t ident;            // also OR the A rows themselves into out (product edge u == t)
-    uint32_t chan;             // 1, 2 or 4 (see src_channels); 0 = always, thr 0
-    uint32_t level, same_level;
-    const uint32_t *box_new_it;
-    const uint32_t *rlast;
-    uint32_t tiles_m, tiles_n;  // tiles of this job
-    uint32_t tile0;             // first global tile index of this job
-    uint32_t pad;
-};
-
 // Decide whether the job takes part in this pass and with which threshold.
 __device__ __forceinline__ bool tc_job_active(const TcJob &j, uint32_t *thr, uint32_t *iter, uint32_t *g) {
     if (!j.ctl) {
@@ -212,7 +189,7 @@ __device__ __forceinline__ bool tc_job_active(const TcJob &j, uint32_t *thr, uin
 }
 
 __global__ void __launch_bounds__(tc::kThreads, 1)
-    k_tc_product(const TcJob *__restrict__ jobs, uint32_t n_jobs, int *err_flag) {
+    k_tc_product(const TcJob *__restrict__ jobs, ExecTables T, int *err_flag) {
     constexpr bool INT8 = false;
     using namespace tc;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -221,196 +198,227 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     __shared__ uint32_t s_changed_rows;
     __shared__ uint8_t s_row_changed[kBM];
 
-    // locate the job of this tile
-    uint32_t jb = 0;
-    {
-        uint32_t lo = 0, hi = n_jobs;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) / 2;
-            if (jobs[mid].tile0 <= blockIdx.x) lo = mid;
-            else hi = mid;
-        }
-        jb = lo;
-    }
-    const TcJob &J = jobs[jb];
-    uint32_t thr, iter, g;
-    if (!tc_job_active(J, &thr, &iter, &g)) return;
-    const uint32_t t = blockIdx.x - J.tile0;
-    if (t >= J.tiles_m * J.tiles_n) return;
-    const uint32_t m0 = (t / J.tiles_n) * kBM, n0 = (t % J.tiles_n) * kBN;
-    const uint32_t n = J.n, W = J.W;
+    const uint32_t total = *T.t_total;
+    if (blockIdx.x >= total) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t one = INT8 ? 0x01u : 0x38u;
-
     unsigned char *stage[2] = {smem_raw, smem_raw + kStageBytes};
     if (warp == 0) tmem_alloc(&tmem_base, kTmemCols);
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
-        s_changed_rows = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (tid < kBM) s_row_changed[tid] = 0;
     tc_before();
     __syncthreads();
     tc_after();
     const uint32_t tmem = tmem_base;
-
     constexpr uint32_t idesc = INT8 ? make_idesc(2, kBM, kBN) : make_idesc(1, kBM, kBN);
-    bool inflight[2] = {false, false};
     uint32_t parity[2] = {0u, 0u};
-    bool started = false, timed_out = false;
-    int buf = 0;
-    const uint32_t ksteps = (n + kBK - 1) / kBK;
+    bool timed_out = false;
 
-    for (uint32_t ks = 0; ks < ksteps && !timed_out; ++ks) {
-        const uint32_t k0 = ks * kBK;  // bits of A's columns / B's rows
-        // ---- load this stage's bits into registers ----
-        // A: 256 threads x (half a row: 64 bits) of the 128 x 128-bit tile
-        const uint32_t ar = (uint32_t)tid >> 1, ah = (uint32_t)tid & 1u;
-        uint64_t abits = 0;
-        {
-            const uint32_t x = m0 + ar, w = (k0 >> 6) + ah;
-            if (x < n && w < W && (!J.a_it || J.a_it[x] == iter)) abits = J.A[(size_t)x * W + w];
+    for (uint32_t li = blockIdx.x; li < total && !timed_out; li += gridDim.x) {
+        // live tile li -> query -> job (tile0 is relative to the query's level group)
+        const uint32_t q = find_owner(T.t_pre, T.nq, li);
+        const uint32_t ti = li - T.t_pre[q];
+        uint32_t lo = T.t_job_beg[q], hi = T.t_job_end[q];
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (jobs[mid].tile0 <= ti) lo = mid;
+            else hi = mid;
         }
-        // B: 32 blocks of 32 (rows) x 32 (columns) bits; warp w owns 4 blocks:
-        // rows k0 + 32 * (w / 2) + lane, columns n0 + 128 * (w % 2) + 32 * b
-        uint32_t bword[4];
-        {
-            const uint32_t y = k0 + 32u * ((uint32_t)warp >> 1) + (uint32_t)lane;
-            const bool rok = y < n && (!J.b_stamp || thr == 0u || J.b_stamp[y] >= thr);
+        const TcJob &J = jobs[lo];
+        uint32_t thr, iter, g;
+        if (!tc_job_active(J, &thr, &iter, &g)) continue;
+        const uint32_t t = ti - J.tile0;
+        if (t >= J.tiles_m * J.tiles_n) continue;
+        const uint32_t m0 = (t / J.tiles_n) * kBM, n0 = (t % J.tiles_n) * kBN;
+        const uint32_t n = J.n, W = J.W;
+        if (tid < kBM) s_row_changed[tid] = 0;
+        if (tid == 0) s_changed_rows = 0;
+        bool inflight[2] = {false, false};
+        bool started = false;
+        int buf = 0;
+        const uint32_t ksteps = J.B ? (n + kBK - 1) / kBK : 0u;
+
+        for (uint32_t ks = 0; ks < ksteps && !timed_out; ++ks) {
+            const uint32_t k0 = ks * kBK;  // bits of A's columns / B's rows
+            // A: 256 threads x (half a row: 64 bits) of the 128 x 128-bit tile
+            const uint32_t ar = (uint32_t)tid >> 1, ah = (uint32_t)tid & 1u;
+            uint64_t abits = 0;
+            {
+                const uint32_t x = m0 + ar, w = (k0 >> 6) + ah;
+                if (x < n && w < W && (!J.a_it || J.a_it[x] == iter)) abits = J.A[(size_t)x * W + w];
+            }
+            // B: 32 blocks of 32 rows x 32 columns; warp w owns 4 of them:
+            // rows k0 + 32 * (w / 2) + lane, columns n0 + 128 * (w % 2) + 32 * b
+            uint32_t bword[4];
+            {
+                const uint32_t y = k0 + 32u * ((uint32_t)warp >> 1) + (uint32_t)lane;
+                const bool rok = y < n && (!J.b_stamp || thr == 0u || J.b_stamp[y] >= thr);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const uint32_t zc = n0 + 128u * ((uint32_t)warp & 1u) + 32u * (uint32_t)b;
+                    uint32_t v = 0;
+                    if (rok && zc < (W << 6)) {
+                        const uint64_t wv = J.B[(size_t)y * W + (zc >> 6)];
+                        v = (uint32_t)(wv >> (zc & 63u));
+                    }
+                    bword[b] = v;
+                }
+            }
+            const int anyA = __syncthreads_or(abits != 0ull);
+            const int anyB = __syncthreads_or((bword[0] | bword[1] | bword[2] | bword[3]) != 0u);
+            if (!anyA || !anyB) continue;  // dirty-tile skip: this stage adds nothing
+
+            if (inflight[buf]) {  // the buffer must be free: wait for the MMAs that read it
+                if (!mbar_wait(&mbar[buf], parity[buf])) timed_out = true;
+                parity[buf] ^= 1u;
+                inflight[buf] = false;
+            }
+            if (__syncthreads_or(timed_out)) { timed_out = true; break; }
+            unsigned char *sa = stage[buf], *sb = stage[buf] + kStageA;
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                const uint32_t kg = ah * 4u + (uint32_t)qq;
+                *reinterpret_cast<uint4 *>(sa + core_off(ar, kg)) =
+                    expand16((uint32_t)(abits >> (16 * qq)) & 0xFFFFu, one);
+            }
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const uint32_t zc = n0 + 128u * ((uint32_t)warp & 1u) + 32u * (uint32_t)b;  // first column
-                uint32_t v = 0;
-                if (rok && zc < (W << 6)) {
-                    const uint64_t wv = J.B[(size_t)y * W + (zc >> 6)];
-                    v = (uint32_t)(wv >> (zc & 63u));
+                const uint32_t col = transpose32(bword[b], lane);  // bit i = row 32 * (warp/2) + i
+                const uint32_t z = 128u * ((uint32_t)warp & 1u) + 32u * (uint32_t)b + (uint32_t)lane;
+                const uint32_t kg = 2u * ((uint32_t)warp >> 1);
+                *reinterpret_cast<uint4 *>(sb + core_off(z, kg)) = expand16(col & 0xFFFFu, one);
+                *reinterpret_cast<uint4 *>(sb + core_off(z, kg + 1u)) = expand16(col >> 16, one);
+            }
+            fence_async_smem();
+            tc_before();
+            __syncthreads();
+            tc_after();
+            if (tid == 0) {
+                const uint32_t abase = smem_u32(sa), bbase = smem_u32(sb);
+#pragma unroll
+                for (int kk = 0; kk < kBK / 32; ++kk) {
+                    const uint64_t ad = make_desc(abase + (uint32_t)kk * 256u, 128u, kKG * 128u);
+                    const uint64_t bd = make_desc(bbase + (uint32_t)kk * 256u, 128u, kKG * 128u);
+                    tc::mma(INT8, tmem, ad, bd, idesc, (started || kk > 0) ? 1u : 0u);
                 }
-                bword[b] = v;
+                mma_commit(&mbar[buf]);
+            }
+            started = true;
+            inflight[buf] = true;
+            buf ^= 1;
+        }
+        for (int b = 0; b < 2; ++b) {  // drain
+            if (inflight[b]) {
+                if (!mbar_wait(&mbar[b], parity[b])) timed_out = true;
+                parity[b] ^= 1u;
+                inflight[b] = false;
             }
         }
-        const int anyA = __syncthreads_or(abits != 0ull);
-        const int anyB = __syncthreads_or((bword[0] | bword[1] | bword[2] | bword[3]) != 0u);
-        if (!anyA || !anyB) continue;  // dirty-tile skip: this stage adds nothing
-
-        // ---- the buffer must be free: wait for the MMAs that read it ----
-        if (inflight[buf]) {
-            if (!mbar_wait(&mbar[buf], parity[buf])) timed_out = true;
-            parity[buf] ^= 1u;
-            inflight[buf] = false;
-        }
-        if (__syncthreads_or(timed_out)) { timed_out = true; break; }
-        unsigned char *sa = stage[buf], *sb = stage[buf] + kStageA;
-        // ---- expand A: row ar, k bits [64 ah, 64 ah + 64) -> 4 core-matrix rows ----
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t kg = ah * 4u + (uint32_t)q;
-            *reinterpret_cast<uint4 *>(sa + core_off(ar, kg)) = expand16((uint32_t)(abits >> (16 * q)) & 0xFFFFu, one);
-        }
-        // ---- expand B transposed: column z gets the bits of rows y as bytes ----
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const uint32_t col = transpose32(bword[b], lane);  // bit i = row (32 * (warp/2) + i)
-            const uint32_t z = 128u * ((uint32_t)warp & 1u) + 32u * (uint32_t)b + (uint32_t)lane;
-            const uint32_t kg = 2u * ((uint32_t)warp >> 1);
-            *reinterpret_cast<uint4 *>(sb + core_off(z, kg)) = expand16(col & 0xFFFFu, one);
-            *reinterpret_cast<uint4 *>(sb + core_off(z, kg + 1u)) = expand16(col >> 16, one);
-        }
-        fence_async_smem();
         tc_before();
         __syncthreads();
         tc_after();
+        if (__syncthreads_or(timed_out)) {
+            timed_out = true;
+            break;
+        }
+        // epilogue: warps 0-3 columns [0,128), warps 4-7 columns [128,256)
+        if (started || J.ident) {
+            const uint32_t quarter = (uint32_t)warp & 3u, half = (uint32_t)warp >> 2;
+            const uint32_t r = quarter * 32u + (uint32_t)lane;  // tile row = TMEM lane
+            const uint32_t x = m0 + r;
+            uint32_t mask[4] = {0u, 0u, 0u, 0u};
+            if (started) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    uint32_t v[32];
+                    const uint32_t col = half * 128u + 32u * (uint32_t)c;
+                    tc::tmem_ld32(tmem + ((quarter * 32u) << 16) + col, v);
+                    uint32_t mbits = 0u;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) mbits |= (v[i] != 0u ? 1u : 0u) << i;
+                    mask[c] = mbits;
+                }
+            }
+            if (x < n) {
+                const uint32_t w0 = (n0 + half * 128u) >> 6;
+                bool ch = false;
+#pragma unroll
+                for (int wq = 0; wq < 2; ++wq) {
+                    const uint32_t w = w0 + (uint32_t)wq;
+                    if (w >= W) continue;
+                    uint64_t add = (uint64_t)mask[2 * wq] | ((uint64_t)mask[2 * wq + 1] << 32);
+                    if (J.ident && (!J.a_it || J.a_it[x] == iter)) add |= J.A[(size_t)x * W + w];
+                    if (!add) continue;
+                    // several jobs (sources) of one output block may share a launch
+                    const uint64_t old = atomicOr(reinterpret_cast<unsigned long long *>(J.out + (size_t)x * W + w),
+                                                  (unsigned long long)add);
+                    if (add & ~old) ch = true;
+                }
+                if (ch) s_row_changed[r] = 1;
+            }
+        }
+        tc_before();
+        __syncthreads();
+        tc_after();
+        if (tid < kBM && s_row_changed[tid]) {
+            if (J.out_stamp) J.out_stamp[m0 + tid] = g;
+            atomicAdd(&s_changed_rows, 1u);
+        }
+        __syncthreads();
         if (tid == 0) {
-            const uint32_t abase = smem_u32(sa), bbase = smem_u32(sb);
-#pragma unroll
-            for (int kk = 0; kk < kBK / 32; ++kk) {
-                const uint64_t ad = make_desc(abase + (uint32_t)kk * 256u, 128u, kKG * 128u);
-                const uint64_t bd = make_desc(bbase + (uint32_t)kk * 256u, 128u, kKG * 128u);
-                tc::mma(INT8, tmem, ad, bd, idesc, (started || kk > 0) ? 1u : 0u);
+            if (s_changed_rows) {
+                if (J.out_last) *J.out_last = g;
+                if (J.ctl) atomicAdd(&J.ctl->changed_rows, (unsigned long long)s_changed_rows);
             }
-            mma_commit(&mbar[buf]);
+            if (J.ctl && started) atomicAdd(&J.ctl->tile_mmas, 1ull);
         }
-        started = true;
-        inflight[buf] = true;
-        buf ^= 1;
+        __syncthreads();
     }
-    // ---- drain ----
-    for (int b = 0; b < 2; ++b) {
-        if (inflight[b]) {
-            if (!mbar_wait(&mbar[b], parity[b])) timed_out = true;
-            parity[b] ^= 1u;
-            inflight[b] = false;
-        }
-    }
+    if (timed_out && tid == 0) atomicOr(err_flag, 1);
     tc_before();
     __syncthreads();
     tc_after();
-    const bool bad = __syncthreads_or(timed_out) != 0;
-    if (bad && tid == 0) atomicOr(err_flag, 1);
-
-    // ---- epilogue: warps 0-3 columns [0,128), warps 4-7 columns [128,256) ----
-    if (!bad && (started || J.ident)) {
-        const uint32_t quarter = (uint32_t)warp & 3u, half = (uint32_t)warp >> 2;
-        const uint32_t r = quarter * 32u + (uint32_t)lane;  // tile row = TMEM lane
-        const uint32_t x = m0 + r;
-        uint32_t mask[4] = {0u, 0u, 0u, 0u};
-        if (started) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                uint32_t v[32];
-                const uint32_t col = half * 128u + 32u * (uint32_t)c;
-                tc::tmem_ld32(tmem + ((quarter * 32u) << 16) + col, v);
-                uint32_t mbits = 0u;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) mbits |= (v[i] != 0u ? 1u : 0u) << i;
-                mask[c] = mbits;
-            }
-        }
-        if (x < n) {
-            const uint32_t w0 = (n0 + half * 128u) >> 6;  // first output word of this half
-            bool ch = false;
-#pragma unroll
-            for (int wq = 0; wq < 2; ++wq) {
-                const uint32_t w = w0 + (uint32_t)wq;
-                if (w >= W) continue;
-                uint64_t add = (uint64_t)mask[2 * wq] | ((uint64_t)mask[2 * wq + 1] << 32);
-                if (J.ident && (!J.a_it || J.a_it[x] == iter)) add |= J.A[(size_t)x * W + w];
-                if (!add) continue;
-                // several jobs (sources) of one output block may share a launch
-                const uint64_t old =
-                    atomicOr(reinterpret_cast<unsigned long long *>(J.out + (size_t)x * W + w), (unsigned long long)add);
-                if (add & ~old) ch = true;
-            }
-            if (ch) s_row_changed[r] = 1;
-        }
-    }
-    tc_before();
-    __syncthreads();
-    tc_after();
-    if (tid < kBM && s_row_changed[tid]) {
-        if (J.out_stamp) J.out_stamp[m0 + tid] = g;
-        atomicAdd(&s_changed_rows, 1u);
-    }
-    __syncthreads();
-    if (tid == 0 && s_changed_rows) {
-        if (J.out_last) *J.out_last = g;
-        if (J.ctl) atomicAdd(&J.ctl->changed_rows, (unsigned long long)s_changed_rows);
-    }
-    if (tid == 0 && J.ctl && started) atomicAdd(&J.ctl->tile_mmas, 1ull);
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
 int tc_smem_bytes() { return 2 * tc::kStageBytes; }
 
-cudaError_t launch_tc_product(bool int8, const TcJob *jobs, uint32_t n_jobs, uint32_t n_tiles, int *err_flag,
+// Persistent launch: at most two CTAs per SM (96 KiB of shared memory and 256
+// TMEM columns each), walking the live tiles of the pass.
+static int g_tc_sms[64];
+
+// Set the kernel's shared-memory limit and record the SM count (call outside
+// any stream capture).
+cudaError_t prepare_tc_launch() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (g_tc_sms[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_tc_product, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes());
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    g_tc_sms[dev] = sms;
+    return cudaSuccess;
+}
+
+cudaError_t launch_tc_product(bool int8, const TcJob *jobs, uint32_t max_tiles, const ExecTables &T, int *err_flag,
                               cudaStream_t st) {
-    if (n_tiles == 0) return cudaSuccess;
+    if (max_tiles == 0) return cudaSuccess;
     if (int8) return cudaErrorNotSupported;
     const int smem = tc_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k_tc_product, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    k_tc_product<<<n_tiles, tc::kThreads, smem, st>>>(jobs, n_jobs, err_flag);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int sms = (dev >= 0 && dev < 64 && g_tc_sms[dev]) ? g_tc_sms[dev] : 0;
+    if (!sms) return cudaErrorNotReady;  // prepare_tc_launch was not called
+    uint32_t grid = (uint32_t)sms * 2u;
+    if (max_tiles < grid) grid = max_tiles;
+    k_tc_product<<<grid, tc::kThreads, smem, st>>>(jobs, T, err_flag);
     return cudaGetLastError();
 }
 
@@ -434,6 +442,7 @@ extern "C" int cfpq_tc_bool_product(uint32_t n, int use_int8, const uint64_t *a,
     uint64_t *dA = nullptr, *dB = nullptr, *dC = nullptr;
     TcJob *dJ = nullptr;
     int *dErr = nullptr;
+    uint32_t *dTab = nullptr;
     int rc = CFPQ_OK;
     auto ck = [&](cudaError_t e) {
         if (e != cudaSuccess && rc == CFPQ_OK) rc = CFPQ_ERR_CUDA;
@@ -441,7 +450,7 @@ extern "C" int cfpq_tc_bool_product(uint32_t n, int use_int8, const uint64_t *a,
     };
     if (ck(cudaMallocAsync((void **)&dA, bytes, st)) && ck(cudaMallocAsync((void **)&dB, bytes, st)) &&
         ck(cudaMallocAsync((void **)&dC, bytes, st)) && ck(cudaMallocAsync((void **)&dJ, sizeof(TcJob), st)) &&
-        ck(cudaMallocAsync((void **)&dErr, sizeof(int), st))) {
+        ck(cudaMallocAsync((void **)&dErr, sizeof(int), st)) && ck(cudaMallocAsync((void **)&dTab, 16, st))) {
         ck(cudaMemsetAsync(dA, 0, bytes, st));
         ck(cudaMemsetAsync(dB, 0, bytes, st));
         ck(cudaMemsetAsync(dC, 0, bytes, st));
@@ -459,7 +468,18 @@ extern "C" int cfpq_tc_bool_product(uint32_t n, int use_int8, const uint64_t *a,
         j.tiles_n = (n_pad + 255) / 256;
         j.tile0 = 0;
         ck(cudaMemcpyAsync(dJ, &j, sizeof(j), cudaMemcpyHostToDevice, st));
-        ck(launch_tc_product(use_int8 != 0, dJ, 1, j.tiles_m * j.tiles_n, dErr, st));
+        // one query, one live job: t_total, t_pre, t_job_beg, t_job_end
+        const uint32_t tab[4] = {j.tiles_m * j.tiles_n, 0u, 0u, 1u};
+        ck(cudaMemcpyAsync(dTab, tab, sizeof(tab), cudaMemcpyHostToDevice, st));
+        ExecTables T;
+        memset(&T, 0, sizeof(T));
+        T.nq = 1;
+        T.t_total = dTab;
+        T.t_pre = dTab + 1;
+        T.t_job_beg = dTab + 2;
+        T.t_job_end = dTab + 3;
+        ck(prepare_tc_launch());
+        ck(launch_tc_product(use_int8 != 0, dJ, tab[0], T, dErr, st));
         int herr = 0;
         ck(cudaMemcpyAsync(&herr, dErr, sizeof(int), cudaMemcpyDeviceToHost, st));
         ck(cudaMemcpy2DAsync(c, wn * 8, dC, W * 8, wn * 8, n, cudaMemcpyDeviceToHost, st));
@@ -471,6 +491,7 @@ extern "C" int cfpq_tc_bool_product(uint32_t n, int use_int8, const uint64_t *a,
     if (dC) cudaFreeAsync(dC, st);
     if (dJ) cudaFreeAsync(dJ, st);
     if (dErr) cudaFreeAsync(dErr, st);
+    if (dTab) cudaFreeAsync(dTab, st);
     cudaStreamSynchronize(st);
     return rc;
 }
