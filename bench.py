@@ -11,6 +11,14 @@ ranks; ``e2e`` is the same metric through the public C ABI with host buffers
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun (N > 1) every rank runs its own query (independent queries,
 no collective on the data path) and rank 0 prints the line.
+
+The other workloads print their own line with ``--workload``:
+  cycles   two coprime cycles (126 vertices, S -> a S b | a b): latency,
+           microseconds per fixpoint iteration;
+  dyck     Dyck-4 on a Zipf graph (n = 65536 by default): closure Bool-GOPS,
+           bit-packed and tensor-core closure modes;
+  batched  512 (graph, RSM) queries in one batch vs one at a time;
+  served   resident 32768-vertex graph, Poisson arrivals, p50/p99 latency.
 """
 from __future__ import annotations
 
@@ -126,8 +134,10 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    from paper_2103_14688_gb300 import shard
     n, deg = args.n, 8
-    g, r = W.rpq_abc(n=n, out_deg=deg, seed=W.SEED_BASE + 2 + rank)
+    # independent queries per rank (weak scaling; no collective on the data path)
+    g, r = W.rpq_abc(n=n, out_deg=deg, seed=shard.rank_seed(W.SEED_BASE + 2, rank))
     m = g.m
     d_src = torch.from_numpy(g.src.astype(np.int32)).to(dev)
     d_lbl = torch.from_numpy(g.lbl.astype(np.int32)).to(dev)
@@ -163,11 +173,7 @@ def run_gpu(args):
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     step_ms = float(np.mean(times))
-    total_ms = float(np.sum(times))
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = shard.max_over_ranks(float(np.sum(times)), dist, dev)
     value = ws * args.steps / (total_ms / 1000.0)
     stats = last
 
@@ -176,12 +182,15 @@ def run_gpu(args):
     bits = ctx.reachable_bits(0)
     assert bits.diagonal().all()
 
-    # closure Bool-GOPS in the accounting of Theorem 2: one length-|Q|n vector
-    # operation per M3 edge and per closure bit, W = (nnz(M3) + nnz(C3)) * |Q|n
+    # closure Bool-GOPS: executed = OR-AND operations of the source-row ORs
+    # (one per bit of a padded row); paper accounting (Theorem 2) = one
+    # length-|Q|n vector operation per M3 edge and per closure bit,
+    # W = (nnz(M3) + nnz(C3)) * |Q|n, an equivalent-work count far above it
     cbits, m3bits = ctx.count_index()
     Nq = r.n_states * n
     work = (cbits + m3bits) * Nq
     gops = work / (step_ms / 1000.0) / 1e9
+    exec_gops = stats.row_ors * (stats.row_bytes * 8) / (step_ms / 1000.0) / 1e9
 
     # end to end through the ABI: host (pinned) edge list in, answer bits out
     h_src = torch.from_numpy(g.src.astype(np.int32)).pin_memory()
@@ -214,11 +223,7 @@ def run_gpu(args):
         step_e2e()
         e_times.append((time.perf_counter() - t0) * 1000.0)
     barrier()
-    e_total = float(np.sum(e_times))
-    if dist:
-        t = torch.tensor([e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_total = float(t.item())
+    e_total = shard.max_over_ranks(float(np.sum(e_times)), dist, dev)
     e2e_value = ws * args.steps / (e_total / 1000.0)
     e2e_equal = bool((out_bits.numpy().view(np.uint64).reshape(n, wn) == ctx.reachable_words(0)).all())
 
@@ -239,6 +244,26 @@ def run_gpu(args):
     staging_kernels = 10
     gpu_launches = args.steps * (stats.gpu_launches + staging_kernels)
 
+    # the same query with the closure products on the tensor cores (0/1 FP8),
+    # for comparison: bit-exact, timed once after a warm-up run
+    modes = None
+    if not args.no_extras:
+        tctx = cfpq.Context(device=local, closure_mode=cfpq.CFPQ_CLOSURE_TC_FP8)
+        tctx.load_rsm(r)
+        tctx.load_graph_device(n, 3, d_src, d_lbl, d_dst)
+        tctx.run()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        tctx.load_graph_device(n, 3, d_src, d_lbl, d_dst)
+        tst = tctx.run()
+        t1.record(stream)
+        t1.synchronize()
+        modes = {"bitpacked_ms_per_query": step_ms, "tc_fp8_ms_per_query": t0.elapsed_time(t1),
+                 "tc_fp8_tiles": tst.tile_mmas,
+                 "tc_equals_bitpacked": bool((tctx.reachable_words(0) == ctx.reachable_words(0)).all())}
+        tctx.close()
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -250,12 +275,14 @@ def run_gpu(args):
                      "frac": achieved / peak, "traffic": traffic, "kernel": "cfpq::k_gather<2>",
                      "peak_source": f"{peak_kind} hbm_gbs", "launches_timed": launches,
                      "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_s * 1e3},
-        "closure_bool_gops": gops,
+        "closure_bool_gops": exec_gops,
+        "closure_bool_gops_paper_accounting": gops,
         "closure_work_W": work,
         "index": {"closure_bits": cbits, "m3_bits": m3bits, "answer_pairs": int(bits.sum()),
                   "iterations": stats.iterations, "passes": stats.rounds, "blocks": stats.closure_blocks,
                   "row_ors": stats.row_ors, "rows_changed": stats.rows_changed},
         "gpu_launches": gpu_launches,
+        "closure_modes": modes,
         "clocks": clk,
         "wall_s": wall,
     }
@@ -301,6 +328,122 @@ def cpu_baseline(g, r, n_sources):
                       f"value = sampled fraction / time"}
 
 
+def _ctx_time(ctx, stream, fn):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
+def run_other(args):
+    """The other configurations, one JSON line each (not the default line)."""
+    import torch
+    from paper_2103_14688_gb300 import cfpq
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    line = {"workload": args.workload, "n_gpus": 1, "data": "synthetic"}
+    if args.workload == "cycles":
+        g, r = W.two_cycles(63, 64)
+        ctx = cfpq.Context()
+        ctx.load_graph(g)
+        ctx.load_rsm(r)
+        ctx.run()
+        ts = []
+        for _ in range(max(1, args.steps)):
+            st, ms = _ctx_time(ctx, stream, ctx.run)
+            ts.append(ms)
+        ms = float(np.median(ts))
+        ans = ctx.reachable_bits(0)
+        line.update({"metric": "time per query (two coprime cycles, 4032-pair closed form)", "unit": "ms",
+                     "value": ms, "higher_is_better": False, "iterations": st.iterations,
+                     "us_per_iteration": 1000.0 * ms / st.iterations, "passes": st.rounds,
+                     "pairs": int(ans.sum()), "closed_form_pairs": 4032})
+    elif args.workload == "dyck":
+        g, r = W.dyck_zipf(args.dyck_n)
+        res = {}
+        for mode, name in ((cfpq.CFPQ_CLOSURE_BITPACKED, "bitpacked"), (cfpq.CFPQ_CLOSURE_TC_FP8, "tc_fp8")):
+            if name == "tc_fp8" and args.no_extras:
+                continue
+            ctx = cfpq.Context(closure_mode=mode)
+            ctx.load_graph(g)
+            ctx.load_rsm(r)
+            st, ms = _ctx_time(ctx, stream, ctx.run)
+            res[name] = {"ms": ms, "iterations": st.iterations, "passes": st.rounds, "row_ors": st.row_ors,
+                         "tile_products": st.tile_mmas, "pairs": ctx.count_reachable(0),
+                         "executed_bool_gops": st.row_ors * st.row_bytes * 8 / (ms / 1e3) / 1e9,
+                         "device_gb": st.device_bytes / 1e9}
+            res[name]["words"] = ctx.reachable_words(0)
+            ctx.close()
+        same = None
+        if "tc_fp8" in res:
+            same = bool((res["tc_fp8"].pop("words") == res["bitpacked"]["words"]).all())
+        res["bitpacked"].pop("words", None)
+        line.update({"metric": "Dyck-4 index creation time", "unit": "ms", "value": res["bitpacked"]["ms"],
+                     "higher_is_better": False, "n": g.n, "m": g.m, "modes": res, "tc_equals_bitpacked": same})
+    elif args.workload == "batched":
+        qs = W.batched_queries(count=args.batch)
+        ctx = cfpq.Context()
+        ctx.batch_run(qs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        per, tot = ctx.batch_run(qs)
+        torch.cuda.synchronize()
+        bt = time.perf_counter() - t0
+        bits = [ctx.batch_reachable_bits(i, 0) for i in range(len(qs))]
+        solo = cfpq.Context()
+        st_s = 0.0
+        mism = 0
+        for i, (g, r) in enumerate(qs):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            solo.load_graph(g)
+            solo.load_rsm(r)
+            solo.run()
+            torch.cuda.synchronize()
+            st_s += time.perf_counter() - a
+            mism += int(not (solo.reachable_bits(0) == bits[i]).all())
+        line.update({"metric": "batched queries/s vs one at a time", "unit": "queries/s",
+                     "value": len(qs) / bt, "higher_is_better": True, "queries": len(qs),
+                     "one_at_a_time_qps": len(qs) / st_s, "speedup": st_s / bt, "mismatches_vs_solo": mism,
+                     "batch_setup_ms": tot.ms_setup, "batch_loop_ms": tot.ms_loop, "passes": tot.rounds,
+                     "device_gb": tot.device_bytes / 1e9})
+    elif args.workload == "served":
+        out = []
+        for lam in [float(x) for x in args.lambdas.split(",")]:
+            wl = W.serving_workload(lam=lam, n_queries=100000, horizon_s=args.horizon)
+            srv = cfpq.Server(wl.graph)
+            t_start = time.perf_counter()
+            pending = list(zip(wl.arrivals.tolist(), wl.choice.tolist()))
+            live, lat, i, waits = {}, [], 0, 0
+            while i < len(pending) or live:
+                now = time.perf_counter() - t_start
+                while i < len(pending) and pending[i][0] <= now:
+                    live[srv.submit(wl.pool[pending[i][1]])] = pending[i][0]
+                    i += 1
+                _, wait = srv.step()
+                waits += wait
+                now = time.perf_counter() - t_start
+                for t in list(live):
+                    if srv.poll(t):
+                        lat.append(now - live.pop(t))
+                        srv.release(t)
+                if not live and i < len(pending):
+                    time.sleep(max(0.0, min(0.001, pending[i][0] - now)))
+            el = time.perf_counter() - t_start
+            lat = np.array(lat)
+            out.append({"lambda": lam, "queries": int(len(lat)), "elapsed_s": el, "qps": len(lat) / el,
+                        "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                        "admission_waits": waits})
+            srv.close()
+        line.update({"metric": "served queries/s and latency", "unit": "queries/s",
+                     "value": max(o["qps"] for o in out), "higher_is_better": True, "n": 32768, "sweep": out})
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The oracle as the reference arm: each step a bounded sample of the
     workload (source vertices), on the host cores."""
@@ -341,11 +484,19 @@ def main():
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--cpu-sources", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="rpq", choices=["rpq", "cycles", "dyck", "batched", "served"])
+    ap.add_argument("--dyck-n", type=int, default=65536)
+    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--lambdas", default="10,30,100,300,1000")
+    ap.add_argument("--horizon", type=float, default=5.0)
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "rpq":
         run_gpu(args)
+    else:
+        run_other(args)
 
 
 if __name__ == "__main__":
