@@ -197,28 +197,43 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                     const uint32_t cnt = e1 - e0;
                     const uint32_t maxcnt = __reduce_max_sync(FULLMASK, cnt);
                     if (maxcnt <= 8u) {
-                        // short adjacency rows (the common case on sparse graphs):
-                        // one edge at a time, no ballot overhead
-                        for (uint32_t e = e0; e < e1; ++e) {
-                            const uint32_t y = d.csr_col[e];
-                            if (use_ident) {
-                                const uint32_t v = y >> 7;
-                                if ((int)(v % lpr) == gl) {
-                                    const int j = (int)(v / lpr);
+                        // short adjacency rows (the common case on sparse
+                        // graphs): no ballot; edges two at a time so that the
+                        // column, stamp and row loads of both are in flight
+                        auto ident_bit = [&](uint32_t y) {
+                            const uint32_t v = y >> 7;
+                            if ((int)(v % lpr) == gl) {
+                                const int j = (int)(v / lpr);
 #pragma unroll
-                                    for (int jj = 0; jj < VPL; ++jj)
-                                        if (jj == j) setbit4(acc[jj], y & 127u);
-                                }
+                                for (int jj = 0; jj < VPL; ++jj)
+                                    if (jj == j) setbit4(acc[jj], y & 127u);
+                            }
+                        };
+                        for (uint32_t e = e0; e < e1; e += 2) {
+                            const bool two = e + 1 < e1;
+                            const uint32_t y0 = d.csr_col[e], y1 = two ? d.csr_col[e + 1] : 0u;
+                            if (use_ident) {
+                                ident_bit(y0);
+                                if (two) ident_bit(y1);
                             }
                             if (d.rblk) {
-                                if (thr && d.rstamp[y] < thr) continue;
-                                const uint4 *r = reinterpret_cast<const uint4 *>(d.rblk + (size_t)y * W);
+                                const bool k0 = !thr || d.rstamp[y0] >= thr;
+                                const bool k1 = two && (!thr || d.rstamp[y1] >= thr);
+                                const uint4 *r0 = reinterpret_cast<const uint4 *>(d.rblk + (size_t)y0 * W);
+                                const uint4 *r1 = reinterpret_cast<const uint4 *>(d.rblk + (size_t)y1 * W);
+                                uint4 a0[VPL], a1[VPL];
 #pragma unroll
                                 for (int j = 0; j < VPL; ++j) {
                                     const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
-                                    if (v < nvec) or4(acc[j], r[v]);
+                                    a0[j] = (k0 && v < nvec) ? r0[v] : make_uint4(0, 0, 0, 0);
+                                    a1[j] = (k1 && v < nvec) ? r1[v] : make_uint4(0, 0, 0, 0);
                                 }
-                                if (gl == 0) ++my_ors;
+#pragma unroll
+                                for (int j = 0; j < VPL; ++j) {
+                                    or4(acc[j], a0[j]);
+                                    or4(acc[j], a1[j]);
+                                }
+                                if (gl == 0) my_ors += (k0 ? 1u : 0u) + (k1 ? 1u : 0u);
                             }
                         }
                     } else {
