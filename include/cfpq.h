@@ -77,6 +77,9 @@ typedef struct {
     uint32_t loop_mode;      /* CFPQ_LOOP_* */
     uint32_t profile;        /* 1 = time every closure-pass launch with CUDA events on the
                                 context's stream (needs CFPQ_LOOP_HOST); see cfpq_run_stats */
+    uint32_t no_single_cta;  /* 0 = a query whose whole device state fits in one SM's shared
+                                memory (rows <= 512 bits) runs its fixpoint inside one CTA;
+                                1 = always use the multi-kernel loop */
     size_t memory_budget;    /* bytes of device memory a context may hold; 0 = no limit */
     cfpq_alloc_fn alloc;     /* NULL = cudaMallocAsync */
     cfpq_free_fn free;

@@ -143,6 +143,11 @@ int ensure_query(cfpq_ctx *ctx) {
         ctx->exec.qs.assign(1, &q);
         rc = ctx->exec.assemble(&ctx->A, ctx->stream, &e);
         if (rc) return fail(ctx, rc, e);
+        q.small_ok = false;
+        if (!ctx->opt.no_single_cta) {
+            rc = q.prepare_small(&ctx->A, ctx->stream, ctx->opt.max_iterations, kDefaultPassCap, &e);
+            if (rc) return fail(ctx, rc, e);
+        }
         ctx->exec_dirty = false;
     }
     return CFPQ_OK;
@@ -284,7 +289,16 @@ int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats) {
     std::vector<QCtl> ctls;
     uint32_t launches = 0, claunch = 0;
     double ms_cl = 0.0;
-    if (int rc = run_executor(ctx, ctx->exec, &ctls, &launches, &ms_cl, &claunch)) return rc;
+    if (ctx->query.small_ok && ctx->opt.loop_mode == CFPQ_LOOP_DEVICE) {
+        // the whole fixpoint in one CTA (state in shared memory)
+        CK(ctx, launch_small_fixpoint(ctx->query.small_desc.p, 1, ctx->query.small_smem, ctx->stream));
+        ctls.resize(1);
+        CK(ctx, cudaMemcpyAsync(ctls.data(), ctx->query.ctl(), sizeof(QCtl), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        launches = 1;
+    } else if (int rc = run_executor(ctx, ctx->exec, &ctls, &launches, &ms_cl, &claunch)) {
+        return rc;
+    }
     ctx->has_result = true;
     const auto t2 = std::chrono::steady_clock::now();
     const double ms = std::chrono::duration<double, std::milli>(t2 - t0).count();

@@ -339,6 +339,53 @@ int QueryDev::prepare(Allocator *A, std::string *err) {
     return CFPQ_OK;
 }
 
+int QueryDev::prepare_small(Allocator *A, cudaStream_t st, uint32_t max_iter, uint32_t max_passes,
+                            std::string *err) {
+    small_ok = false;
+    const uint32_t nblk = (uint32_t)blocks.size();
+    if (W > 8 || closure_mode == CFPQ_CLOSURE_TC_FP8) return CFPQ_OK;
+    const size_t smem = small_smem_bytes(n, W, B, nblk);
+    const size_t limit = small_smem_limit();
+    if (smem == 0 || smem > limit) return CFPQ_OK;
+    // arrays: level, src0, nsrc (per block), f0, nf, nullable (per box), fblocks
+    std::vector<uint32_t> arr;
+    const size_t off_level = arr.size();
+    arr.insert(arr.end(), blk_level.begin(), blk_level.end());
+    const size_t off_src0 = arr.size();
+    arr.insert(arr.end(), blk_src0.begin(), blk_src0.end());
+    const size_t off_nsrc = arr.size();
+    arr.insert(arr.end(), blk_nsrc.begin(), blk_nsrc.end());
+    const size_t off_f0 = arr.size();
+    arr.insert(arr.end(), box_f0.begin(), box_f0.end());
+    const size_t off_nf = arr.size();
+    arr.insert(arr.end(), box_nf.begin(), box_nf.end());
+    const size_t off_null = arr.size();
+    for (uint32_t b = 0; b < B; ++b) arr.push_back(rsm.final_[rsm.box_start[b]] ? 1u : 0u);
+    const size_t off_fb = arr.size();
+    arr.insert(arr.end(), fblocks.begin(), fblocks.end());
+    while (arr.size() % 4) arr.push_back(0);  // 16-byte alignment of the sources that follow
+    const size_t ssz = small_src_size();
+    std::vector<unsigned char> blob(arr.size() * 4 + std::max<size_t>(srcs.size(), 1) * ssz);
+    memcpy(blob.data(), arr.data(), arr.size() * 4);
+    for (size_t k = 0; k < srcs.size(); ++k)
+        fill_small_src(blob.data() + arr.size() * 4 + k * ssz, srcs[k].label_kind, srcs[k].label, srcs[k].ident,
+                       srcs[k].same_level, srcs[k].rblk);
+    if (!small_arrays.ensure(A, blob.size(), err) || !small_desc.ensure(A, small_desc_size(), err))
+        return CFPQ_ERR_OUT_OF_MEMORY;
+    const uint32_t *dev_arr = small_arrays.as<uint32_t>();
+    const SmallSrc *dev_src = reinterpret_cast<const SmallSrc *>(small_arrays.as<unsigned char>() + arr.size() * 4);
+    std::vector<unsigned char> desc(small_desc_size());
+    build_small_desc(desc.data(), n, W, B, nblk, n_levels, cyclic_mask, max_iter, max_passes, dev_arr, dev_src,
+                     off_level, off_src0, off_nsrc, off_f0, off_nf, off_fb, off_null, g->csr_off.as<uint32_t>(),
+                     g->csr_col.as<uint32_t>(), blk_mem.as<uint64_t>(), m2_mem.as<uint64_t>(), ctl());
+    ENG_CK(cudaMemcpyAsync(small_arrays.p, blob.data(), blob.size(), cudaMemcpyHostToDevice, st));
+    ENG_CK(cudaMemcpyAsync(small_desc.p, desc.data(), desc.size(), cudaMemcpyHostToDevice, st));
+    ENG_CK(cudaStreamSynchronize(st));
+    small_smem = smem;
+    small_ok = true;
+    return CFPQ_OK;
+}
+
 int QueryDev::enqueue_init(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes) {
     std::string *err = nullptr;
     const size_t nblk = blocks.size();

@@ -43,6 +43,21 @@ cudaError_t launch_popcount(const uint64_t *p, size_t nwords, unsigned long long
 cudaError_t launch_copy_rows(const uint64_t *const *ptrs, const uint32_t *rows, uint32_t njobs, uint32_t W,
                              uint64_t *out, cudaStream_t st);
 
+// ---- single-CTA fixpoint (cfpq_small.cu) ----
+struct SmallSrc;
+size_t small_smem_bytes(uint32_t n, uint32_t W, uint32_t B, uint32_t nblk);
+size_t small_desc_size();
+size_t small_src_size();
+size_t small_smem_limit();
+cudaError_t launch_small_fixpoint(const void *descs, uint32_t count, size_t smem, cudaStream_t st);
+void build_small_desc(void *desc_out, uint32_t n, uint32_t W, uint32_t B, uint32_t nblk, uint32_t n_levels,
+                      unsigned long long cyclic_mask, uint32_t max_iter, uint32_t max_passes,
+                      const uint32_t *dev_arrays, const SmallSrc *dev_srcs, size_t off_level, size_t off_src0,
+                      size_t off_nsrc, size_t off_f0, size_t off_nf, size_t off_fb, size_t off_null,
+                      const uint32_t *csr_off, const uint32_t *csr_col, uint64_t *blk_out, uint64_t *m2_out,
+                      QCtl *ctl);
+void fill_small_src(void *dst, uint32_t kind, uint32_t label, uint32_t ident, uint32_t same_level, int32_t rblk);
+
 // ---- device memory ----
 struct Allocator {
     cfpq_alloc_fn alloc = nullptr;
@@ -140,6 +155,11 @@ struct QueryDev {
     int prepare(Allocator *A, std::string *err);  // plan + buffers
     // Reset this query's device state and loop control (start of its fixpoint).
     int enqueue_init(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes);
+    // single-CTA path: eligible when rows are <= 512 bits and the state fits one SM
+    DBuf small_arrays, small_desc;
+    size_t small_smem = 0;
+    bool small_ok = false;
+    int prepare_small(Allocator *A, cudaStream_t st, uint32_t max_iter, uint32_t max_passes, std::string *err);
     QCtl *ctl() const { return ctl_mem.as<QCtl>(); }
     uint64_t *blk_ptr(uint32_t b) const { return blk_mem.as<uint64_t>() + (size_t)b * n * W; }
     uint32_t *stamp_ptr(uint32_t b) const { return stamp_mem.as<uint32_t>() + (size_t)b * n; }

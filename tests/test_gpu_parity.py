@@ -224,3 +224,29 @@ def test_extract_paths_random(cfpq, seed):
                 assert got == want, (b, vs, vf)
                 for p in got:
                     assert oracle.rsm_accepts(r, g.n_terminals, b, [l for _, l, _ in p])
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_single_cta_path_equals_multi_kernel(cfpq, seed):
+    """Small queries run their whole fixpoint in one CTA; the answer, the
+    iteration count and the closure equal the multi-kernel loop's."""
+    rng = np.random.Generator(np.random.PCG64(7000 + seed))
+    n = int(rng.integers(1, 500))
+    g, r = W.small_random_instance(7000 + seed, n=n, m=int(rng.integers(0, 3 * n + 1)),
+                                   n_labels=int(rng.integers(1, 4)), max_states=12)
+    c1, s1, a = _run(cfpq, g, r)
+    c2, s2, b = _run(cfpq, g, r, no_single_cta=1)
+    assert (a == b).all()
+    assert s1.iterations == s2.iterations and s1.edges_added == s2.edges_added
+    rows = [(s, x) for s in range(r.n_states) for x in range(0, n, max(1, n // 7))]
+    assert (c1.closure_rows(rows) == c2.closure_rows(rows)).all()
+    if n <= 200:
+        assert (a == oracle.worklist(g, r)).all()
+
+
+def test_single_cta_path_two_cycles_full(cfpq):
+    g, r = W.two_cycles(63, 64)
+    _, s1, a = _run(cfpq, g, r)
+    _, s2, b = _run(cfpq, g, r, no_single_cta=1)
+    assert s1.gpu_launches == 1 and s2.gpu_launches > 1
+    assert (a == b).all() and s1.iterations == s2.iterations == 4033
