@@ -77,7 +77,7 @@ int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t 
         n_gather += ex.n_items[v] ? 1 : 0;
         n_extract += ex.n_xitems[v] ? 1 : 0;
     }
-    const uint32_t per_pass = n_gather + n_extract + (ex.n_tcjobs ? 1 : 0) + 1;
+    const uint32_t per_pass = n_gather + n_extract + (ex.n_tcjobs ? 1 : 0) + (n_extract ? 0 : 1);
     if (ctx->opt.loop_mode == CFPQ_LOOP_HOST) {
         if (ex.enqueue_prologue(st, mi, mr, mp)) return fail(ctx, CFPQ_ERR_CUDA, "prologue launch failed");
         int running = 1;

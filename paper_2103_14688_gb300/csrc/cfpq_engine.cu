@@ -420,7 +420,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     const uint32_t nq = (uint32_t)qs.size();
     if (!ctl_ptrs.ensure(A, std::max<uint32_t>(nq, 1) * sizeof(QCtl *), err) ||
         !mirror.ensure(A, std::max<uint32_t>(nq, 1) * sizeof(QCtl), err) || !running.ensure(A, 16, err) ||
-        !tc_err.ensure(A, 16, err))
+        !tc_err.ensure(A, 16, err) || !done_counter.ensure(A, 16, err))
         return CFPQ_ERR_OUT_OF_MEMORY;
     uint32_t maxL1 = 2;
     for (QueryDev *q : qs) maxL1 = std::max(maxL1, q->n_levels + 1);
@@ -645,6 +645,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     T.t_job_end = take(nqa);
     ENG_CK(cudaMemcpyAsync(dbase, ht.data(), words * 4, cudaMemcpyHostToDevice, st));
     ENG_CK(cudaMemsetAsync(tc_err.p, 0, 16, st));
+    ENG_CK(cudaMemsetAsync(done_counter.p, 0, 16, st));
     if (n_tcjobs) ENG_CK(prepare_tc_launch());
     ENG_CK(cudaStreamSynchronize(st));
     drop_graph();
@@ -673,10 +674,19 @@ int Executor::enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int us
                              st));
     if (n_tcjobs) ENG_CK(launch_tc_product(false, tcjobs.as<TcJob>(), max_tc_tiles, T, tc_err.as<int>(), st));
     if (ev_after) ENG_CK(cudaEventRecord(ev_after, st));
+    // the last extraction launch of the pass also runs the loop control
+    int last_x = -1;
     for (int c = 0; c < kClasses; c += 2)
-        ENG_CK(launch_extract(kVplOf[c / 2], xitems[c].as<XItem>(), n_xitems[c], fds.as<FDesc>(), T, c, st));
-    ENG_CK(launch_control(ctl_ptrs.as<QCtl *>(), (uint32_t)qs.size(), mirror.as<QCtl>(), h, use_handle, running_out, T,
-                          1, st));
+        if (n_xitems[c]) last_x = c;
+    for (int c = 0; c < kClasses; c += 2) {
+        const bool fuse = c == last_x;
+        ENG_CK(launch_extract(kVplOf[c / 2], xitems[c].as<XItem>(), n_xitems[c], fds.as<FDesc>(), T, c,
+                              fuse ? ctl_ptrs.as<QCtl *>() : nullptr, (uint32_t)qs.size(), mirror.as<QCtl>(), h,
+                              use_handle, running_out, done_counter.as<unsigned int>(), st));
+    }
+    if (last_x < 0)
+        ENG_CK(launch_control(ctl_ptrs.as<QCtl *>(), (uint32_t)qs.size(), mirror.as<QCtl>(), h, use_handle,
+                              running_out, T, 1, st));
     return CFPQ_OK;
 }
 

@@ -16,7 +16,8 @@ int vpl_for_words(uint32_t W);
 cudaError_t launch_gather(int vpl, bool nt, const GItem *items, uint32_t n_items, const SrcDesc *srcs,
                           const ExecTables &T, int cls, cudaStream_t st);
 cudaError_t launch_extract(int vpl, const XItem *items, uint32_t n_items, const FDesc *fds, const ExecTables &T,
-                           int cls, cudaStream_t st);
+                           int cls, QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGraphConditionalHandle h,
+                           int use_handle, int *running_out, unsigned int *done_counter, cudaStream_t st);
 cudaError_t launch_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGraphConditionalHandle h, int use_handle,
                            int *running_out, const ExecTables &T, int advance, cudaStream_t st);
 cudaError_t launch_tc_product(bool int8, const TcJob *jobs, uint32_t max_tiles, const ExecTables &T, int *err_flag,
@@ -171,7 +172,7 @@ struct QueryDev {
 struct Executor {
     std::vector<QueryDev *> qs;
     DBuf ctl_ptrs, mirror, items[kClasses], xitems[kClasses], srcs, fds, running;
-    DBuf tcjobs, tables, tc_err;
+    DBuf tcjobs, tables, tc_err, done_counter;
     ExecTables T;
     uint32_t n_items[kClasses] = {0}, n_xitems[kClasses] = {0};
     uint32_t max_live[kClasses] = {0};  // bound on live items of a pass: sum over queries of the largest level

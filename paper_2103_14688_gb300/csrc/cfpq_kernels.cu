@@ -318,10 +318,27 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
 // --------------------------------------------------------------------------
 // Extraction: runs for a query only after a pass that changed no row.
 // --------------------------------------------------------------------------
+__device__ void control_body(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGraphConditionalHandle handle,
+                             int use_handle, int *running_out, const ExecTables &T, int advance);
+
+// Control fused into the last extraction launch of a pass: the CTA that
+// finishes last (counted with an atomic after a fence) runs control_body.
+struct FusedControl {
+    QCtl *const *ctls;
+    QCtl *mirror;
+    int *running_out;
+    unsigned int *done_counter;
+    cudaGraphConditionalHandle handle;
+    uint32_t nq;
+    int use_handle;
+    int enabled;
+};
+
 template <int VPL>
 __global__ void __launch_bounds__(256) k_extract(const XItem *__restrict__ items, const FDesc *__restrict__ fds,
-                                                 ExecTables T, int cls) {
+                                                 ExecTables T, int cls, FusedControl FC) {
     __shared__ unsigned long long s_new;
+    __shared__ int s_last;
     const uint32_t total = T.x_total[cls];
     for (uint32_t li = blockIdx.x; li < total; li += gridDim.x) {
     const uint32_t q = find_owner(T.x_pre[cls], T.nq, li);
@@ -398,14 +415,30 @@ __global__ void __launch_bounds__(256) k_extract(const XItem *__restrict__ items
     }
     __syncthreads();
     }
+    if (FC.enabled) {
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned int prev = atomicAdd(FC.done_counter, 1u);
+            s_last = (prev == gridDim.x - 1) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            if (threadIdx.x == 0) *FC.done_counter = 0u;
+            control_body(FC.ctls, FC.nq, FC.mirror, FC.handle, FC.use_handle, FC.running_out, T, 1);
+        }
+    }
 }
 
 // --------------------------------------------------------------------------
 // Loop control: one CTA for all queries.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror,
-                                                  cudaGraphConditionalHandle handle, int use_handle, int *running_out,
-                                                  ExecTables T, int advance) {
+// Loop control for every query of the executor, run by one whole CTA (any
+// size up to 1024 threads): advance each running query's state machine
+// (unless `advance` is 0), then build the live lists of the next pass.
+__device__ void control_body(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGraphConditionalHandle handle,
+                             int use_handle, int *running_out, const ExecTables &T, int advance) {
     int running = 0;
     for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
         QCtl &c = *ctls[q];
@@ -541,6 +574,12 @@ __global__ void __launch_bounds__(1024) k_control(QCtl *const *ctls, uint32_t nq
         if (use_handle) cudaGraphSetConditional(handle, running ? 1u : 0u);
         if (running_out) *running_out = running;
     }
+}
+
+__global__ void __launch_bounds__(1024) k_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror,
+                                                  cudaGraphConditionalHandle handle, int use_handle, int *running_out,
+                                                  ExecTables T, int advance) {
+    control_body(ctls, nq, mirror, handle, use_handle, running_out, T, advance);
 }
 
 // Reset the loop state of queries [0, nq) (start of a run).
@@ -784,15 +823,19 @@ cudaError_t launch_gather(int vpl, bool nt, const GItem *items, uint32_t n_items
     return cudaGetLastError();
 }
 
+// With fused control (ctls != null) this launch also runs the pass's loop
+// control in its last CTA; done_counter must be 0 before the first launch.
 cudaError_t launch_extract(int vpl, const XItem *items, uint32_t n_items, const FDesc *fds, const ExecTables &T,
-                           int cls, cudaStream_t st) {
+                           int cls, QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGraphConditionalHandle h,
+                           int use_handle, int *running_out, unsigned int *done_counter, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
+    FusedControl fc{ctls, mirror, running_out, done_counter, h, nq, use_handle, ctls != nullptr ? 1 : 0};
     switch (vpl) {
-        case 1: k_extract<1><<<n_items, 256, 0, st>>>(items, fds, T, cls); break;
-        case 2: k_extract<2><<<n_items, 256, 0, st>>>(items, fds, T, cls); break;
-        case 4: k_extract<4><<<n_items, 256, 0, st>>>(items, fds, T, cls); break;
-        case 8: k_extract<8><<<n_items, 256, 0, st>>>(items, fds, T, cls); break;
-        case 16: k_extract<16><<<n_items, 256, 0, st>>>(items, fds, T, cls); break;
+        case 1: k_extract<1><<<n_items, 256, 0, st>>>(items, fds, T, cls, fc); break;
+        case 2: k_extract<2><<<n_items, 256, 0, st>>>(items, fds, T, cls, fc); break;
+        case 4: k_extract<4><<<n_items, 256, 0, st>>>(items, fds, T, cls, fc); break;
+        case 8: k_extract<8><<<n_items, 256, 0, st>>>(items, fds, T, cls, fc); break;
+        case 16: k_extract<16><<<n_items, 256, 0, st>>>(items, fds, T, cls, fc); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
