@@ -346,6 +346,10 @@ def run_other(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     line = {"workload": args.workload, "n_gpus": 1, "data": "synthetic"}
+    # host-driven loop: one launch per kernel and pass, visible to profilers
+    loop_mode = cfpq.CFPQ_LOOP_HOST if args.loop == "host" else cfpq.CFPQ_LOOP_DEVICE
+    if args.loop == "host":
+        line["loop"] = "host"
     if args.workload == "cycles":
         g, r = W.two_cycles(63, 64)
         ctx = cfpq.Context()
@@ -365,25 +369,32 @@ def run_other(args):
     elif args.workload == "dyck":
         g, r = W.dyck_zipf(args.dyck_n)
         res = {}
-        for mode, name in ((cfpq.CFPQ_CLOSURE_BITPACKED, "bitpacked"), (cfpq.CFPQ_CLOSURE_TC_FP8, "tc_fp8")):
-            if name == "tc_fp8" and args.no_extras:
-                continue
-            ctx = cfpq.Context(closure_mode=mode)
+        all_modes = {"auto": cfpq.CFPQ_CLOSURE_AUTO, "bitpacked": cfpq.CFPQ_CLOSURE_BITPACKED,
+                     "tc_fp8": cfpq.CFPQ_CLOSURE_TC_FP8}
+        names = [m for m in args.modes.split(",") if m in all_modes]
+        if args.no_extras:
+            names = names[:1]
+        for name in names:
+            mode = all_modes[name]
+            ctx = cfpq.Context(closure_mode=mode, loop_mode=loop_mode)
             ctx.load_graph(g)
             ctx.load_rsm(r)
             st, ms = _ctx_time(ctx, stream, ctx.run)
             res[name] = {"ms": ms, "iterations": st.iterations, "passes": st.rounds, "row_ors": st.row_ors,
-                         "tile_products": st.tile_mmas, "pairs": ctx.count_reachable(0),
+                         "tile_products": st.tile_mmas, "tile_kstages": st.tile_kstages,
+                         "issued_tensor_tflop": st.tile_kstages * 2.0 * 128 * 256 * 128 / 1e12,
+                         "pairs": ctx.count_reachable(0),
                          "executed_bool_gops": st.row_ors * st.row_bytes * 8 / (ms / 1e3) / 1e9,
                          "device_gb": st.device_bytes / 1e9}
             res[name]["words"] = ctx.reachable_words(0)
             ctx.close()
-        same = None
-        if "tc_fp8" in res:
-            same = bool((res["tc_fp8"].pop("words") == res["bitpacked"]["words"]).all())
-        res["bitpacked"].pop("words", None)
-        line.update({"metric": "Dyck-4 index creation time", "unit": "ms", "value": res["bitpacked"]["ms"],
-                     "higher_is_better": False, "n": g.n, "m": g.m, "modes": res, "tc_equals_bitpacked": same})
+        ref = res[names[0]]["words"]
+        same = {k: bool((v["words"] == ref).all()) for k, v in res.items()}
+        for v in res.values():
+            v.pop("words", None)
+        line.update({"metric": "Dyck-4 index creation time", "unit": "ms", "value": res[names[0]]["ms"],
+                     "higher_is_better": False, "n": g.n, "m": g.m, "modes": res,
+                     f"modes_equal_{names[0]}": same})
     elif args.workload == "batched":
         qs = W.batched_queries(count=args.batch)
         ctx = cfpq.Context()
@@ -503,6 +514,10 @@ def main():
     ap.add_argument("--lambdas", default="10,30,100,300,1000")
     ap.add_argument("--horizon", type=float, default=5.0)
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--loop", default="device", choices=["device", "host"],
+                    help="dyck workload: fixpoint loop in a CUDA graph (device) or one launch per pass (host)")
+    ap.add_argument("--modes", default="auto,bitpacked,tc_fp8",
+                    help="dyck workload: closure modes to run (the first is the line's value)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

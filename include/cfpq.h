@@ -59,9 +59,16 @@ typedef void *(*cfpq_alloc_fn)(size_t bytes, void *stream, void *user);
 typedef void (*cfpq_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
 
 /* Closure kernels (Listing 1, incremental transitive closure). */
-#define CFPQ_CLOSURE_AUTO 0      /* bit-packed rows; tensor-core tiles where a label matrix is dense */
+/* AUTO: bit-packed rows; from n = 2048 on, a nonterminal whose matrix M2
+ * holds >= n^2/32 edges (checked after every iteration) moves its products
+ * with the dirty closure rows to tensor-core tiles as in TC_FP8. */
+#define CFPQ_CLOSURE_AUTO 0
 #define CFPQ_CLOSURE_BITPACKED 1 /* bit-packed uint64 rows only */
-#define CFPQ_CLOSURE_TC_FP8 2    /* dense tiles as 0/1 FP8-E4M3 tcgen05 products, FP32 accumulate, > 0 */
+/* TC_FP8: products of whole label matrices with the closure rows changed in
+ * the previous pass run as 0/1 FP8-E4M3 tcgen05 tiles (FP32 accumulate,
+ * count > 0), the inner dimension compacted to the changed rows; products of
+ * the new edges of an iteration stay on bit-packed rows. */
+#define CFPQ_CLOSURE_TC_FP8 2
 #define CFPQ_CLOSURE_TC_I8 3     /* 0/1 INT8 tcgen05 products: CFPQ_ERR_UNSUPPORTED on sm_103a (no kind::i8) */
 
 /* Fixpoint loop driver (Listing 1, "while M2 is changing"). */
@@ -130,6 +137,8 @@ typedef struct {
     double ms_loop;            /* host clock: the fixpoint loop (launch to completion) */
     uint32_t closure_launches; /* closure-pass launches timed (profile = 1) */
     uint32_t pad_;
+    uint64_t tile_kstages;     /* K stages of 128 multiplied by the tile products; each stage is
+                                  128 x 256 x 128 tensor-core multiply-adds */
 } cfpq_run_stats;
 
 /* ---- context ---------------------------------------------------------------- */

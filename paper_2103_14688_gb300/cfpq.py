@@ -61,7 +61,8 @@ class cfpq_run_stats(Structure):
                 ("tile_mmas", c_uint64), ("closure_blocks", c_uint64),
                 ("device_bytes", c_uint64), ("ms_total", c_double), ("ms_closure", c_double),
                 ("ms_setup", c_double), ("ms_loop", c_double),
-                ("closure_launches", c_uint32), ("pad_", c_uint32)]
+                ("closure_launches", c_uint32), ("pad_", c_uint32),
+                ("tile_kstages", c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

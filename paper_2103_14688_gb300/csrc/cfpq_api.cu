@@ -60,6 +60,7 @@ void fill_stats(cfpq_run_stats *s, const QCtl &c, const QueryDev &q, double ms) 
     s->edges_added = c.edges_total;
     s->row_ors = c.row_ors;
     s->tile_mmas = c.tile_mmas;
+    s->tile_kstages = c.tile_kstages;
     s->closure_blocks = q.blocks.size();
     s->device_bytes = q.device_bytes;
     s->ms_total = ms;
@@ -77,7 +78,8 @@ int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t 
         n_gather += ex.n_items[v] ? 1 : 0;
         n_extract += ex.n_xitems[v] ? 1 : 0;
     }
-    const uint32_t per_pass = n_gather + n_extract + (ex.n_tcjobs ? 1 : 0) + (n_extract ? 0 : 1);
+    // tile products: row list, column gather, product
+    const uint32_t per_pass = n_gather + n_extract + (ex.n_tcjobs ? 3 : 0) + (n_extract ? 0 : 1);
     if (ctx->opt.loop_mode == CFPQ_LOOP_HOST) {
         if (ex.enqueue_prologue(st, mi, mr, mp)) return fail(ctx, CFPQ_ERR_CUDA, "prologue launch failed");
         int running = 1;
@@ -120,7 +122,8 @@ int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t 
     }
     int tc_error = 0;
     if (ex.read_ctls(st, ctls, &tc_error)) return fail(ctx, CFPQ_ERR_CUDA, "reading loop state failed");
-    if (tc_error) return fail(ctx, CFPQ_ERR_TIMEOUT, "a tensor-core tile gave up waiting for its MMAs");
+    if (tc_error)
+        return fail(ctx, CFPQ_ERR_TIMEOUT, "a tile-product kernel gave up (bounded wait on its MMAs or on a counter)");
     if (ctx->opt.loop_mode != CFPQ_LOOP_HOST && launches) {
         uint32_t passes = 0;
         for (const auto &c : *ctls) passes = std::max(passes, c.passes);
@@ -727,6 +730,7 @@ extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_quer
         tot.edges_added += s.edges_added;
         tot.row_ors += s.row_ors;
         tot.tile_mmas += s.tile_mmas;
+        tot.tile_kstages += s.tile_kstages;
         tot.closure_blocks += s.closure_blocks;
         tot.device_bytes += s.device_bytes;
         if (status_of(ctls[i])) worst = status_of(ctls[i]);

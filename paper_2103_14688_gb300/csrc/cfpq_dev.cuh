@@ -53,11 +53,20 @@ struct QCtl {
     uint32_t level;           // level being processed
     uint32_t n_levels;        // levels of this query (>= 1)
     unsigned long long cyclic_mask;   // bit L: level L has a cycle (REPEAT passes)
+    // Density switch of nonterminal sources (closure mode AUTO): bit b set when
+    // box b's matrix M2^b holds at least n^2 / kDenseDiv edges; decided at the
+    // end of every iteration, so a pass never mixes the two forms of a source.
+    unsigned long long *box_edges;    // per box: edges of M2^b (null: no switch)
+    uint32_t dense_mask;
+    uint32_t n_boxes;
+    uint32_t n;
+    uint32_t pad2;
     unsigned long long changed_rows;  // rows changed by the pass in progress
     unsigned long long new_edges;     // edges added by the extraction in progress
     unsigned long long edges_total;   // edges added so far (epsilon edges included)
     unsigned long long row_ors;       // source rows ORed (all passes)
     unsigned long long tile_mmas;     // dense tiles multiplied (all passes)
+    unsigned long long tile_kstages;  // K stages of those tiles run on the tensor cores (128 x 256 x 128 MACs each)
     unsigned long long rounds_total;
     unsigned long long rows_changed_total;  // summed over passes
 };
@@ -78,7 +87,15 @@ struct SrcDesc {
     uint32_t ident;            // u == t: the product edge itself lands in C[s,t]
     uint32_t same_level;       // C[u,t] is on the level of C[s,t] (same cyclic component)
     uint32_t dense;            // label matrix handled by dense tiles (not here)
-    uint32_t pad;
+    uint32_t box_switch;       // nonterminal source that moves to dense tiles when its box is dense
+    uint32_t label_box;        // box of a nonterminal source
+    // C[u,t] is the union of at most two terminal adjacencies (every source of
+    // block (u,t) is a direct terminal transition u -l-> t): its row y is read
+    // as those labels' CSR rows of y instead of n bits.  rblk/rstamp/rlast
+    // still give the dirty state of the block.
+    uint32_t pure_n;
+    const uint32_t *pure_off[2];
+    const uint32_t *pure_col;
 };
 
 // Gather work item: rows [row0, row1) of one output block.
@@ -107,6 +124,7 @@ struct XItem {
     uint64_t *a2;
     uint32_t *a2_it;
     uint32_t *box_new_it;
+    unsigned long long *box_edges;  // edge counter of the box (density switch)
     QCtl *ctl;
     uint32_t f0, nf;
     uint32_t row0, row1;
@@ -134,8 +152,20 @@ struct TcJob {
     const uint32_t *rlast;
     uint32_t tiles_m, tiles_n;  // tiles of this job
     uint32_t tile0;             // first global tile index of this job
-    uint32_t pad;
+    uint32_t box;               // nonterminal label (switchable jobs)
+    uint32_t switchable;        // active only while the box is dense (closure mode AUTO)
+    uint32_t Wc;                // words per row of `ac`; at most Wc * 64 compacted rows
+    // Dirty-row compaction (channels 2 and 4): before the products of a pass,
+    // the B rows with stamp >= thr are listed in `ys` and the columns of A at
+    // those rows gathered into `ac`, so that the product's inner dimension
+    // runs over the dirty rows only.  `kcount` = (pass stamp << 32) | count.
+    uint32_t *ys;
+    unsigned long long *kcount;
+    uint64_t *ac;
 };
+
+constexpr uint32_t kDenseDiv = 32;  // a box is dense from n^2 / 32 edges on (one bit in two words)
+constexpr uint32_t kAutoTilesMinN = 2048;  // AUTO switches boxes to tile products only from this n on
 
 // Per-executor work tables.  Items of each kind are sorted by (query, level);
 // the static tables give, for query q and level L, the first item of that
@@ -144,8 +174,9 @@ struct TcJob {
 // level and an exclusive prefix over queries, so that persistent kernels walk
 // only the live items.
 constexpr int kVplClasses = 5;
-// Item classes: row width class (VPL 1, 2, 4, 8, 16) x whether the block has
-// sources over nonterminal (bit-row) adjacency: class = 2 * vpl_index + nt.
+// Item classes: row width class (VPL 1, 2, 4, 8, 16) x kernel variant: the
+// general variant (nt = 1) serves blocks with sources over nonterminal
+// (bit-row) adjacency or reading pure-terminal blocks; class = 2 * vpl_index + nt.
 constexpr int kClasses = 2 * kVplClasses;
 struct ExecTables {
     uint32_t nq;

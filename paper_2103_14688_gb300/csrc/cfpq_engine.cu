@@ -265,6 +265,8 @@ int QueryDev::plan(std::string *err) {
     }
     // Sources of block (s,t): transitions s -l-> u with u == t or t reachable from u.
     srcs.clear();
+    n_tc_src = 0;
+    Wc = std::max<uint32_t>(2u, ((W + 3u) / 4u + 1u) & ~1u);
     blk_src0.assign(blocks.size(), 0);
     blk_nsrc.assign(blocks.size(), 0);
     for (size_t b = 0; b < blocks.size(); ++b) {
@@ -277,13 +279,37 @@ int QueryDev::plan(std::string *err) {
             const int32_t rb = blk_of[(size_t)u * Q + t];
             if (!ident && rb < 0) continue;
             const uint32_t same = (rb >= 0 && blk_level[(size_t)rb] == blk_level[b]) ? 1u : 0u;
-            // tensor-core mode: every source that reads a closure block is a
-            // dense product job; sources that only add the product edges
-            // themselves (u == t on an acyclic state) stay bit-packed
-            const uint32_t dense = (closure_mode == CFPQ_CLOSURE_TC_FP8 && rb >= 0) ? 1u : 0u;
-            srcs.push_back({tr.kind, tr.sym, ident ? 1u : 0u, rb, same, dense});
+            srcs.push_back({tr.kind, tr.sym, ident ? 1u : 0u, rb, same, 0u, 0u, -1, 0u});
         }
         blk_nsrc[b] = (uint32_t)srcs.size() - blk_src0[b];
+    }
+    // Pure-terminal blocks: every source a direct terminal transition u -l-> t
+    // (no closure block read), at most two labels.  Such a block equals the
+    // union of those adjacencies, so its readers expand CSR rows.
+    blk_pure_n.assign(blocks.size(), 0);
+    blk_pure_lbl.assign(blocks.size() * 2, 0);
+    for (size_t b = 0; b < blocks.size(); ++b) {
+        bool pure = blk_nsrc[b] > 0 && blk_nsrc[b] <= 2;
+        for (uint32_t k = 0; k < blk_nsrc[b] && pure; ++k) {
+            const Src &sd = srcs[blk_src0[b] + k];
+            pure = sd.rblk < 0 && sd.label_kind == 0 && sd.ident;
+        }
+        if (!pure) continue;
+        blk_pure_n[b] = blk_nsrc[b];
+        for (uint32_t k = 0; k < blk_nsrc[b]; ++k) blk_pure_lbl[b * 2 + k] = srcs[blk_src0[b] + k].label;
+    }
+    for (auto &sd : srcs) {
+        sd.pure_rb = (sd.rblk >= 0 && !sd.ident && sd.label_kind == 1 && blk_pure_n[(size_t)sd.rblk] > 0) ? 1u : 0u;
+        const bool tiles_ok = sd.rblk >= 0 && !sd.pure_rb;
+        // tensor-core mode: the dirty-row channels of every source that reads
+        // a (non-pure) closure block are tile products; new edges stay on the
+        // row gather
+        sd.dense = (closure_mode == CFPQ_CLOSURE_TC_FP8 && tiles_ok) ? 1u : 0u;
+        // AUTO: the same for a nonterminal source while its box's matrix is
+        // dense (large queries only: a tile is 128 x 256)
+        sd.box_switch =
+            (closure_mode == CFPQ_CLOSURE_AUTO && sd.label_kind == 1 && tiles_ok && n >= kAutoTilesMinN) ? 1u : 0u;
+        sd.tc_slot = (sd.dense || sd.box_switch) ? (int32_t)n_tc_src++ : -1;
     }
     // Extraction blocks: (q0_b, f) for f final in box b.
     fblocks.clear();
@@ -302,9 +328,14 @@ int QueryDev::plan(std::string *err) {
     return CFPQ_OK;
 }
 
+uint64_t QueryDev::tc_slot_bytes() const {
+    return (uint64_t)W * 64 * 4 + 256 + (uint64_t)n * Wc * 8;
+}
+
 uint64_t QueryDev::footprint() const {
     const uint64_t nblk = std::max<uint64_t>(blocks.size(), 1), bw = (uint64_t)n * W * 8;
-    return nblk * bw + nblk * n * 4 + nblk * 4 + 2ull * B * bw + (uint64_t)B * n * 4 + B * 4 + 4096;
+    return nblk * bw + nblk * n * 4 + nblk * 4 + 2ull * B * bw + (uint64_t)B * n * 4 + B * 4 + 4096 +
+           (uint64_t)n_tc_src * tc_slot_bytes();
 }
 
 int QueryDev::prepare(Allocator *A, std::string *err) {
@@ -317,17 +348,20 @@ int QueryDev::prepare(Allocator *A, std::string *err) {
         !last_mem.ensure(A, std::max<size_t>(nblk, 1) * 4, err) || !m2_mem.ensure(A, (size_t)B * bw, err) ||
         !a2_mem.ensure(A, (size_t)B * bw, err) || !a2it_mem.ensure(A, (size_t)B * n * 4, err) ||
         !boxit_mem.ensure(A, (size_t)B * 4, err) || !ctl_mem.ensure(A, sizeof(QCtl), err) ||
+        !boxedge_mem.ensure(A, (size_t)B * 8, err) ||
         !ctl_ptr_mem.ensure(A, sizeof(QCtl *), err) ||
-        !eps_mem.ensure(A, std::max<size_t>(n_eps, 1) * eps_desc_size(), err))
+        !eps_mem.ensure(A, std::max<size_t>(n_eps, 1) * eps_desc_size(), err) ||
+        !tc_mem.ensure(A, std::max<size_t>(n_tc_src * tc_slot_bytes(), 64), err))
         return CFPQ_ERR_OUT_OF_MEMORY;
     device_bytes = blk_mem.bytes + stamp_mem.bytes + last_mem.bytes + m2_mem.bytes + a2_mem.bytes + a2it_mem.bytes +
-                   boxit_mem.bytes;
+                   boxit_mem.bytes + (n_tc_src ? tc_mem.bytes : 0);
     std::vector<unsigned char> he(std::max<size_t>(n_eps, 1) * eps_desc_size());
     uint32_t k = 0;
     for (uint32_t b = 0; b < B; ++b) {
         if (!rsm.final_[rsm.box_start[b]]) continue;
         fill_eps_desc(he.data() + (size_t)k * eps_desc_size(), m2_ptr(b), a2_ptr(b),
-                      a2it_mem.as<uint32_t>() + (size_t)b * n, boxit_mem.as<uint32_t>() + b, ctl(), n, W);
+                      a2it_mem.as<uint32_t>() + (size_t)b * n, boxit_mem.as<uint32_t>() + b, ctl(),
+                      boxedge_mem.as<unsigned long long>() + b, n, W);
         ++k;
     }
     QCtl *cp = ctl();
@@ -397,7 +431,11 @@ int QueryDev::enqueue_init(cudaStream_t st, uint32_t max_iter, uint32_t max_roun
     ENG_CK(cudaMemsetAsync(m2_mem.p, 0, (size_t)B * n * W * 8, st));
     ENG_CK(cudaMemsetAsync(a2it_mem.p, 0, (size_t)B * n * 4, st));
     ENG_CK(cudaMemsetAsync(boxit_mem.p, 0, (size_t)B * 4, st));
-    ENG_CK(launch_ctl_reset(ctl_ptr_mem.as<QCtl *>(), 1, max_iter, max_rounds, max_passes, n_levels, cyclic_mask, st));
+    ENG_CK(cudaMemsetAsync(boxedge_mem.p, 0, (size_t)B * 8, st));
+    for (uint32_t k = 0; k < n_tc_src; ++k) ENG_CK(cudaMemsetAsync(tc_kcount(k), 0, 8, st));
+    ENG_CK(launch_ctl_reset(ctl_ptr_mem.as<QCtl *>(), 1, max_iter, max_rounds, max_passes, n_levels, cyclic_mask,
+                            closure_mode == CFPQ_CLOSURE_AUTO ? boxedge_mem.as<unsigned long long>() : nullptr, B, n,
+                            st));
     ENG_CK(launch_eps_init(eps_mem.p, n_eps, 152, st));
     return CFPQ_OK;
 }
@@ -438,6 +476,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     }
     std::vector<uint32_t> t_lvl((size_t)nq * maxL1, 0), t_lvl_tiles((size_t)nq * maxL1, 0);
     max_tc_tiles = 0;
+    max_tc_w = 0;
     uint32_t live_bound[kClasses] = {0};
     for (uint32_t qi = 0; qi < nq; ++qi) {
         QueryDev &q = *qs[qi];
@@ -468,14 +507,24 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                 d.rstamp = q.stamp_ptr((uint32_t)sd.rblk);
                 d.rlast = q.last_mem.as<uint32_t>() + sd.rblk;
             }
+            if (sd.pure_rb) {
+                const size_t rb = (size_t)sd.rblk;
+                d.pure_n = q.blk_pure_n[rb];
+                for (uint32_t p = 0; p < d.pure_n; ++p)
+                    d.pure_off[p] = g.csr_off.as<uint32_t>() + (size_t)q.blk_pure_lbl[rb * 2 + p] * q.n;
+                d.pure_col = g.csr_col.as<uint32_t>();
+            }
             d.ident = sd.ident;
             d.same_level = sd.same_level;
             d.dense = sd.dense;
+            d.box_switch = sd.box_switch;
+            d.label_box = sd.label_kind == 1 ? sd.label : 0u;
             hs.push_back(d);
         }
         const int vi = vpl_index(q.vpl);
         const uint32_t rows_per_step = 8u * (32u / q.lpr);
         const uint32_t rpi = std::max<uint32_t>(64u, rows_per_step * 4u);
+        // product jobs: tcgen05 tiles of 128 rows x 256 columns
         const uint32_t tiles_m = (q.n + 127u) / 128u, tiles_n = (q.n + 255u) / 256u;
         for (uint32_t L = 0; L <= q.n_levels; ++L) {
             for (int v = 0; v < kClasses; ++v) g_lvl[v][(size_t)qi * maxL1 + L] = (uint32_t)hi[v].size();
@@ -487,7 +536,8 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                 bool has_nt = false;
                 for (uint32_t k = 0; k < q.blk_nsrc[b]; ++k) {
                     const auto &sd = q.srcs[q.blk_src0[b] + k];
-                    has_nt |= (sd.label_kind != 0 && !sd.dense);
+                    // the general kernel variant: nonterminal adjacency rows, pure-terminal blocks
+                    has_nt |= (sd.label_kind != 0) || sd.pure_rb;
                 }
                 const int cls = 2 * vi + (has_nt ? 1 : 0);
                 for (uint32_t r0 = 0; r0 < q.n; r0 += rpi) {
@@ -506,43 +556,47 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                     it.pad = 0;
                     hi[cls].push_back(it);
                 }
-                // dense sources of this block: one product job per channel
+                // tile sources of this block: one product job for the dirty-row
+                // channel (4 on a cyclic level's own blocks, else 2)
                 for (uint32_t k = 0; k < q.blk_nsrc[b]; ++k) {
                     const auto &sd = q.srcs[q.blk_src0[b] + k];
-                    if (!sd.dense) continue;
+                    if (sd.tc_slot < 0) continue;
                     const SrcDesc &d = hs[base + q.blk_src0[b] + k];
-                    const uint32_t chans[2] = {1u, sd.same_level ? 4u : 2u};
-                    for (uint32_t ch : chans) {
-                        TcJob j;
-                        memset(&j, 0, sizeof(j));
-                        j.out = q.blk_ptr((uint32_t)b);
-                        j.out_stamp = q.stamp_ptr((uint32_t)b);
-                        j.out_last = q.last_mem.as<uint32_t>() + b;
-                        if (sd.label_kind == 0) {
-                            j.A = g.term_bits.as<uint64_t>() + (size_t)sd.label * q.n * q.W;
-                            j.a_it = nullptr;
-                            j.box_new_it = nullptr;
-                        } else {
-                            j.A = ch == 1u ? q.a2_ptr(sd.label) : q.m2_ptr(sd.label);
-                            j.a_it = ch == 1u ? d.nt_new_it : nullptr;
-                            j.box_new_it = d.box_new_it;
-                        }
-                        j.B = d.rblk;
-                        j.b_stamp = d.rstamp;
-                        j.rlast = d.rlast;
-                        j.ctl = cp;
-                        j.n = q.n;
-                        j.W = q.W;
-                        j.ident = (ch == 1u) ? sd.ident : 0u;
-                        j.chan = ch;
-                        j.level = L;
-                        j.same_level = sd.same_level;
-                        j.tiles_m = tiles_m;
-                        j.tiles_n = tiles_n;
-                        j.tile0 = lvl_tiles;
-                        lvl_tiles += tiles_m * tiles_n;
-                        hj.push_back(j);
+                    TcJob j;
+                    memset(&j, 0, sizeof(j));
+                    j.out = q.blk_ptr((uint32_t)b);
+                    j.out_stamp = q.stamp_ptr((uint32_t)b);
+                    j.out_last = q.last_mem.as<uint32_t>() + b;
+                    if (sd.label_kind == 0) {
+                        j.A = g.term_bits.as<uint64_t>() + (size_t)sd.label * q.n * q.W;
+                        j.box_new_it = nullptr;
+                    } else {
+                        j.A = q.m2_ptr(sd.label);
+                        j.box_new_it = d.box_new_it;
                     }
+                    j.a_it = nullptr;
+                    j.B = d.rblk;
+                    j.b_stamp = d.rstamp;
+                    j.rlast = d.rlast;
+                    j.ctl = cp;
+                    j.n = q.n;
+                    j.W = q.W;
+                    j.ident = 0u;
+                    j.chan = sd.same_level ? 4u : 2u;
+                    j.level = L;
+                    j.same_level = sd.same_level;
+                    j.tiles_m = tiles_m;
+                    j.tiles_n = tiles_n;
+                    j.box = sd.label_kind == 1 ? sd.label : 0u;
+                    j.switchable = sd.box_switch;
+                    j.Wc = q.Wc;
+                    j.ys = q.tc_ys((uint32_t)sd.tc_slot);
+                    j.kcount = q.tc_kcount((uint32_t)sd.tc_slot);
+                    j.ac = q.tc_ac((uint32_t)sd.tc_slot);
+                    j.tile0 = lvl_tiles;
+                    lvl_tiles += tiles_m * tiles_n;
+                    hj.push_back(j);
+                    max_tc_w = std::max(max_tc_w, q.W);
                 }
             }
             t_lvl_tiles[(size_t)qi * maxL1 + L] = lvl_tiles;
@@ -568,6 +622,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
             if (q.box_nf[b] == 0) continue;
             for (uint32_t r0 = 0; r0 < q.n; r0 += rpi) {
                 XItem x;
+                x.box_edges = q.boxedge_mem.as<unsigned long long>() + b;
                 x.m2 = q.m2_ptr(b);
                 x.a2 = q.a2_ptr(b);
                 x.a2_it = q.a2it_mem.as<uint32_t>() + (size_t)b * q.n;
@@ -672,7 +727,10 @@ int Executor::enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int us
     for (int c = 0; c < kClasses; ++c)
         ENG_CK(launch_gather(kVplOf[c / 2], (c & 1) != 0, items[c].as<GItem>(), max_live[c], srcs.as<SrcDesc>(), T, c,
                              st));
-    if (n_tcjobs) ENG_CK(launch_tc_product(false, tcjobs.as<TcJob>(), max_tc_tiles, T, tc_err.as<int>(), st));
+    if (n_tcjobs) {
+        ENG_CK(launch_tc_compact(tcjobs.as<TcJob>(), T, max_tc_w, tc_err.as<int>(), st));
+        ENG_CK(launch_tc_product(false, tcjobs.as<TcJob>(), max_tc_tiles, T, tc_err.as<int>(), st));
+    }
     if (ev_after) ENG_CK(cudaEventRecord(ev_after, st));
     // the last extraction launch of the pass also runs the loop control
     int last_x = -1;

@@ -22,15 +22,19 @@ cudaError_t launch_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGra
                            int *running_out, const ExecTables &T, int advance, cudaStream_t st);
 cudaError_t launch_tc_product(bool int8, const TcJob *jobs, uint32_t max_tiles, const ExecTables &T, int *err_flag,
                               cudaStream_t st);
+// Per pass, before launch_tc_product: list each live job's dirty B rows and
+// gather A's columns at them (max_w = the largest W of any job).
+cudaError_t launch_tc_compact(const TcJob *jobs, const ExecTables &T, uint32_t max_w, int *err_flag, cudaStream_t st);
 cudaError_t prepare_tc_launch();
 cudaError_t launch_csr_to_bits(const uint32_t *off, const uint32_t *col, size_t rows, uint32_t W, uint64_t *bits,
                                cudaStream_t st);
 cudaError_t launch_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds,
-                             uint32_t max_passes, uint32_t n_levels, unsigned long long cyclic_mask, cudaStream_t st);
+                             uint32_t max_passes, uint32_t n_levels, unsigned long long cyclic_mask,
+                             unsigned long long *box_edges, uint32_t n_boxes, uint32_t n, cudaStream_t st);
 cudaError_t launch_eps_init(const void *eds, uint32_t ned, uint32_t grid, cudaStream_t st);
 size_t eps_desc_size();
-void fill_eps_desc(void *dst, uint64_t *m2, uint64_t *a2, uint32_t *a2_it, uint32_t *box_new_it, QCtl *ctl, uint32_t n,
-                   uint32_t W);
+void fill_eps_desc(void *dst, uint64_t *m2, uint64_t *a2, uint32_t *a2_it, uint32_t *box_new_it, QCtl *ctl,
+                   unsigned long long *box_edges, uint32_t n, uint32_t W);
 cudaError_t scan_exclusive(const uint32_t *in, uint32_t *out, size_t n, uint32_t *tmp, cudaStream_t st);
 cudaError_t launch_stage_count(const uint32_t *src, const uint32_t *lbl, const uint32_t *dst, size_t m, uint32_t n,
                                uint32_t n_term, const int32_t *label_map, uint32_t *cnt, int *err, cudaStream_t st);
@@ -136,12 +140,31 @@ struct QueryDev {
     uint32_t n = 0, W = 0, Q = 0, B = 0, vpl = 0, lpr = 0;
     std::vector<int32_t> blk_of;  // Q*Q -> block or -1
     std::vector<std::pair<uint32_t, uint32_t>> blocks;
-    DBuf blk_mem, stamp_mem, last_mem, m2_mem, a2_mem, a2it_mem, boxit_mem, ctl_mem, eps_mem, ctl_ptr_mem;
+    DBuf blk_mem, stamp_mem, last_mem, m2_mem, a2_mem, a2it_mem, boxit_mem, ctl_mem, eps_mem, ctl_ptr_mem, boxedge_mem;
     uint32_t n_eps = 0;
     uint64_t device_bytes = 0;
     // host descriptors (pointers filled once buffers exist; ctl set by the executor)
     uint32_t closure_mode = CFPQ_CLOSURE_AUTO;
-    struct Src { uint32_t label_kind, label, ident; int32_t rblk; uint32_t same_level, dense; };
+    struct Src {
+        uint32_t label_kind, label, ident;
+        int32_t rblk;
+        uint32_t same_level, dense, box_switch;
+        int32_t tc_slot;  // compaction buffers of the source's product job, or -1
+        uint32_t pure_rb; // the block read is pure-terminal: expand CSR rows
+    };
+    std::vector<uint32_t> blk_pure_n, blk_pure_lbl;  // per block: labels of a pure-terminal block (<= 2)
+    // Product jobs' compaction buffers, one slot per tile source: the dirty
+    // row list (n_pad entries), its pass-stamped count, and A's gathered
+    // columns (n rows of Wc words).
+    DBuf tc_mem;
+    uint32_t n_tc_src = 0, Wc = 0;
+    uint64_t tc_slot_bytes() const;
+    unsigned char *tc_slot(uint32_t k) const { return tc_mem.as<unsigned char>() + (size_t)k * tc_slot_bytes(); }
+    uint32_t *tc_ys(uint32_t k) const { return reinterpret_cast<uint32_t *>(tc_slot(k)); }
+    unsigned long long *tc_kcount(uint32_t k) const {
+        return reinterpret_cast<unsigned long long *>(tc_slot(k) + (size_t)W * 64 * 4);
+    }
+    uint64_t *tc_ac(uint32_t k) const { return reinterpret_cast<uint64_t *>(tc_slot(k) + (size_t)W * 64 * 4 + 256); }
     std::vector<uint32_t> blk_src0, blk_nsrc;  // per block
     std::vector<uint32_t> blk_level;           // per block, 0..n_levels-1
     uint32_t n_levels = 1;
@@ -176,7 +199,7 @@ struct Executor {
     ExecTables T;
     uint32_t n_items[kClasses] = {0}, n_xitems[kClasses] = {0};
     uint32_t max_live[kClasses] = {0};  // bound on live items of a pass: sum over queries of the largest level
-    uint32_t n_tcjobs = 0, max_tc_tiles = 0;
+    uint32_t n_tcjobs = 0, max_tc_tiles = 0, max_tc_w = 0;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream: capture is not allowed on the legacy default stream

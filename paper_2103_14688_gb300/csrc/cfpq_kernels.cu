@@ -50,6 +50,59 @@ __device__ __forceinline__ void setbit4(uint4 &v, uint32_t pos) {
     }
 }
 
+// Set bit z of a row held by a group of lpr lanes (lane gl holds the 128-bit
+// vectors gl, gl + lpr, ...).
+template <int VPL>
+__device__ __forceinline__ void set_row_bit(uint4 (&acc)[VPL], uint32_t z, int lpr, int gl) {
+    const uint32_t v = z >> 7;
+    if ((int)(v % (uint32_t)lpr) == gl) {
+        const int j = (int)(v / (uint32_t)lpr);
+#pragma unroll
+        for (int jj = 0; jj < VPL; ++jj)
+            if (jj == j) setbit4(acc[jj], z & 127u);
+    }
+}
+
+// OR rows of a pure-terminal block (see SrcDesc::pure_n) into the group's
+// row: every lane with keep_l expands its own source row y_l (the columns of
+// y_l's CSR rows under the block's labels, all lanes' loads in flight at
+// once), and each column found is passed by shuffle to the lane that holds
+// its bit.  Called by all lanes of the warp.
+template <int VPL>
+__device__ __forceinline__ void or_pure_rows(uint4 (&acc)[VPL], const SrcDesc &d, uint32_t y_l, bool keep_l,
+                                             int lpr, int gl, int grp, unsigned gmask) {
+    uint32_t e0 = 0, e1 = 0, f0 = 0, f1 = 0;
+    if (keep_l) {
+        e0 = d.pure_off[0][y_l];
+        e1 = d.pure_off[0][y_l + 1];
+        if (d.pure_n > 1) {
+            f0 = d.pure_off[1][y_l];
+            f1 = d.pure_off[1][y_l + 1];
+        }
+    }
+    while (true) {
+        bool has = false;
+        uint32_t z = 0;
+        if (e0 < e1) {
+            z = d.pure_col[e0++];
+            has = true;
+        } else if (f0 < f1) {
+            z = d.pure_col[f0++];
+            has = true;
+        }
+        const unsigned bal = __ballot_sync(FULLMASK, has);
+        if (!bal) break;
+        unsigned mine = (bal & gmask) >> (grp * lpr);
+        while (__any_sync(FULLMASK, mine != 0u)) {
+            const bool h = mine != 0u;
+            const int src = h ? __ffs(mine) - 1 : 0;
+            if (h) mine &= mine - 1u;
+            const uint32_t zz = __shfl_sync(FULLMASK, z, src, lpr);
+            if (h) set_row_bit<VPL>(acc, zz, lpr, gl);
+        }
+    }
+}
+
 // Lowest set bit of a 128-bit vector, -1 if none; clears it when `clear`.
 __device__ __forceinline__ int lowbit4(uint4 &v, bool clear) {
     if (v.x) { int b = __ffs(v.x) - 1; if (clear) v.x &= v.x - 1; return b; }
@@ -66,9 +119,12 @@ __device__ __forceinline__ int lowbit4(uint4 &v, bool clear) {
 //      (FIRST pass; those levels are final for the iteration);
 //   4  all edges, source rows of this level changed in the previous pass
 //      (REPEAT pass of a cyclic level).
+// Channels 2 and 4 of a tensor-core source (and of a switchable source while
+// its box is dense) run as tile products over the dirty rows instead.
 __device__ __forceinline__ uint32_t src_channels(const SrcDesc &d, uint32_t mode, uint32_t iter, uint32_t g,
-                                                 uint32_t g0) {
-    if (d.dense) return 0u;
+                                                 uint32_t g0, uint32_t dense_mask) {
+    const bool tiles = d.dense || (d.box_switch && d.csr_off == nullptr && d.label_box < 32u &&
+                                   ((dense_mask >> d.label_box) & 1u));
     uint32_t ch = 0u;
     if (mode == kModeNew) {
         const bool term1 = d.csr_off != nullptr && iter == 1;
@@ -77,13 +133,15 @@ __device__ __forceinline__ uint32_t src_channels(const SrcDesc &d, uint32_t mode
     } else {
         if (d.rblk && d.same_level && *d.rlast + 1u >= g) ch |= 4u;
     }
-    return ch;
+    return tiles ? (ch & 1u) : ch;
 }
 
 // --------------------------------------------------------------------------
 // Closure pass (bit-packed rows).  One CTA of 8 warps per work item; a row is
 // handled by a group of `lpr` lanes, each lane holding VPL 128-bit vectors
-// (words 2v, 2v+1 for v = lane_in_group + j * lpr).
+// (words 2v, 2v+1 for v = lane_in_group + j * lpr).  NT selects the general
+// variant (nonterminal adjacency rows, pure-terminal blocks); without it the
+// kernel holds only the CSR paths, which keeps its registers for the rows.
 // --------------------------------------------------------------------------
 // Occupancy target per row width: narrow rows keep 4 CTAs (32 warps) per SM.
 template <int VPL>
@@ -104,11 +162,11 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
     const GItem it = items[T.g_beg[cls][q] + (li - T.g_pre[cls][q])];
     const QCtl *c = it.ctl;
     if (c->phase != kPhaseRun || c->level != it.level) continue;
-    const uint32_t g = c->g, iter = c->iter, mode = c->mode, g0 = c->g_iter_start;
+    const uint32_t g = c->g, iter = c->iter, mode = c->mode, g0 = c->g_iter_start, dmask = c->dense_mask;
 
     int act = 0;
     for (uint32_t k = threadIdx.x; k < it.nsrc; k += blockDim.x)
-        act |= src_channels(srcs[it.src0 + k], mode, iter, g, g0) != 0u;
+        act |= src_channels(srcs[it.src0 + k], mode, iter, g, g0, dmask) != 0u;
     if (!__syncthreads_or(act)) continue;
 
     if (threadIdx.x == 0) { s_changed = 0; s_ors = 0; }
@@ -129,7 +187,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
 
         for (uint32_t k = 0; k < it.nsrc; ++k) {
             const SrcDesc d = srcs[it.src0 + k];
-            const uint32_t chans = src_channels(d, mode, iter, g, g0);
+            const uint32_t chans = src_channels(d, mode, iter, g, g0, dmask);
             for (uint32_t cbit = 1u; cbit <= 4u; cbit <<= 1) {
                 if (!(chans & cbit)) continue;
                 const bool new_edges = cbit == 1u;
@@ -146,6 +204,12 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                 constexpr int U = VPL >= 4 ? 1 : 4 / VPL;
                 auto take_batch = [&](uint32_t y_l, bool has_l) {
                     const bool keep = has_l && (d.rblk == nullptr || thr == 0u || d.rstamp[y_l] >= thr);
+                    if constexpr (NT) {
+                        if (d.pure_n && !use_ident) {
+                            or_pure_rows<VPL>(acc, d, y_l, keep, lpr, gl, grp, gmask);
+                            return;
+                        }
+                    }
                     const unsigned bal = __ballot_sync(FULLMASK, keep);
                     unsigned mine = (bal & gmask) >> (grp * lpr);
                     while (__any_sync(FULLMASK, mine != 0u)) {
@@ -171,7 +235,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                                 }
                             }
                         }
-                        if (d.rblk) {
+                        if (d.rblk && (!NT || !d.pure_n)) {
                             uint4 rv[U][VPL];
 #pragma unroll
                             for (int u = 0; u < U; ++u) {
@@ -196,7 +260,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                     const uint32_t e0 = valid ? d.csr_off[row] : 0u, e1 = valid ? d.csr_off[row + 1] : 0u;
                     const uint32_t cnt = e1 - e0;
                     const uint32_t maxcnt = __reduce_max_sync(FULLMASK, cnt);
-                    if (maxcnt <= 8u) {
+                    if (maxcnt <= 8u && (!NT || !d.pure_n)) {
                         // short adjacency rows (the common case on sparse
                         // graphs): no ballot; edges two at a time so that the
                         // column, stamp and row loads of both are in flight
@@ -412,6 +476,7 @@ __global__ void __launch_bounds__(256) k_extract(const XItem *__restrict__ items
     if (threadIdx.x == 0 && s_new) {
         *it.box_new_it = iter + 1;
         atomicAdd(&it.ctl->new_edges, s_new);
+        if (it.box_edges) atomicAdd(it.box_edges, s_new);
     }
     __syncthreads();
     }
@@ -468,6 +533,13 @@ __device__ void control_body(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaG
             // extraction ran in this pass: the iteration is complete
             c.iters_done = c.iter;
             c.edges_total += c.new_edges;
+            if (c.box_edges) {
+                const unsigned long long dense_at = (unsigned long long)c.n * c.n / kDenseDiv;
+                uint32_t m = 0;
+                for (uint32_t b = 0; b < c.n_boxes && b < 32u; ++b)
+                    if (c.box_edges[b] >= dense_at && dense_at > 0ull) m |= 1u << b;
+                c.dense_mask = m;
+            }
             if (c.new_edges == 0ull) {
                 c.phase = kPhaseDone;
             } else if (c.max_iter && c.iter >= c.max_iter) {
@@ -584,7 +656,8 @@ __global__ void __launch_bounds__(1024) k_control(QCtl *const *ctls, uint32_t nq
 
 // Reset the loop state of queries [0, nq) (start of a run).
 __global__ void k_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds,
-                            uint32_t max_passes, uint32_t n_levels, unsigned long long cyclic_mask) {
+                            uint32_t max_passes, uint32_t n_levels, unsigned long long cyclic_mask,
+                            unsigned long long *box_edges, uint32_t n_boxes, uint32_t n) {
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
         QCtl c;
         memset(&c, 0, sizeof(c));
@@ -599,6 +672,10 @@ __global__ void k_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, u
         c.level = 0;
         c.n_levels = n_levels;
         c.cyclic_mask = cyclic_mask;
+        c.box_edges = box_edges;
+        c.n_boxes = n_boxes;
+        c.n = n;
+        c.dense_mask = 0;
         *ctls[q] = c;
     }
 }
@@ -611,6 +688,7 @@ struct EpsDesc {
     uint64_t *m2, *a2;
     uint32_t *a2_it, *box_new_it;
     QCtl *ctl;
+    unsigned long long *box_edges;
     uint32_t n, W;
 };
 __global__ void k_eps_init(const EpsDesc *__restrict__ eds, uint32_t ned) {
@@ -627,6 +705,7 @@ __global__ void k_eps_init(const EpsDesc *__restrict__ eds, uint32_t ned) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             *d.box_new_it = 1;
             atomicAdd(&d.ctl->edges_total, (unsigned long long)d.n);
+            if (d.box_edges) atomicAdd(d.box_edges, (unsigned long long)d.n);
         }
     }
 }
@@ -853,8 +932,10 @@ cudaError_t launch_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGra
 }
 
 cudaError_t launch_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds,
-                             uint32_t max_passes, uint32_t n_levels, unsigned long long cyclic_mask, cudaStream_t st) {
-    k_ctl_reset<<<(nq + 255) / 256, 256, 0, st>>>(ctls, nq, max_iter, max_rounds, max_passes, n_levels, cyclic_mask);
+                             uint32_t max_passes, uint32_t n_levels, unsigned long long cyclic_mask,
+                             unsigned long long *box_edges, uint32_t n_boxes, uint32_t n, cudaStream_t st) {
+    k_ctl_reset<<<(nq + 255) / 256, 256, 0, st>>>(ctls, nq, max_iter, max_rounds, max_passes, n_levels, cyclic_mask,
+                                                  box_edges, n_boxes, n);
     return cudaGetLastError();
 }
 
@@ -865,9 +946,9 @@ cudaError_t launch_eps_init(const void *eds, uint32_t ned, uint32_t grid, cudaSt
 }
 
 size_t eps_desc_size() { return sizeof(EpsDesc); }
-void fill_eps_desc(void *dst, uint64_t *m2, uint64_t *a2, uint32_t *a2_it, uint32_t *box_new_it, QCtl *ctl, uint32_t n,
-                   uint32_t W) {
-    EpsDesc d{m2, a2, a2_it, box_new_it, ctl, n, W};
+void fill_eps_desc(void *dst, uint64_t *m2, uint64_t *a2, uint32_t *a2_it, uint32_t *box_new_it, QCtl *ctl,
+                   unsigned long long *box_edges, uint32_t n, uint32_t W) {
+    EpsDesc d{m2, a2, a2_it, box_new_it, ctl, box_edges, n, W};
     memcpy(dst, &d, sizeof(d));
 }
 

@@ -74,6 +74,8 @@ int cfpq_server_create(cfpq_server **out, const cfpq_options *opt, void *stream,
             cfpq_default_options(&s->opt);
         }
         if ((s->opt.alloc == nullptr) != (s->opt.free == nullptr)) return CFPQ_ERR_INVALID_ARG;
+        if (s->opt.closure_mode > CFPQ_CLOSURE_TC_I8) return CFPQ_ERR_INVALID_ARG;
+        if (s->opt.closure_mode == CFPQ_CLOSURE_TC_I8) return CFPQ_ERR_UNSUPPORTED;
         if (cudaSetDevice(s->opt.device) != cudaSuccess) {
             cudaGetLastError();
             return CFPQ_ERR_CUDA;
@@ -114,7 +116,7 @@ int cfpq_submit(cfpq_server *s, const cfpq_rsm *rsm, uint64_t *ticket) {
     try {
         cfpq_server::Job j;
         j.q.reset(new QueryDev());
-        j.q->closure_mode = s->opt.closure_mode == CFPQ_CLOSURE_TC_FP8 ? CFPQ_CLOSURE_TC_FP8 : CFPQ_CLOSURE_BITPACKED;
+        j.q->closure_mode = s->opt.closure_mode;
         std::string e;
         int rc = copy_rsm(rsm, &j.q->rsm, &e);
         if (rc) return sfail(s, rc, e);

@@ -164,6 +164,7 @@ __device__ __forceinline__ bool tc_job_active(const TcJob &j, uint32_t *thr, uin
     }
     const QCtl *c = j.ctl;
     if (c->phase != kPhaseRun || c->level != j.level) return false;
+    if (j.switchable && (j.box >= 32u || !((c->dense_mask >> j.box) & 1u))) return false;
     *iter = c->iter;
     *g = c->g;
     const uint32_t g0 = c->g_iter_start;
@@ -188,7 +189,34 @@ __device__ __forceinline__ bool tc_job_active(const TcJob &j, uint32_t *thr, uin
     return false;
 }
 
-__global__ void __launch_bounds__(tc::kThreads, 1)
+// The inner dimension of a job in this pass: compacted (the dirty rows listed
+// by k_tc_rows, A's columns gathered by k_tc_cols) when the job has buffers
+// and the list fits them, else all n rows with a stamp filter.
+struct KDim {
+    const uint64_t *A;
+    uint32_t wa;      // words per row of A
+    uint32_t kdim;    // rows of the inner dimension
+    bool compact;
+};
+
+__device__ __forceinline__ KDim job_kdim(const TcJob &J, uint32_t g) {
+    KDim k{J.A, J.W, J.B ? J.n : 0u, false};
+    if (J.ys && J.kcount) {
+        const unsigned long long kc = *reinterpret_cast<volatile unsigned long long *>(J.kcount);
+        const uint32_t d = ((uint32_t)(kc >> 32) == g) ? (uint32_t)kc : 0u;
+        if (d <= J.Wc * 64u) k = KDim{J.ac, J.Wc, d, true};
+    }
+    return k;
+}
+
+// Operand bits of one K stage held in registers: A, 64 bits of row m0 + tid/2;
+// B, 4 x 32 bits of one row (see the layout below).
+struct TcStage {
+    uint64_t a;
+    uint32_t b[4];
+};
+
+__global__ void __launch_bounds__(tc::kThreads, 2)
     k_tc_product(const TcJob *__restrict__ jobs, ExecTables T, int *err_flag) {
     constexpr bool INT8 = false;
     using namespace tc;
@@ -197,6 +225,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     __shared__ uint32_t tmem_base;
     __shared__ uint32_t s_changed_rows;
     __shared__ uint8_t s_row_changed[kBM];
+    __shared__ uint32_t s_flags[2][kThreads / 32];
 
     const uint32_t total = *T.t_total;
     if (blockIdx.x >= total) return;
@@ -215,9 +244,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     const uint32_t tmem = tmem_base;
     constexpr uint32_t idesc = INT8 ? make_idesc(2, kBM, kBN) : make_idesc(1, kBM, kBN);
     uint32_t parity[2] = {0u, 0u};
+    bool inflight[2] = {false, false};
+    int buf = 0;
     bool timed_out = false;
+    // A: thread = (row ar, half ah) of the 128 x 128-bit stage.  B: 32 blocks
+    // of 32 rows x 32 columns; warp w loads rows 32 * (w / 2) + lane of the
+    // stage, columns n0 + 128 * (w % 2) + 32 * b.
+    const uint32_t ar = (uint32_t)tid >> 1, ah = (uint32_t)tid & 1u;
 
-    for (uint32_t li = blockIdx.x; li < total && !timed_out; li += gridDim.x) {
+    for (uint32_t li = blockIdx.x; li < total; li += gridDim.x) {
         // live tile li -> query -> job (tile0 is relative to the query's level group)
         const uint32_t q = find_owner(T.t_pre, T.nq, li);
         const uint32_t ti = li - T.t_pre[q];
@@ -229,86 +264,128 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         }
         const TcJob &J = jobs[lo];
         uint32_t thr, iter, g;
-        if (!tc_job_active(J, &thr, &iter, &g)) continue;
         const uint32_t t = ti - J.tile0;
-        if (t >= J.tiles_m * J.tiles_n) continue;
+        const bool act = tc_job_active(J, &thr, &iter, &g) && t < J.tiles_m * J.tiles_n;
+        const KDim K = act ? job_kdim(J, g) : KDim{nullptr, 0u, 0u, false};
+        if (!act || (K.kdim == 0u && !J.ident)) {
+            // skip the rest of this job's tiles in this CTA's stride
+            const uint32_t left = J.tiles_m * J.tiles_n > t ? J.tiles_m * J.tiles_n - t : 1u;
+            li += ((left - 1u) / gridDim.x) * gridDim.x;
+            continue;
+        }
         const uint32_t m0 = (t / J.tiles_n) * kBM, n0 = (t % J.tiles_n) * kBN;
         const uint32_t n = J.n, W = J.W;
+        const uint32_t kwords = (K.kdim + 63u) >> 6;
         if (tid < kBM) s_row_changed[tid] = 0;
         if (tid == 0) s_changed_rows = 0;
-        bool inflight[2] = {false, false};
         bool started = false;
-        int buf = 0;
-        const uint32_t ksteps = J.B ? (n + kBK - 1) / kBK : 0u;
+        uint32_t stages_run = 0;
+        const uint32_t ksteps = (K.kdim + kBK - 1) / kBK;
+        const uint32_t xa = m0 + ar;
+        const bool xa_ok = xa < n && (!J.a_it || J.a_it[xa] == iter);
 
-        for (uint32_t ks = 0; ks < ksteps && !timed_out; ++ks) {
-            const uint32_t k0 = ks * kBK;  // bits of A's columns / B's rows
-            // A: 256 threads x (half a row: 64 bits) of the 128 x 128-bit tile
-            const uint32_t ar = (uint32_t)tid >> 1, ah = (uint32_t)tid & 1u;
-            uint64_t abits = 0;
-            {
-                const uint32_t x = m0 + ar, w = (k0 >> 6) + ah;
-                if (x < n && w < W && (!J.a_it || J.a_it[x] == iter)) abits = J.A[(size_t)x * W + w];
-            }
-            // B: 32 blocks of 32 rows x 32 columns; warp w owns 4 of them:
-            // rows k0 + 32 * (w / 2) + lane, columns n0 + 128 * (w % 2) + 32 * b
-            uint32_t bword[4];
-            {
-                const uint32_t y = k0 + 32u * ((uint32_t)warp >> 1) + (uint32_t)lane;
-                const bool rok = y < n && (!J.b_stamp || thr == 0u || J.b_stamp[y] >= thr);
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const uint32_t zc = n0 + 128u * ((uint32_t)warp & 1u) + 32u * (uint32_t)b;
-                    uint32_t v = 0;
-                    if (rok && zc < (W << 6)) {
-                        const uint64_t wv = J.B[(size_t)y * W + (zc >> 6)];
-                        v = (uint32_t)(wv >> (zc & 63u));
-                    }
-                    bword[b] = v;
-                }
-            }
-            const int anyA = __syncthreads_or(abits != 0ull);
-            const int anyB = __syncthreads_or((bword[0] | bword[1] | bword[2] | bword[3]) != 0u);
-            if (!anyA || !anyB) continue;  // dirty-tile skip: this stage adds nothing
-
-            if (inflight[buf]) {  // the buffer must be free: wait for the MMAs that read it
-                if (!mbar_wait(&mbar[buf], parity[buf])) timed_out = true;
-                parity[buf] ^= 1u;
-                inflight[buf] = false;
-            }
-            if (__syncthreads_or(timed_out)) { timed_out = true; break; }
-            unsigned char *sa = stage[buf], *sb = stage[buf] + kStageA;
-#pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-                const uint32_t kg = ah * 4u + (uint32_t)qq;
-                *reinterpret_cast<uint4 *>(sa + core_off(ar, kg)) =
-                    expand16((uint32_t)(abits >> (16 * qq)) & 0xFFFFu, one);
+        auto load = [&](uint32_t ks, TcStage &st) {
+            const uint32_t k0 = ks * kBK;
+            const uint32_t w = (k0 >> 6) + ah;
+            st.a = (xa_ok && w < kwords) ? K.A[(size_t)xa * K.wa + w] : 0ull;
+            const uint32_t kk = k0 + 32u * ((uint32_t)warp >> 1) + (uint32_t)lane;
+            uint32_t y = kk;
+            bool rok;
+            if (K.compact) {
+                rok = kk < K.kdim;
+                y = rok ? J.ys[kk] : 0u;
+            } else {
+                rok = kk < n && (!J.b_stamp || thr == 0u || J.b_stamp[kk] >= thr);
             }
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const uint32_t col = transpose32(bword[b], lane);  // bit i = row 32 * (warp/2) + i
-                const uint32_t z = 128u * ((uint32_t)warp & 1u) + 32u * (uint32_t)b + (uint32_t)lane;
-                const uint32_t kg = 2u * ((uint32_t)warp >> 1);
-                *reinterpret_cast<uint4 *>(sb + core_off(z, kg)) = expand16(col & 0xFFFFu, one);
-                *reinterpret_cast<uint4 *>(sb + core_off(z, kg + 1u)) = expand16(col >> 16, one);
+                const uint32_t zc = n0 + 128u * ((uint32_t)warp & 1u) + 32u * (uint32_t)b;
+                uint32_t v = 0;
+                if (rok && zc < (W << 6)) v = (uint32_t)(J.B[(size_t)y * W + (zc >> 6)] >> (zc & 63u));
+                st.b[b] = v;
             }
-            fence_async_smem();
+        };
+        // per-warp flags of a stage: bit 0 some A bit, bit 1 some B bit, bit 2 a wait timed out
+        auto flags_of = [&](const TcStage &st) -> uint32_t {
+            const bool fa = __any_sync(0xffffffffu, st.a != 0ull);
+            const bool fb = __any_sync(0xffffffffu, (st.b[0] | st.b[1] | st.b[2] | st.b[3]) != 0u);
+            return (fa ? 1u : 0u) | (fb ? 2u : 0u);
+        };
+
+        TcStage s0{0ull, {0u, 0u, 0u, 0u}}, s1{0ull, {0u, 0u, 0u, 0u}}, s2{0ull, {0u, 0u, 0u, 0u}};
+        if (ksteps > 0) load(0, s0);
+        if (ksteps > 1) load(1, s1);
+        {
+            const uint32_t f = ksteps > 0 ? flags_of(s0) : 0u;
+            if (lane == 0) s_flags[0][warp] = f;
+        }
+        __syncthreads();
+        for (uint32_t ks = 0; ks < ksteps; ++ks) {
+            // flags of stage ks were published before the last barrier
+            uint32_t fa = 0u, fb = 0u, fx = 0u;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) {
+                const uint32_t f = s_flags[ks & 1u][w];
+                fa |= f & 1u;
+                fb |= f & 2u;
+                fx |= f & 4u;
+            }
+            if (fx) {
+                timed_out = true;
+                break;
+            }
+            if (ks + 2 < ksteps) load(ks + 2, s2);  // two stages in flight
+            const bool run = fa && fb;              // dirty-tile skip: a stage with no A or no B bit adds nothing
+            bool my_to = false;
+            if (run) {
+                if (inflight[buf]) {  // the buffer must be free: wait for the MMAs that read it
+                    if (!mbar_wait(&mbar[buf], parity[buf])) my_to = true;
+                    parity[buf] ^= 1u;
+                    inflight[buf] = false;
+                }
+                unsigned char *sa = stage[buf], *sb = stage[buf] + kStageA;
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    const uint32_t kg = ah * 4u + (uint32_t)qq;
+                    *reinterpret_cast<uint4 *>(sa + core_off(ar, kg)) =
+                        expand16((uint32_t)(s0.a >> (16 * qq)) & 0xFFFFu, one);
+                }
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const uint32_t col = transpose32(s0.b[b], lane);  // bit i = row 32 * (warp/2) + i
+                    const uint32_t z = 128u * ((uint32_t)warp & 1u) + 32u * (uint32_t)b + (uint32_t)lane;
+                    const uint32_t kg = 2u * ((uint32_t)warp >> 1);
+                    *reinterpret_cast<uint4 *>(sb + core_off(z, kg)) = expand16(col & 0xFFFFu, one);
+                    *reinterpret_cast<uint4 *>(sb + core_off(z, kg + 1u)) = expand16(col >> 16, one);
+                }
+                fence_async_smem();
+            }
+            {
+                uint32_t f = ks + 1 < ksteps ? flags_of(s1) : 0u;
+                if (__any_sync(0xffffffffu, my_to)) f |= 4u;
+                if (lane == 0) s_flags[(ks + 1) & 1u][warp] = f;
+            }
             tc_before();
             __syncthreads();
             tc_after();
-            if (tid == 0) {
-                const uint32_t abase = smem_u32(sa), bbase = smem_u32(sb);
+            if (run) {
+                if (tid == 0) {
+                    const uint32_t abase = smem_u32(stage[buf]), bbase = smem_u32(stage[buf] + kStageA);
 #pragma unroll
-                for (int kk = 0; kk < kBK / 32; ++kk) {
-                    const uint64_t ad = make_desc(abase + (uint32_t)kk * 256u, 128u, kKG * 128u);
-                    const uint64_t bd = make_desc(bbase + (uint32_t)kk * 256u, 128u, kKG * 128u);
-                    tc::mma(INT8, tmem, ad, bd, idesc, (started || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < kBK / 32; ++kk) {
+                        const uint64_t ad = make_desc(abase + (uint32_t)kk * 256u, 128u, kKG * 128u);
+                        const uint64_t bd = make_desc(bbase + (uint32_t)kk * 256u, 128u, kKG * 128u);
+                        tc::mma(INT8, tmem, ad, bd, idesc, (started || kk > 0) ? 1u : 0u);
+                    }
+                    mma_commit(&mbar[buf]);
                 }
-                mma_commit(&mbar[buf]);
+                started = true;
+                ++stages_run;
+                inflight[buf] = true;
+                buf ^= 1;
             }
-            started = true;
-            inflight[buf] = true;
-            buf ^= 1;
+            s0 = s1;
+            s1 = s2;
         }
         for (int b = 0; b < 2; ++b) {  // drain
             if (inflight[b]) {
@@ -373,7 +450,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 if (J.out_last) *J.out_last = g;
                 if (J.ctl) atomicAdd(&J.ctl->changed_rows, (unsigned long long)s_changed_rows);
             }
-            if (J.ctl && started) atomicAdd(&J.ctl->tile_mmas, 1ull);
+            if (J.ctl && started) {
+                atomicAdd(&J.ctl->tile_mmas, 1ull);
+                atomicAdd(&J.ctl->tile_kstages, (unsigned long long)stages_run);
+            }
         }
         __syncthreads();
     }
@@ -384,11 +464,126 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
+// ---------------------------------------------------------------------------
+// Dirty-row compaction of the product jobs (channels 2 and 4).
+// ---------------------------------------------------------------------------
+constexpr uint32_t kRowChunk = 2048;  // k_tc_rows: rows per unit
+constexpr uint32_t kColRows = 8;      // k_tc_cols: rows per unit (one per warp)
+constexpr uint32_t kColMaxW = 1024;   // largest row in words (n <= 65536)
+constexpr uint32_t kCasLimit = 1u << 20;
+
+// Reserve `cnt` entries of the job's list for pass g; the count word carries
+// the pass stamp, so the first reservation of a pass starts from 0.
+__device__ __forceinline__ uint32_t reserve_rows(unsigned long long *kc, uint32_t g, uint32_t cnt, int *err_flag) {
+    unsigned long long old = *reinterpret_cast<volatile unsigned long long *>(kc);
+    for (uint32_t i = 0; i < kCasLimit; ++i) {
+        const uint32_t cur = ((uint32_t)(old >> 32) == g) ? (uint32_t)old : 0u;
+        const unsigned long long nw = ((unsigned long long)g << 32) | (unsigned long long)(cur + cnt);
+        const unsigned long long prev = atomicCAS(kc, old, nw);
+        if (prev == old) return cur;
+        old = prev;
+    }
+    atomicOr(err_flag, 2);
+    return 0xFFFFFFFFu;
+}
+
+// Units (job, chunk) of the live jobs are numbered in job order; the CTA
+// takes those congruent to its index.  `body(J, c)` runs for each.
+template <typename F>
+__device__ __forceinline__ void for_job_chunks(const TcJob *jobs, const ExecTables &T, uint32_t rows_per_chunk,
+                                               F body) {
+    uint32_t u0 = 0;
+    for (uint32_t q = 0; q < T.nq; ++q) {
+        const uint32_t jb = T.t_job_beg[q], je = T.t_job_end[q];
+        for (uint32_t j = jb; j < je; ++j) {
+            const TcJob &J = jobs[j];
+            const uint32_t chunks = (J.n + rows_per_chunk - 1) / rows_per_chunk;
+            const uint32_t first = (blockIdx.x + gridDim.x - (u0 % gridDim.x)) % gridDim.x;
+            u0 += chunks;
+            if (first >= chunks || !J.ys) continue;
+            for (uint32_t c = first; c < chunks; c += gridDim.x) body(J, c);
+        }
+    }
+}
+
+// List the rows y of B with stamp >= thr (order irrelevant: the product sums
+// over them).
+__global__ void __launch_bounds__(256) k_tc_rows(const TcJob *__restrict__ jobs, ExecTables T, int *err_flag) {
+    const int lane = threadIdx.x & 31;
+    for_job_chunks(jobs, T, kRowChunk, [&](const TcJob &J, uint32_t c) {
+        uint32_t thr, iter, g;
+        if (!tc_job_active(J, &thr, &iter, &g) || !J.b_stamp) return;
+        const uint32_t y_end = min(J.n, (c + 1u) * kRowChunk);
+        for (uint32_t y0 = c * kRowChunk; y0 < y_end; y0 += blockDim.x) {
+            const uint32_t y = y0 + threadIdx.x;
+            const bool dirty = y < y_end && J.b_stamp[y] >= thr;
+            const unsigned bal = __ballot_sync(0xffffffffu, dirty);
+            if (!bal) continue;
+            uint32_t base = 0;
+            if (lane == 0) base = reserve_rows(J.kcount, g, (uint32_t)__popc(bal), err_flag);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (dirty && base != 0xFFFFFFFFu) J.ys[base + (uint32_t)__popc(bal & ((1u << lane) - 1u))] = y;
+        }
+    });
+}
+
+// ac[x][k] = A[x][ys[k]] for k < D, one warp per row x: the row is staged in
+// shared memory, lanes test 64 listed columns per step and ballot them into a
+// word; 32 words are written at once.
+__global__ void __launch_bounds__(256) k_tc_cols(const TcJob *__restrict__ jobs, ExecTables T, uint32_t max_w) {
+    extern __shared__ uint64_t s_rowbuf[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t *row = s_rowbuf + (size_t)warp * max_w;
+    for_job_chunks(jobs, T, kColRows, [&](const TcJob &J, uint32_t c) {
+        uint32_t thr, iter, g;
+        if (!tc_job_active(J, &thr, &iter, &g)) return;
+        const KDim K = job_kdim(J, g);
+        if (!K.compact || K.kdim == 0u) return;
+        const uint32_t x = c * kColRows + (uint32_t)warp;
+        if (x >= J.n) return;
+        const uint32_t W = J.W, D = K.kdim, nw = (D + 63u) >> 6;
+        const uint4 *src = reinterpret_cast<const uint4 *>(J.A + (size_t)x * W);
+        bool nz = false;
+        for (uint32_t v = (uint32_t)lane; v < W / 2u; v += 32u) {
+            const uint4 t4 = src[v];
+            reinterpret_cast<uint4 *>(row)[v] = t4;
+            nz |= (t4.x | t4.y | t4.z | t4.w) != 0u;
+        }
+        nz = __any_sync(0xffffffffu, nz);
+        __syncwarp();
+        uint64_t *dst = J.ac + (size_t)x * J.Wc;
+        for (uint32_t wb = 0; wb < nw; wb += 32u) {
+            uint64_t mine = 0ull;
+            const uint32_t wend = min(nw, wb + 32u);
+            if (nz) {
+                for (uint32_t w = wb; w < wend; ++w) {
+                    const uint32_t k0 = w * 64u + (uint32_t)lane, k1 = k0 + 32u;
+                    bool b0 = false, b1 = false;
+                    if (k0 < D) {
+                        const uint32_t y = __ldg(J.ys + k0);
+                        b0 = (row[y >> 6] >> (y & 63u)) & 1ull;
+                    }
+                    if (k1 < D) {
+                        const uint32_t y = __ldg(J.ys + k1);
+                        b1 = (row[y >> 6] >> (y & 63u)) & 1ull;
+                    }
+                    const unsigned lo = __ballot_sync(0xffffffffu, b0), hi2 = __ballot_sync(0xffffffffu, b1);
+                    if ((uint32_t)lane == w - wb) mine = (uint64_t)lo | ((uint64_t)hi2 << 32);
+                }
+            }
+            if (wb + (uint32_t)lane < wend) dst[wb + lane] = mine;
+        }
+        __syncwarp();  // the next row reuses the staging buffer
+    });
+}
+
+static int g_tc_sms[64];
+
 int tc_smem_bytes() { return 2 * tc::kStageBytes; }
 
 // Persistent launch: at most two CTAs per SM (96 KiB of shared memory and 256
 // TMEM columns each), walking the live tiles of the pass.
-static int g_tc_sms[64];
+
 
 // Set the kernel's shared-memory limit and record the SM count (call outside
 // any stream capture).
@@ -399,6 +594,9 @@ cudaError_t prepare_tc_launch() {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (g_tc_sms[dev]) return cudaSuccess;
     e = cudaFuncSetAttribute(k_tc_product, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_cols, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kColMaxW * 8u * (256u / 32u)));
     if (e != cudaSuccess) return e;
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -419,6 +617,20 @@ cudaError_t launch_tc_product(bool int8, const TcJob *jobs, uint32_t max_tiles, 
     uint32_t grid = (uint32_t)sms * 2u;
     if (max_tiles < grid) grid = max_tiles;
     k_tc_product<<<grid, tc::kThreads, smem, st>>>(jobs, T, err_flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_compact(const TcJob *jobs, const ExecTables &T, uint32_t max_w, int *err_flag, cudaStream_t st) {
+    if (max_w == 0) return cudaSuccess;
+    if (max_w > kColMaxW) return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int sms = (dev >= 0 && dev < 64 && g_tc_sms[dev]) ? g_tc_sms[dev] : 0;
+    if (!sms) return cudaErrorNotReady;  // prepare_tc_launch was not called
+    k_tc_rows<<<(unsigned)sms * 4u, 256, 0, st>>>(jobs, T, err_flag);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_tc_cols<<<(unsigned)sms * 4u, 256, (size_t)max_w * 8u * 8u, st>>>(jobs, T, max_w);
     return cudaGetLastError();
 }
 

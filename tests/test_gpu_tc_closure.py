@@ -91,3 +91,45 @@ def test_int8_mode_is_rejected(C):
     with pytest.raises(C.CfpqError) as e:
         C.Context(closure_mode=C.CFPQ_CLOSURE_TC_I8)
     assert e.value.status == C.CFPQ_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("n", [512, 2048, 4096])
+def test_auto_dense_tiles_dyck(C, n):
+    """AUTO moves the products of Dyck-4's dense nonterminal matrix with the
+    dirty closure rows to tensor-core tiles; the answer equals the row-gather
+    closure and the oracle."""
+    g, r = W.dyck_zipf(n)
+    _, s1, a = _run(g, r, C.CFPQ_CLOSURE_AUTO, no_single_cta=1)
+    _, s2, b = _run(g, r, C.CFPQ_CLOSURE_BITPACKED)
+    assert (a == b).all()
+    assert s1.iterations == s2.iterations
+    if n >= 2048:                    # S is denser than 1/32 there: dense tiles ran
+        assert s1.tile_mmas > 0
+    if n <= 2048:
+        assert (a == oracle.worklist(g, r)).all()
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_auto_random_dense_boxes(C, seed):
+    rng = np.random.Generator(np.random.PCG64(900 + seed))
+    n = int(rng.integers(20, 700))
+    g, r = W.small_random_instance(900 + seed, n=n, m=int(rng.integers(n, 6 * n)),
+                                   n_labels=int(rng.integers(1, 3)), max_states=14)
+    c1, s1, a = _run(g, r, C.CFPQ_CLOSURE_AUTO, no_single_cta=1)
+    c2, s2, b = _run(g, r, C.CFPQ_CLOSURE_BITPACKED, no_single_cta=1)
+    assert (a == b).all() and s1.iterations == s2.iterations
+    rows = [(s, x) for s in range(r.n_states) for x in range(0, n, max(1, n // 9))]
+    assert (c1.closure_rows(rows) == c2.closure_rows(rows)).all()
+    if n <= 300:
+        assert (a == oracle.worklist(g, r)).all()
+
+
+def test_auto_batch_dense_boxes(C):
+    qs = [W.dyck_zipf(n, seed=40 + i) for i, n in enumerate([300, 700, 1200])]
+    qs += W.batched_queries(count=5, n_min=100, n_max=600, seed=12)
+    ctx = C.Context(closure_mode=C.CFPQ_CLOSURE_AUTO)
+    per, tot = ctx.batch_run(qs)
+    for i, (g, r) in enumerate(qs):
+        want = oracle.worklist(g, r)
+        for b in range(r.n_boxes):
+            assert (ctx.batch_reachable_bits(i, b) == want[b]).all()
