@@ -154,18 +154,24 @@ struct TcJob {
     uint32_t tile0;             // first global tile index of this job
     uint32_t box;               // nonterminal label (switchable jobs)
     uint32_t switchable;        // active only while the box is dense (closure mode AUTO)
-    uint32_t Wc;                // words per row of `ac`; at most Wc * 64 compacted rows
+    uint32_t kcap;              // most compacted rows (a multiple of 128)
     // Dirty-row compaction (channels 2 and 4): before the products of a pass,
-    // the B rows with stamp >= thr are listed in `ys` and the columns of A at
-    // those rows gathered into `ac`, so that the product's inner dimension
-    // runs over the dirty rows only.  `kcount` = (pass stamp << 32) | count.
+    // the B rows with stamp >= thr are listed in `ys`; A's columns at those
+    // rows and the listed B rows are expanded to 0/1 FP8 bytes, A as
+    // a8[x][k] (n rows of kcap bytes), B transposed as b8[z][k] (n_pad rows
+    // of kcap bytes), and the product runs its inner dimension over the
+    // listed rows only, operands brought in by TMA.  kcount = (pass stamp <<
+    // 32) | count.  A job whose list is longer than kcap runs uncompacted.
     uint32_t *ys;
     unsigned long long *kcount;
-    uint64_t *ac;
+    uint8_t *a8;
+    uint8_t *b8;
+    uint32_t map;               // index of the job's pair of tensor maps (a8, b8)
+    uint32_t pad3;
 };
 
 constexpr uint32_t kDenseDiv = 32;  // a box is dense from n^2 / 32 edges on (one bit in two words)
-constexpr uint32_t kAutoTilesMinN = 2048;  // AUTO switches boxes to tile products only from this n on
+constexpr uint32_t kAutoTilesMinN = 8192;  // AUTO switches boxes to tile products only from this n on
 
 // Per-executor work tables.  Items of each kind are sorted by (query, level);
 // the static tables give, for query q and level L, the first item of that

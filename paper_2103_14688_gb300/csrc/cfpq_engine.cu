@@ -266,7 +266,8 @@ int QueryDev::plan(std::string *err) {
     // Sources of block (s,t): transitions s -l-> u with u == t or t reachable from u.
     srcs.clear();
     n_tc_src = 0;
-    Wc = std::max<uint32_t>(2u, ((W + 3u) / 4u + 1u) & ~1u);
+    // compacted inner dimension: up to half of the rows, a multiple of 128
+    kcap = std::max<uint32_t>(128u, ((W * 32u) + 127u) & ~127u);
     blk_src0.assign(blocks.size(), 0);
     blk_nsrc.assign(blocks.size(), 0);
     for (size_t b = 0; b < blocks.size(); ++b) {
@@ -329,7 +330,7 @@ int QueryDev::plan(std::string *err) {
 }
 
 uint64_t QueryDev::tc_slot_bytes() const {
-    return (uint64_t)W * 64 * 4 + 256 + (uint64_t)n * Wc * 8;
+    return (uint64_t)W * 64 * 4 + 256 + ((uint64_t)n + (uint64_t)W * 64) * kcap;
 }
 
 uint64_t QueryDev::footprint() const {
@@ -477,6 +478,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     std::vector<uint32_t> t_lvl((size_t)nq * maxL1, 0), t_lvl_tiles((size_t)nq * maxL1, 0);
     max_tc_tiles = 0;
     max_tc_w = 0;
+    uint32_t n_maps = 0;
     uint32_t live_bound[kClasses] = {0};
     for (uint32_t qi = 0; qi < nq; ++qi) {
         QueryDev &q = *qs[qi];
@@ -589,10 +591,12 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                     j.tiles_n = tiles_n;
                     j.box = sd.label_kind == 1 ? sd.label : 0u;
                     j.switchable = sd.box_switch;
-                    j.Wc = q.Wc;
+                    j.kcap = q.kcap;
                     j.ys = q.tc_ys((uint32_t)sd.tc_slot);
                     j.kcount = q.tc_kcount((uint32_t)sd.tc_slot);
-                    j.ac = q.tc_ac((uint32_t)sd.tc_slot);
+                    j.a8 = q.tc_a8((uint32_t)sd.tc_slot);
+                    j.b8 = q.tc_b8((uint32_t)sd.tc_slot);
+                    j.map = n_maps++;
                     j.tile0 = lvl_tiles;
                     lvl_tiles += tiles_m * tiles_n;
                     hj.push_back(j);
@@ -650,6 +654,12 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     if ((rc = upload(fds, hf.data(), hf.size() * sizeof(FDesc)))) return rc;
     if ((rc = upload(tcjobs, hj.data(), hj.size() * sizeof(TcJob)))) return rc;
     n_tcjobs = (uint32_t)hj.size();
+    // TMA descriptors of the jobs' FP8 operands (a8, b8 per job)
+    if (n_maps) {
+        std::vector<unsigned char> hm((size_t)n_maps * 2 * tc_map_bytes());
+        ENG_CK(tc_encode_maps(hj.data(), (uint32_t)hj.size(), hm.data()));
+        if ((rc = upload(tcmaps, hm.data(), hm.size()))) return rc;
+    }
     for (int v = 0; v < kClasses; ++v) {
         max_live[v] = live_bound[v];
         n_items[v] = (uint32_t)hi[v].size();
@@ -702,6 +712,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     ENG_CK(cudaMemsetAsync(tc_err.p, 0, 16, st));
     ENG_CK(cudaMemsetAsync(done_counter.p, 0, 16, st));
     if (n_tcjobs) ENG_CK(prepare_tc_launch());
+    ENG_CK(prepare_gather_launch());
     ENG_CK(cudaStreamSynchronize(st));
     drop_graph();
     built = true;
@@ -730,6 +741,7 @@ int Executor::enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int us
     if (n_tcjobs) {
         ENG_CK(launch_tc_compact(tcjobs.as<TcJob>(), T, max_tc_w, tc_err.as<int>(), st));
         ENG_CK(launch_tc_product(false, tcjobs.as<TcJob>(), max_tc_tiles, T, tc_err.as<int>(), st));
+        ENG_CK(launch_tc_product_tma(tcjobs.as<TcJob>(), tcmaps.p, max_tc_tiles, T, tc_err.as<int>(), st));
     }
     if (ev_after) ENG_CK(cudaEventRecord(ev_after, st));
     // the last extraction launch of the pass also runs the loop control

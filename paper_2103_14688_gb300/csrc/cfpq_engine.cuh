@@ -22,10 +22,19 @@ cudaError_t launch_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGra
                            int *running_out, const ExecTables &T, int advance, cudaStream_t st);
 cudaError_t launch_tc_product(bool int8, const TcJob *jobs, uint32_t max_tiles, const ExecTables &T, int *err_flag,
                               cudaStream_t st);
-// Per pass, before launch_tc_product: list each live job's dirty B rows and
-// gather A's columns at them (max_w = the largest W of any job).
+// Per pass, before the products: list each live job's dirty B rows and
+// expand A's columns and B's rows at them to FP8 (max_w = the largest W).
 cudaError_t launch_tc_compact(const TcJob *jobs, const ExecTables &T, uint32_t max_w, int *err_flag, cudaStream_t st);
+// Products of the compacted jobs: TMA-fed tcgen05 pipeline (maps = the
+// jobs' tensor maps, two per job, from tc_encode_maps).
+cudaError_t launch_tc_product_tma(const TcJob *jobs, const void *maps, uint32_t max_tiles, const ExecTables &T,
+                                  int *err_flag, cudaStream_t st);
+// Bytes of one tensor map; encode the a8/b8 maps of every job with buffers
+// (job.map indexes pairs) into host memory.
+size_t tc_map_bytes();
+cudaError_t tc_encode_maps(const TcJob *jobs, uint32_t n_jobs, void *out);
 cudaError_t prepare_tc_launch();
+cudaError_t prepare_gather_launch();
 cudaError_t launch_csr_to_bits(const uint32_t *off, const uint32_t *col, size_t rows, uint32_t W, uint64_t *bits,
                                cudaStream_t st);
 cudaError_t launch_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds,
@@ -154,17 +163,19 @@ struct QueryDev {
     };
     std::vector<uint32_t> blk_pure_n, blk_pure_lbl;  // per block: labels of a pure-terminal block (<= 2)
     // Product jobs' compaction buffers, one slot per tile source: the dirty
-    // row list (n_pad entries), its pass-stamped count, and A's gathered
-    // columns (n rows of Wc words).
+    // row list (n_pad entries), its pass-stamped count, A's columns at the
+    // listed rows as FP8 bytes (n rows of kcap) and the listed B rows
+    // transposed (n_pad rows of kcap).  Every part starts 128-byte aligned.
     DBuf tc_mem;
-    uint32_t n_tc_src = 0, Wc = 0;
+    uint32_t n_tc_src = 0, kcap = 0;
     uint64_t tc_slot_bytes() const;
     unsigned char *tc_slot(uint32_t k) const { return tc_mem.as<unsigned char>() + (size_t)k * tc_slot_bytes(); }
     uint32_t *tc_ys(uint32_t k) const { return reinterpret_cast<uint32_t *>(tc_slot(k)); }
     unsigned long long *tc_kcount(uint32_t k) const {
         return reinterpret_cast<unsigned long long *>(tc_slot(k) + (size_t)W * 64 * 4);
     }
-    uint64_t *tc_ac(uint32_t k) const { return reinterpret_cast<uint64_t *>(tc_slot(k) + (size_t)W * 64 * 4 + 256); }
+    uint8_t *tc_a8(uint32_t k) const { return tc_slot(k) + (size_t)W * 64 * 4 + 256; }
+    uint8_t *tc_b8(uint32_t k) const { return tc_a8(k) + (size_t)n * kcap; }
     std::vector<uint32_t> blk_src0, blk_nsrc;  // per block
     std::vector<uint32_t> blk_level;           // per block, 0..n_levels-1
     uint32_t n_levels = 1;
@@ -195,7 +206,7 @@ struct QueryDev {
 struct Executor {
     std::vector<QueryDev *> qs;
     DBuf ctl_ptrs, mirror, items[kClasses], xitems[kClasses], srcs, fds, running;
-    DBuf tcjobs, tables, tc_err, done_counter;
+    DBuf tcjobs, tcmaps, tables, tc_err, done_counter;
     ExecTables T;
     uint32_t n_items[kClasses] = {0}, n_xitems[kClasses] = {0};
     uint32_t max_live[kClasses] = {0};  // bound on live items of a pass: sum over queries of the largest level

@@ -103,6 +103,26 @@ __device__ __forceinline__ void or_pure_rows(uint4 (&acc)[VPL], const SrcDesc &d
     }
 }
 
+// Asynchronous 16-byte global -> shared copy (zero-filled when !valid); the
+// copies of a thread form groups it can wait for.
+__device__ __forceinline__ void cp_async16(uint4 *dst, const void *src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Source rows a warp of the general gather keeps in flight (shared-memory
+// ring), for rows of 4+ vectors per lane where registers allow only one row
+// load at a time; narrower rows batch their loads in registers.
+template <int VPL>
+struct GatherRing {
+    static constexpr bool on = VPL >= 4;
+    static constexpr int depth = VPL <= 8 ? 4 : 3;
+    static constexpr size_t bytes = on ? (size_t)8 * depth * 32 * VPL * 16 : 0;  // 8 warps
+};
+
 // Lowest set bit of a 128-bit vector, -1 if none; clears it when `clear`.
 __device__ __forceinline__ int lowbit4(uint4 &v, bool clear) {
     if (v.x) { int b = __ffs(v.x) - 1; if (clear) v.x &= v.x - 1; return b; }
@@ -153,6 +173,10 @@ template <int VPL, bool NT>
 __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
     k_gather(const GItem *__restrict__ items, const SrcDesc *__restrict__ srcs, ExecTables T, int cls) {
     __shared__ unsigned long long s_changed, s_ors;
+    // general variant: per-warp ring of source rows loaded with cp.async
+    extern __shared__ uint4 s_ring[];
+    constexpr int P = GatherRing<VPL>::depth;
+    uint4 *ring = s_ring + (size_t)(threadIdx.x >> 5) * P * 32 * VPL;
     // one CTA per live item (the grid covers every item of the class; CTAs
     // past the live count exit at once): a CTA that finishes early frees its
     // slot for the next one, which a persistent loop would not.
@@ -207,6 +231,56 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                     if constexpr (NT) {
                         if (d.pure_n && !use_ident) {
                             or_pure_rows<VPL>(acc, d, y_l, keep, lpr, gl, grp, gmask);
+                            return;
+                        }
+                        if (GatherRing<VPL>::on && d.rblk && !d.pure_n) {
+                            // Rows through the warp's shared-memory ring, P in
+                            // flight: row i is copied into slot i % P by
+                            // cp.async (each lane its own 16-byte pieces, so a
+                            // lane reads back only what it copied) and ORed
+                            // once P - 1 later rows have been issued.
+                            const unsigned bal = __ballot_sync(FULLMASK, keep);
+                            unsigned mine = (bal & gmask) >> (grp * lpr);
+                            uint32_t issued = 0, done = 0, vmask = 0;
+                            auto or_slot = [&](uint32_t sidx) {
+                                const uint4 *sl = ring + sidx * 32u * VPL;
+#pragma unroll
+                                for (int j = 0; j < VPL; ++j) or4(acc[j], sl[j * 32 + lane]);
+                            };
+                            while (__any_sync(FULLMASK, mine != 0u)) {
+                                const bool h = mine != 0u;
+                                const int pl = h ? __ffs(mine) - 1 : 0;
+                                if (h) mine &= mine - 1u;
+                                const uint32_t y = __shfl_sync(FULLMASK, y_l, pl, lpr);
+                                if (use_ident && h) set_row_bit<VPL>(acc, y, lpr, gl);
+                                const uint32_t sidx = issued % (uint32_t)P;
+                                if (h) {
+                                    uint4 *sl = ring + sidx * 32u * VPL;
+                                    const uint4 *r = reinterpret_cast<const uint4 *>(d.rblk + (size_t)y * W);
+#pragma unroll
+                                    for (int j = 0; j < VPL; ++j) {
+                                        const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
+                                        cp_async16(&sl[j * 32 + lane], r + (v < nvec ? v : 0u), v < nvec);
+                                    }
+                                    if (gl == 0) ++my_ors;
+                                    vmask |= 1u << sidx;
+                                } else {
+                                    vmask &= ~(1u << sidx);
+                                }
+                                cp_async_commit();
+                                ++issued;
+                                if (issued - done == (uint32_t)P) {
+                                    cp_async_wait<P - 1>();
+                                    const uint32_t ds = done % (uint32_t)P;
+                                    if ((vmask >> ds) & 1u) or_slot(ds);
+                                    ++done;
+                                }
+                            }
+                            cp_async_wait<0>();
+                            for (; done < issued; ++done) {
+                                const uint32_t ds = done % (uint32_t)P;
+                                if ((vmask >> ds) & 1u) or_slot(ds);
+                            }
                             return;
                         }
                     }
@@ -888,7 +962,7 @@ cudaError_t launch_gather(int vpl, bool nt, const GItem *items, uint32_t n_items
                           const ExecTables &T, int cls, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
 #define CFPQ_GATHER(V)                                                                         \
-    if (nt) k_gather<V, true><<<n_items, 256, 0, st>>>(items, srcs, T, cls);                   \
+    if (nt) k_gather<V, true><<<n_items, 256, GatherRing<V>::bytes, st>>>(items, srcs, T, cls); \
     else k_gather<V, false><<<n_items, 256, 0, st>>>(items, srcs, T, cls);
     switch (vpl) {
         case 1: CFPQ_GATHER(1) break;
@@ -900,6 +974,20 @@ cudaError_t launch_gather(int vpl, bool nt, const GItem *items, uint32_t n_items
     }
 #undef CFPQ_GATHER
     return cudaGetLastError();
+}
+
+// Shared-memory limits of the general gather variants (call outside any
+// stream capture).
+cudaError_t prepare_gather_launch() {
+#define CFPQ_RING(V)                                                                                      \
+    {                                                                                                     \
+        const cudaError_t e = cudaFuncSetAttribute(k_gather<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                   (int)GatherRing<V>::bytes);                            \
+        if (e != cudaSuccess) return e;                                                                   \
+    }
+    CFPQ_RING(4) CFPQ_RING(8) CFPQ_RING(16)
+#undef CFPQ_RING
+    return cudaSuccess;
 }
 
 // With fused control (ctls != null) this launch also runs the pass's loop

@@ -116,7 +116,11 @@ int cfpq_submit(cfpq_server *s, const cfpq_rsm *rsm, uint64_t *ticket) {
     try {
         cfpq_server::Job j;
         j.q.reset(new QueryDev());
-        j.q->closure_mode = s->opt.closure_mode;
+        // AUTO serves with bit-packed rows only: tile products would add an
+        // n x n-byte operand workspace per dense source to every query's
+        // footprint and cut the number of queries admitted together
+        j.q->closure_mode = s->opt.closure_mode == CFPQ_CLOSURE_AUTO ? (uint32_t)CFPQ_CLOSURE_BITPACKED
+                                                                     : s->opt.closure_mode;
         std::string e;
         int rc = copy_rsm(rsm, &j.q->rsm, &e);
         if (rc) return sfail(s, rc, e);

@@ -20,6 +20,8 @@
 // a buffer.  Stages whose A or B tile is all zero are skipped (dirty tiles).
 // The epilogue reads the accumulator with tcgen05.ld, thresholds it, ORs the
 // bits into the output rows and stamps the rows that changed.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -190,21 +192,20 @@ __device__ __forceinline__ bool tc_job_active(const TcJob &j, uint32_t *thr, uin
 }
 
 // The inner dimension of a job in this pass: compacted (the dirty rows listed
-// by k_tc_rows, A's columns gathered by k_tc_cols) when the job has buffers
-// and the list fits them, else all n rows with a stamp filter.
+// by k_tc_rows, operands expanded by k_tc_a8/k_tc_b8, multiplied by
+// k_tc_product_tma) when the job has buffers and the list fits them, else all
+// n rows with a stamp filter (k_tc_product).
 struct KDim {
-    const uint64_t *A;
-    uint32_t wa;      // words per row of A
-    uint32_t kdim;    // rows of the inner dimension
+    uint32_t kdim;  // rows of the inner dimension
     bool compact;
 };
 
 __device__ __forceinline__ KDim job_kdim(const TcJob &J, uint32_t g) {
-    KDim k{J.A, J.W, J.B ? J.n : 0u, false};
+    KDim k{J.B ? J.n : 0u, false};
     if (J.ys && J.kcount) {
         const unsigned long long kc = *reinterpret_cast<volatile unsigned long long *>(J.kcount);
         const uint32_t d = ((uint32_t)(kc >> 32) == g) ? (uint32_t)kc : 0u;
-        if (d <= J.Wc * 64u) k = KDim{J.ac, J.Wc, d, true};
+        if (d <= J.kcap) k = KDim{d, true};
     }
     return k;
 }
@@ -266,8 +267,9 @@ __global__ void __launch_bounds__(tc::kThreads, 2)
         uint32_t thr, iter, g;
         const uint32_t t = ti - J.tile0;
         const bool act = tc_job_active(J, &thr, &iter, &g) && t < J.tiles_m * J.tiles_n;
-        const KDim K = act ? job_kdim(J, g) : KDim{nullptr, 0u, 0u, false};
-        if (!act || (K.kdim == 0u && !J.ident)) {
+        const KDim K = act ? job_kdim(J, g) : KDim{0u, false};
+        // compacted jobs run in k_tc_product_tma
+        if (!act || K.compact || (K.kdim == 0u && !J.ident)) {
             // skip the rest of this job's tiles in this CTA's stride
             const uint32_t left = J.tiles_m * J.tiles_n > t ? J.tiles_m * J.tiles_n - t : 1u;
             li += ((left - 1u) / gridDim.x) * gridDim.x;
@@ -287,16 +289,10 @@ __global__ void __launch_bounds__(tc::kThreads, 2)
         auto load = [&](uint32_t ks, TcStage &st) {
             const uint32_t k0 = ks * kBK;
             const uint32_t w = (k0 >> 6) + ah;
-            st.a = (xa_ok && w < kwords) ? K.A[(size_t)xa * K.wa + w] : 0ull;
+            st.a = (xa_ok && w < kwords) ? J.A[(size_t)xa * W + w] : 0ull;
             const uint32_t kk = k0 + 32u * ((uint32_t)warp >> 1) + (uint32_t)lane;
-            uint32_t y = kk;
-            bool rok;
-            if (K.compact) {
-                rok = kk < K.kdim;
-                y = rok ? J.ys[kk] : 0u;
-            } else {
-                rok = kk < n && (!J.b_stamp || thr == 0u || J.b_stamp[kk] >= thr);
-            }
+            const uint32_t y = kk;
+            const bool rok = kk < n && (!J.b_stamp || thr == 0u || J.b_stamp[kk] >= thr);
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const uint32_t zc = n0 + 128u * ((uint32_t)warp & 1u) + 32u * (uint32_t)b;
@@ -527,10 +523,10 @@ __global__ void __launch_bounds__(256) k_tc_rows(const TcJob *__restrict__ jobs,
     });
 }
 
-// ac[x][k] = A[x][ys[k]] for k < D, one warp per row x: the row is staged in
-// shared memory, lanes test 64 listed columns per step and ballot them into a
-// word; 32 words are written at once.
-__global__ void __launch_bounds__(256) k_tc_cols(const TcJob *__restrict__ jobs, ExecTables T, uint32_t max_w) {
+// a8[x][k] = A[x][ys[k]] as a 0/1 FP8 byte for k < D, 0 up to the next
+// multiple of 128; one warp per row x, the row staged in shared memory, each
+// lane writing 4 consecutive bytes of a coalesced 128-byte step.
+__global__ void __launch_bounds__(256) k_tc_a8(const TcJob *__restrict__ jobs, ExecTables T, uint32_t max_w) {
     extern __shared__ uint64_t s_rowbuf[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t *row = s_rowbuf + (size_t)warp * max_w;
@@ -541,7 +537,7 @@ __global__ void __launch_bounds__(256) k_tc_cols(const TcJob *__restrict__ jobs,
         if (!K.compact || K.kdim == 0u) return;
         const uint32_t x = c * kColRows + (uint32_t)warp;
         if (x >= J.n) return;
-        const uint32_t W = J.W, D = K.kdim, nw = (D + 63u) >> 6;
+        const uint32_t W = J.W, D = K.kdim, dpad = (D + 127u) & ~127u;
         const uint4 *src = reinterpret_cast<const uint4 *>(J.A + (size_t)x * W);
         bool nz = false;
         for (uint32_t v = (uint32_t)lane; v < W / 2u; v += 32u) {
@@ -551,30 +547,315 @@ __global__ void __launch_bounds__(256) k_tc_cols(const TcJob *__restrict__ jobs,
         }
         nz = __any_sync(0xffffffffu, nz);
         __syncwarp();
-        uint64_t *dst = J.ac + (size_t)x * J.Wc;
-        for (uint32_t wb = 0; wb < nw; wb += 32u) {
-            uint64_t mine = 0ull;
-            const uint32_t wend = min(nw, wb + 32u);
-            if (nz) {
-                for (uint32_t w = wb; w < wend; ++w) {
-                    const uint32_t k0 = w * 64u + (uint32_t)lane, k1 = k0 + 32u;
-                    bool b0 = false, b1 = false;
-                    if (k0 < D) {
-                        const uint32_t y = __ldg(J.ys + k0);
-                        b0 = (row[y >> 6] >> (y & 63u)) & 1ull;
-                    }
-                    if (k1 < D) {
-                        const uint32_t y = __ldg(J.ys + k1);
-                        b1 = (row[y >> 6] >> (y & 63u)) & 1ull;
-                    }
-                    const unsigned lo = __ballot_sync(0xffffffffu, b0), hi2 = __ballot_sync(0xffffffffu, b1);
-                    if ((uint32_t)lane == w - wb) mine = (uint64_t)lo | ((uint64_t)hi2 << 32);
-                }
+        uint32_t *dst = reinterpret_cast<uint32_t *>(J.a8 + (size_t)x * J.kcap);
+        for (uint32_t k0 = 0; k0 < dpad; k0 += 128u) {
+            const uint32_t kb = k0 + 4u * (uint32_t)lane;
+            uint32_t word = 0u;
+            if (nz && kb < D) {
+                const uint4 y4 = *reinterpret_cast<const uint4 *>(J.ys + kb);
+                const uint32_t yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (kb + (uint32_t)i < D && ((row[yv[i] >> 6] >> (yv[i] & 63u)) & 1ull)) word |= 0x38u << (8 * i);
             }
-            if (wb + (uint32_t)lane < wend) dst[wb + lane] = mine;
+            dst[kb >> 2] = word;
         }
         __syncwarp();  // the next row reuses the staging buffer
     });
+}
+
+// b8[z][k] = B[ys[k]][z] as a 0/1 FP8 byte (B's listed rows transposed), for
+// z < n_pad and k below the next multiple of 128 of D.  Unit: 128 listed rows
+// x 256 columns; the rows' 256-bit slices are staged in shared memory and each
+// thread writes the 128 bytes of one column z.
+__global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, ExecTables T) {
+    __shared__ uint64_t s_bits[128][4];
+    const int tid = threadIdx.x;
+    uint32_t u0 = 0;
+    for (uint32_t q = 0; q < T.nq; ++q) {
+        const uint32_t jb = T.t_job_beg[q], je = T.t_job_end[q];
+        for (uint32_t j = jb; j < je; ++j) {
+            const TcJob &J = jobs[j];
+            if (!J.ys) continue;
+            uint32_t thr, iter, g;
+            if (!tc_job_active(J, &thr, &iter, &g)) continue;
+            const KDim K = job_kdim(J, g);
+            if (!K.compact || K.kdim == 0u) continue;
+            const uint32_t D = K.kdim, kchunks = (D + 127u) / 128u, W = J.W, zchunks = (W * 64u + 255u) / 256u;
+            const uint32_t units = kchunks * zchunks;
+            const uint32_t first = (blockIdx.x + gridDim.x - (u0 % gridDim.x)) % gridDim.x;
+            u0 += units;
+            for (uint32_t u = first; u < units; u += gridDim.x) {
+                const uint32_t k0 = (u / zchunks) * 128u, w0 = (u % zchunks) * 4u;
+                __syncthreads();  // the previous unit's reads of s_bits are done
+                {
+                    const uint32_t i = (uint32_t)tid >> 1, h = ((uint32_t)tid & 1u) * 2u;
+                    const bool ok = k0 + i < D;
+                    const uint32_t y = ok ? J.ys[k0 + i] : 0u;
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const uint32_t w = w0 + h + (uint32_t)t;
+                        s_bits[i][h + t] = (ok && w < W) ? J.B[(size_t)y * W + w] : 0ull;
+                    }
+                }
+                __syncthreads();
+                const uint32_t z = w0 * 64u + (uint32_t)tid;
+                if (z < W * 64u) {
+                    const int wi = tid >> 6, bi = tid & 63;
+                    uint4 *dst = reinterpret_cast<uint4 *>(J.b8 + (size_t)z * J.kcap + k0);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        uint32_t v[4];
+#pragma unroll
+                        for (int qd = 0; qd < 4; ++qd) {
+                            uint32_t wv = 0u;
+#pragma unroll
+                            for (int b = 0; b < 4; ++b)
+                                if ((s_bits[c * 16 + qd * 4 + b][wi] >> bi) & 1ull) wv |= 0x38u << (8 * b);
+                            v[qd] = wv;
+                        }
+                        dst[c] = make_uint4(v[0], v[1], v[2], v[3]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// TMA-fed product of the compacted jobs.  Warp 0 (one lane) streams the FP8
+// operand tiles of every K stage into a ring of kRing shared-memory stages
+// with cp.async.bulk.tensor (128-byte swizzle); warp 1 (one lane) issues the
+// tcgen05 MMAs into one of two TMEM accumulators and commits each stage back
+// to the producer; warps 2-5 read a finished accumulator (each its TMEM lane
+// quarter), threshold it and OR the bits into the output block while the
+// next tile accumulates in the other half of TMEM.
+// ---------------------------------------------------------------------------
+namespace tc2 {
+constexpr int kRing = 4;
+constexpr uint32_t kABytes = 128u * 128u, kBBytes = 256u * 128u, kStage = kABytes + kBBytes;  // 48 KiB
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 512;  // two 256-column accumulators
+
+// K-major operand tile written by TMA with the 128-byte swizzle: 128-byte
+// rows, 8-row groups 1024 bytes apart; layout type 2 (SWIZZLE_128B).
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1u << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void arrive_expect_tx(uint64_t *m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(m)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void arrive(uint64_t *m) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(m)) : "memory");
+}
+
+__device__ __forceinline__ void tma_load(void *dst, const void *map, int32_t c0, int32_t c1, uint64_t *m) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(tc::smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(tc::smem_u32(m))
+        : "memory");
+}
+
+// The next live tile of a compacted job at or after li (same walk in every
+// role): job, tile origin, K stages and pass stamp.  The job of the last tile
+// is cached with its range of live-tile indices, so the tables are read once
+// per job rather than once per tile.
+struct Tile {
+    const TcJob *J;
+    uint32_t m0, n0, ks, g;
+};
+struct JobCache {
+    const TcJob *J = nullptr;
+    uint32_t li0 = 1u, li1 = 0u;  // live-tile indices of the job: [li0, li1)
+    uint32_t ks = 0, g = 0;
+    bool ok = false;
+};
+
+__device__ __forceinline__ bool next_tile(const TcJob *jobs, const ExecTables &T, uint32_t total, uint32_t &li,
+                                          Tile &tl, JobCache &jc) {
+    for (; li < total; li += gridDim.x) {
+        if (li >= jc.li0 && li < jc.li1) {
+            if (!jc.ok) {  // skip the rest of the cached job's tiles
+                li += ((jc.li1 - 1u - li) / gridDim.x) * gridDim.x;
+                continue;
+            }
+            const uint32_t t = li - jc.li0;
+            tl.J = jc.J;
+            tl.m0 = (t / jc.J->tiles_n) * 128u;
+            tl.n0 = (t % jc.J->tiles_n) * 256u;
+            tl.ks = jc.ks;
+            tl.g = jc.g;
+            return true;
+        }
+        const uint32_t q = find_owner(T.t_pre, T.nq, li);
+        const uint32_t ti = li - T.t_pre[q];
+        uint32_t lo = T.t_job_beg[q], hi = T.t_job_end[q];
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (jobs[mid].tile0 <= ti) lo = mid;
+            else hi = mid;
+        }
+        const TcJob &J = jobs[lo];
+        const uint32_t t = ti - J.tile0, tiles = J.tiles_m * J.tiles_n;
+        if (t >= tiles) continue;  // past the jobs of this query's level
+        uint32_t thr, iter, g = 0;
+        bool ok = J.ys != nullptr && tc_job_active(J, &thr, &iter, &g);
+        KDim K{0u, false};
+        if (ok) {
+            K = job_kdim(J, g);
+            ok = K.compact && K.kdim > 0u;
+        }
+        jc.J = &J;
+        jc.li0 = li - t;
+        jc.li1 = li - t + tiles;
+        jc.ok = ok;
+        jc.ks = (K.kdim + 127u) / 128u;
+        jc.g = g;
+        li -= gridDim.x;  // re-enter through the cache
+    }
+    return false;
+}
+}  // namespace tc2
+
+__global__ void __launch_bounds__(tc2::kThreads, 1)
+    k_tc_product_tma(const TcJob *__restrict__ jobs, const unsigned char *__restrict__ maps, ExecTables T,
+                     int *err_flag) {
+    using namespace tc;
+    using namespace tc2;
+    extern __shared__ __align__(1024) unsigned char smem_raw2[];
+    __shared__ uint64_t full[kRing], empty[kRing], tfull[2], tempty[2];
+    __shared__ uint32_t tmem_base;
+    const uint32_t total = *T.t_total;
+    if (blockIdx.x >= total) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // stage buffers start 1024-byte aligned (the swizzle pattern repeats every 1024 bytes)
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw2) + 1023u) & ~static_cast<uintptr_t>(1023u));
+    if (warp == 0) tmem_alloc(&tmem_base, tc2::kTmemCols);
+    if (tid == 0) {
+        for (int i = 0; i < kRing; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = make_idesc(1, 128, 256);
+    bool to = false;
+
+    if (warp == 0) {
+        if (lane == 0) {  // TMA producer
+            uint32_t stage = 0, ph = 0, li = blockIdx.x;
+            Tile tl;
+            JobCache jc;
+            while (!to && next_tile(jobs, T, total, li, tl, jc)) {
+                const unsigned char *ma = maps + (size_t)tl.J->map * 2u * 128u, *mb = ma + 128;
+                for (uint32_t k = 0; k < tl.ks; ++k) {
+                    if (!mbar_wait(&empty[stage], ph ^ 1u)) { to = true; break; }
+                    unsigned char *sa = base + (size_t)stage * kStage, *sb = sa + kABytes;
+                    arrive_expect_tx(&full[stage], kStage);
+                    tma_load(sa, ma, (int32_t)(k * 128u), (int32_t)tl.m0, &full[stage]);
+                    tma_load(sb, mb, (int32_t)(k * 128u), (int32_t)tl.n0, &full[stage]);
+                    if (++stage == (uint32_t)kRing) { stage = 0; ph ^= 1u; }
+                }
+                li += gridDim.x;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            uint32_t stage = 0, ph = 0, acc = 0, aph = 0, li = blockIdx.x;
+            Tile tl;
+            JobCache jc;
+            while (!to && next_tile(jobs, T, total, li, tl, jc)) {
+                if (!mbar_wait(&tempty[acc], aph ^ 1u)) { to = true; break; }
+                tc_after();
+                const uint32_t d = tmem + acc * 256u;
+                for (uint32_t k = 0; k < tl.ks; ++k) {
+                    if (!mbar_wait(&full[stage], ph)) { to = true; break; }
+                    tc_after();
+                    const uint32_t sa = smem_u32(base + (size_t)stage * kStage), sb = sa + kABytes;
+#pragma unroll
+                    for (uint32_t kk = 0; kk < 4; ++kk)
+                        tc::mma(false, d, desc_sw128(sa + kk * 32u), desc_sw128(sb + kk * 32u), idesc,
+                                (k > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(&empty[stage]);  // the stage is free once these MMAs have read it
+                    if (++stage == (uint32_t)kRing) { stage = 0; ph ^= 1u; }
+                }
+                if (to) break;
+                mma_commit(&tfull[acc]);
+                QCtl *cw = tl.J->ctl;
+                if (cw) {
+                    atomicAdd(&cw->tile_mmas, 1ull);
+                    atomicAdd(&cw->tile_kstages, (unsigned long long)tl.ks);
+                }
+                if (++acc == 2u) { acc = 0; aph ^= 1u; }
+                li += gridDim.x;
+            }
+        }
+    } else {  // epilogue: warps 2-5, TMEM lanes 32 * (warp % 4) ...
+        const uint32_t quarter = (uint32_t)warp & 3u;
+        uint32_t acc = 0, aph = 0, li = blockIdx.x;
+        Tile tl;
+        JobCache jc;
+        while (!to && next_tile(jobs, T, total, li, tl, jc)) {
+            if (!mbar_wait(&tfull[acc], aph)) { to = true; }
+            if (__any_sync(0xffffffffu, to)) { to = true; break; }
+            tc_after();
+            const TcJob &J = *tl.J;
+            const uint32_t r = quarter * 32u + (uint32_t)lane, x = tl.m0 + r;
+            uint32_t mask[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                uint32_t v[32];
+                tmem_ld32(tmem + acc * 256u + 32u * (uint32_t)c + ((quarter * 32u) << 16), v);
+                uint32_t mb = 0u;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) mb |= (v[i] != 0u ? 1u : 0u) << i;
+                mask[c] = mb;
+            }
+            tc_before();
+            __syncwarp();
+            if (lane == 0) arrive(&tempty[acc]);  // the accumulator may be overwritten
+            bool ch = false;
+            if (x < J.n) {
+                const uint32_t w0 = tl.n0 >> 6;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const uint32_t ww = w0 + (uint32_t)w;
+                    const uint64_t add = (uint64_t)mask[2 * w] | ((uint64_t)mask[2 * w + 1] << 32);
+                    if (ww >= J.W || !add) continue;
+                    const uint64_t old = atomicOr(reinterpret_cast<unsigned long long *>(J.out + (size_t)x * J.W + ww),
+                                                  (unsigned long long)add);
+                    if (add & ~old) ch = true;
+                }
+            }
+            if (ch && J.out_stamp) J.out_stamp[x] = tl.g;
+            const unsigned chb = __ballot_sync(0xffffffffu, ch);
+            if (lane == 0 && chb) {
+                if (J.out_last) *J.out_last = tl.g;
+                if (J.ctl) atomicAdd(&J.ctl->changed_rows, (unsigned long long)__popc(chb));
+            }
+            if (++acc == 2u) { acc = 0; aph ^= 1u; }
+            li += gridDim.x;
+        }
+    }
+    if (to) atomicOr(err_flag, 1);
+    tc_before();
+    __syncthreads();
+    tc_after();
+    if (warp == 0) tmem_dealloc(tmem, tc2::kTmemCols);
 }
 
 static int g_tc_sms[64];
@@ -595,8 +876,11 @@ cudaError_t prepare_tc_launch() {
     if (g_tc_sms[dev]) return cudaSuccess;
     e = cudaFuncSetAttribute(k_tc_product, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes());
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_cols, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_tc_a8, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kColMaxW * 8u * (256u / 32u)));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_product_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(tc2::kRing * tc2::kStage + 1024u));
     if (e != cudaSuccess) return e;
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -630,8 +914,58 @@ cudaError_t launch_tc_compact(const TcJob *jobs, const ExecTables &T, uint32_t m
     k_tc_rows<<<(unsigned)sms * 4u, 256, 0, st>>>(jobs, T, err_flag);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_tc_cols<<<(unsigned)sms * 4u, 256, (size_t)max_w * 8u * 8u, st>>>(jobs, T, max_w);
+    k_tc_a8<<<(unsigned)sms * 4u, 256, (size_t)max_w * 8u * 8u, st>>>(jobs, T, max_w);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_tc_b8<<<(unsigned)sms * 4u, 256, 0, st>>>(jobs, T);
     return cudaGetLastError();
+}
+
+cudaError_t launch_tc_product_tma(const TcJob *jobs, const void *maps, uint32_t max_tiles, const ExecTables &T,
+                                  int *err_flag, cudaStream_t st) {
+    if (max_tiles == 0 || maps == nullptr) return cudaSuccess;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int sms = (dev >= 0 && dev < 64 && g_tc_sms[dev]) ? g_tc_sms[dev] : 0;
+    if (!sms) return cudaErrorNotReady;  // prepare_tc_launch was not called
+    uint32_t grid = (uint32_t)sms;  // one CTA per SM: the ring and both accumulators fill it
+    if (max_tiles < grid) grid = max_tiles;
+    k_tc_product_tma<<<grid, tc2::kThreads, tc2::kRing * tc2::kStage + 1024u, st>>>(
+        jobs, static_cast<const unsigned char *>(maps), T, err_flag);
+    return cudaGetLastError();
+}
+
+static_assert(sizeof(CUtensorMap) == 128, "the product kernel indexes tensor maps in 128-byte steps");
+size_t tc_map_bytes() { return sizeof(CUtensorMap); }
+
+// a8: kcap x n bytes, box 128 x 128; b8: kcap x n_pad bytes, box 128 x 256;
+// both UINT8 with the 128-byte swizzle (the K-major layout the MMA reads).
+cudaError_t tc_encode_maps(const TcJob *jobs, uint32_t n_jobs, void *out) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult qr;
+        void *fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
+        if (e != cudaSuccess || qr != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    CUtensorMap *m = static_cast<CUtensorMap *>(out);
+    for (uint32_t j = 0; j < n_jobs; ++j) {
+        const TcJob &J = jobs[j];
+        if (!J.ys) continue;
+        const cuuint64_t dims_a[2] = {J.kcap, J.n}, dims_b[2] = {J.kcap, (cuuint64_t)J.W * 64u};
+        const cuuint64_t stride[1] = {J.kcap};
+        const cuuint32_t box_a[2] = {128u, 128u}, box_b[2] = {128u, 256u}, es[2] = {1u, 1u};
+        CUresult r = encode(&m[2 * J.map], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, J.a8, dims_a, stride, box_a, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        r = encode(&m[2 * J.map + 1], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, J.b8, dims_b, stride, box_b, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
 }
 
 size_t tc_job_size() { return sizeof(TcJob); }

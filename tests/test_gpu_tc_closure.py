@@ -93,7 +93,7 @@ def test_int8_mode_is_rejected(C):
     assert e.value.status == C.CFPQ_ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("n", [512, 2048, 4096])
+@pytest.mark.parametrize("n", [512, 2048, 8192])
 def test_auto_dense_tiles_dyck(C, n):
     """AUTO moves the products of Dyck-4's dense nonterminal matrix with the
     dirty closure rows to tensor-core tiles; the answer equals the row-gather
@@ -103,8 +103,8 @@ def test_auto_dense_tiles_dyck(C, n):
     _, s2, b = _run(g, r, C.CFPQ_CLOSURE_BITPACKED)
     assert (a == b).all()
     assert s1.iterations == s2.iterations
-    if n >= 2048:                    # S is denser than 1/32 there: dense tiles ran
-        assert s1.tile_mmas > 0
+    if n >= 8192:                    # large enough to switch, and S is denser than 1/32: tiles ran
+        assert s1.tile_mmas > 0 and s1.tile_kstages > 0
     if n <= 2048:
         assert (a == oracle.worklist(g, r)).all()
 
