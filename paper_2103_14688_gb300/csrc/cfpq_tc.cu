@@ -634,7 +634,8 @@ __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, E
 namespace tc2 {
 constexpr int kRing = 4;
 constexpr uint32_t kABytes = 128u * 128u, kBBytes = 256u * 128u, kStage = kABytes + kBBytes;  // 48 KiB
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;      // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr uint32_t kEpiWarps = 8;
 constexpr uint32_t kTmemCols = 512;  // two 256-column accumulators
 
 // K-major operand tile written by TMA with the 128-byte swizzle: 128-byte
@@ -744,7 +745,7 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tfull[i], 1);
-            mbar_init(&tempty[i], 4);
+            mbar_init(&tempty[i], kEpiWarps);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -804,8 +805,8 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
                 li += gridDim.x;
             }
         }
-    } else {  // epilogue: warps 2-5, TMEM lanes 32 * (warp % 4) ...
-        const uint32_t quarter = (uint32_t)warp & 3u;
+    } else {  // epilogue: warps 2-9; TMEM lanes 32 * (warp % 4) ..., columns half * 128 ...
+        const uint32_t quarter = (uint32_t)warp & 3u, half = (uint32_t)(warp - 2) >> 2;
         uint32_t acc = 0, aph = 0, li = blockIdx.x;
         Tile tl;
         JobCache jc;
@@ -815,24 +816,26 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
             tc_after();
             const TcJob &J = *tl.J;
             const uint32_t r = quarter * 32u + (uint32_t)lane, x = tl.m0 + r;
-            uint32_t mask[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
+            uint32_t mask[4];
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
                 uint32_t v[32];
-                tmem_ld32(tmem + acc * 256u + 32u * (uint32_t)c + ((quarter * 32u) << 16), v);
+                tmem_ld32(tmem + acc * 256u + half * 128u + 32u * (uint32_t)c + ((quarter * 32u) << 16), v);
                 uint32_t mb = 0u;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) mb |= (v[i] != 0u ? 1u : 0u) << i;
-                mask[c] = mb;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc)
+                    if (cc == c) mask[cc] = mb;
             }
             tc_before();
             __syncwarp();
             if (lane == 0) arrive(&tempty[acc]);  // the accumulator may be overwritten
             bool ch = false;
             if (x < J.n) {
-                const uint32_t w0 = tl.n0 >> 6;
+                const uint32_t w0 = (tl.n0 >> 6) + half * 2u;
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
+                for (int w = 0; w < 2; ++w) {
                     const uint32_t ww = w0 + (uint32_t)w;
                     const uint64_t add = (uint64_t)mask[2 * w] | ((uint64_t)mask[2 * w + 1] << 32);
                     if (ww >= J.W || !add) continue;
@@ -841,7 +844,7 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
                     if (add & ~old) ch = true;
                 }
             }
-            if (ch && J.out_stamp) J.out_stamp[x] = tl.g;
+            if (ch && J.out_stamp) J.out_stamp[x] = tl.g;  // both halves may stamp: same value
             const unsigned chb = __ballot_sync(0xffffffffu, ch);
             if (lane == 0 && chb) {
                 if (J.out_last) *J.out_last = tl.g;
