@@ -405,6 +405,16 @@ def run_other(args):
         torch.cuda.synchronize()
         bt = time.perf_counter() - t0
         bits = [ctx.batch_reachable_bits(i, 0) for i in range(len(qs))]
+        # the same batch with bit-packed rows only (no tensor-core tiles)
+        bctx = cfpq.Context(closure_mode=cfpq.CFPQ_CLOSURE_BITPACKED)
+        bctx.batch_run(qs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bctx.batch_run(qs)
+        torch.cuda.synchronize()
+        bp_t = time.perf_counter() - t0
+        bp_same = all((bctx.batch_reachable_bits(i, 0) == bits[i]).all() for i in range(len(qs)))
+        bctx.close()
         solo = cfpq.Context()
         st_s = 0.0
         mism = 0
@@ -420,6 +430,7 @@ def run_other(args):
         line.update({"metric": "batched queries/s vs one at a time", "unit": "queries/s",
                      "value": len(qs) / bt, "higher_is_better": True, "queries": len(qs),
                      "one_at_a_time_qps": len(qs) / st_s, "speedup": st_s / bt, "mismatches_vs_solo": mism,
+                     "batched_bitpacked_qps": len(qs) / bp_t, "bitpacked_equal": bool(bp_same),
                      "batch_setup_ms": tot.ms_setup, "batch_loop_ms": tot.ms_loop, "passes": tot.rounds,
                      "device_gb": tot.device_bytes / 1e9})
     elif args.workload == "served":

@@ -171,7 +171,7 @@ struct TcJob {
 };
 
 constexpr uint32_t kDenseDiv = 32;  // a box is dense from n^2 / 32 edges on (one bit in two words)
-constexpr uint32_t kAutoTilesMinN = 8192;  // AUTO switches boxes to tile products only from this n on
+constexpr uint32_t kAutoTilesMinN = 2048;  // AUTO switches boxes to tile products only from this n on
 
 // Per-executor work tables.  Items of each kind are sorted by (query, level);
 // the static tables give, for query q and level L, the first item of that

@@ -103,7 +103,7 @@ def test_auto_dense_tiles_dyck(C, n):
     _, s2, b = _run(g, r, C.CFPQ_CLOSURE_BITPACKED)
     assert (a == b).all()
     assert s1.iterations == s2.iterations
-    if n >= 8192:                    # large enough to switch, and S is denser than 1/32: tiles ran
+    if n >= 2048:                    # large enough to switch, and S is denser than 1/32: tiles ran
         assert s1.tile_mmas > 0 and s1.tile_kstages > 0
     if n <= 2048:
         assert (a == oracle.worklist(g, r)).all()
