@@ -43,7 +43,8 @@ cfpq_free_fn = CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
 class cfpq_options(Structure):
     _fields_ = [("struct_size", c_uint32), ("device", c_int32), ("max_iterations", c_uint32),
                 ("max_rounds", c_uint32), ("closure_mode", c_uint32), ("loop_mode", c_uint32),
-                ("profile", c_uint32), ("no_single_cta", c_uint32), ("memory_budget", c_size_t), ("alloc", cfpq_alloc_fn), ("free", cfpq_free_fn),
+                ("profile", c_uint32), ("no_single_cta", c_uint32), ("gather_slices", c_uint32),
+                ("memory_budget", c_size_t), ("alloc", cfpq_alloc_fn), ("free", cfpq_free_fn),
                 ("alloc_user", c_void_p)]
 
 

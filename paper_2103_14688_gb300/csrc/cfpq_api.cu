@@ -139,6 +139,7 @@ int ensure_query(cfpq_ctx *ctx) {
     QueryDev &q = ctx->query;
     q.g = &ctx->graph;
     q.closure_mode = ctx->opt.closure_mode;
+    q.gather_slices = ctx->opt.gather_slices;
     if (!q.prepared || q.graph_generation != ctx->graph.generation || ctx->exec_dirty) {
         std::string e;
         int rc = q.prepare(&ctx->A, &e);
@@ -700,6 +701,7 @@ extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_quer
         if (rc) return fail(ctx, rc, "query " + std::to_string(i) + ": " + e);
         std::unique_ptr<QueryDev> q(new QueryDev());
         q->closure_mode = ctx->opt.closure_mode;
+        q->gather_slices = ctx->opt.gather_slices;
         rc = copy_rsm(qq.rsm, &q->rsm, &e);
         if (rc) return fail(ctx, rc, "query " + std::to_string(i) + ": " + e);
         q->g = g.get();

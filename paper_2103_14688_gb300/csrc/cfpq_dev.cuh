@@ -109,7 +109,11 @@ struct GItem {
     uint32_t W;    // words per row
     uint32_t lpr;  // lanes per row (power of two <= 32)
     uint32_t level;
-    uint32_t pad;
+    // Column slice of the nonterminal adjacency rows this item enumerates,
+    // in 128-bit vectors: [slice & 0xFFFF, slice >> 16).  Items of one row
+    // range with different slices share the output rows and merge them with
+    // atomicOr; the CSR sources are taken by the slice that starts at 0.
+    uint32_t slice;
 };
 
 // Final-state block used by extraction: C[q0(b), f] with f final in box b.

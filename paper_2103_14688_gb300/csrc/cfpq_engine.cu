@@ -542,7 +542,14 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                     has_nt |= (sd.label_kind != 0) || sd.pure_rb;
                 }
                 const int cls = 2 * vi + (has_nt ? 1 : 0);
-                for (uint32_t r0 = 0; r0 < q.n; r0 += rpi) {
+                // wide rows of nonterminal blocks: the adjacency columns are
+                // split over several items, so that rows with thousands of new
+                // edges (hubs) spread over several CTAs
+                const uint32_t nvec = q.W / 2u;
+                uint32_t n_slices = (has_nt && q.W >= 256u) ? std::min<uint32_t>(8u, q.W / 64u) : 1u;
+                if (q.gather_slices) n_slices = (has_nt && q.W >= 256u) ? std::min<uint32_t>(q.gather_slices, 16u) : 1u;
+                for (uint32_t r0 = 0; r0 < q.n; r0 += rpi)
+                for (uint32_t sl = 0; sl < n_slices; ++sl) {
                     GItem it;
                     it.out = q.blk_ptr((uint32_t)b);
                     it.out_stamp = q.stamp_ptr((uint32_t)b);
@@ -555,7 +562,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                     it.W = q.W;
                     it.lpr = q.lpr;
                     it.level = L;
-                    it.pad = 0;
+                    it.slice = (nvec * sl / n_slices) | ((nvec * (sl + 1) / n_slices) << 16);
                     hi[cls].push_back(it);
                 }
                 // tile sources of this block: one product job for the dirty-row

@@ -154,6 +154,7 @@ struct QueryDev {
     uint64_t device_bytes = 0;
     // host descriptors (pointers filled once buffers exist; ctl set by the executor)
     uint32_t closure_mode = CFPQ_CLOSURE_AUTO;
+    uint32_t gather_slices = 0;  // cfpq_options::gather_slices
     struct Src {
         uint32_t label_kind, label, ident;
         int32_t rblk;

@@ -200,6 +200,11 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
     const int lpr = (int)it.lpr, grp = lane / lpr, gl = lane % lpr, rpw = 32 / lpr;
     const unsigned gmask = (lpr == 32 ? FULLMASK : ((1u << lpr) - 1u)) << (grp * lpr);
     const uint32_t W = it.W, nvec = W / 2;
+    // column slice of the nonterminal adjacency (general variant, rows of 4+
+    // vectors per lane: the engine slices only those)
+    constexpr bool kSlices = NT && VPL >= 4;
+    const uint32_t sv0 = kSlices ? (it.slice & 0xFFFFu) : 0u, sv1 = kSlices ? (it.slice >> 16) : nvec;
+    const bool sliced = kSlices && (sv0 != 0u || sv1 < nvec);
     uint32_t my_changed = 0, my_ors = 0;
 
     for (uint32_t rbase = it.row0 + (uint32_t)(warp * rpw); rbase < it.row1; rbase += 8u * rpw) {
@@ -331,6 +336,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                 };
 
                 if (d.csr_off) {
+                    if (sv0 != 0u) continue;  // CSR sources belong to the first slice
                     const uint32_t e0 = valid ? d.csr_off[row] : 0u, e1 = valid ? d.csr_off[row + 1] : 0u;
                     const uint32_t cnt = e1 - e0;
                     const uint32_t maxcnt = __reduce_max_sync(FULLMASK, cnt);
@@ -391,8 +397,9 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
 #pragma unroll
                     for (int j = 0; j < VPL; ++j) {
                         const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
-                        a[j] = (rowok && v < nvec) ? reinterpret_cast<const uint4 *>(adj + (size_t)row * W)[v]
-                                                   : make_uint4(0, 0, 0, 0);
+                        a[j] = (rowok && v >= sv0 && v < sv1 && v < nvec)
+                                   ? reinterpret_cast<const uint4 *>(adj + (size_t)row * W)[v]
+                                   : make_uint4(0, 0, 0, 0);
                     }
                     // Each lane proposes the lowest set bit of its part of the
                     // adjacency row per step (ballot/ffs enumeration).
@@ -415,7 +422,20 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
         }
 
         bool ch = false;
-        if (valid) {
+        if (valid && sliced) {
+            // other slices write the same rows: merge with atomics
+            unsigned long long *o = reinterpret_cast<unsigned long long *>(it.out + (size_t)row * W);
+#pragma unroll
+            for (int j = 0; j < VPL; ++j) {
+                const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
+                if (v < nvec && nz4(acc[j])) {
+                    const unsigned long long lo = ((unsigned long long)acc[j].y << 32) | acc[j].x;
+                    const unsigned long long hi = ((unsigned long long)acc[j].w << 32) | acc[j].z;
+                    if (lo && (lo & ~atomicOr(o + 2u * v, lo))) ch = true;
+                    if (hi && (hi & ~atomicOr(o + 2u * v + 1u, hi))) ch = true;
+                }
+            }
+        } else if (valid) {
             uint4 *o = reinterpret_cast<uint4 *>(it.out + (size_t)row * W);
 #pragma unroll
             for (int j = 0; j < VPL; ++j) {

@@ -121,6 +121,7 @@ int cfpq_submit(cfpq_server *s, const cfpq_rsm *rsm, uint64_t *ticket) {
         // footprint and cut the number of queries admitted together
         j.q->closure_mode = s->opt.closure_mode == CFPQ_CLOSURE_AUTO ? (uint32_t)CFPQ_CLOSURE_BITPACKED
                                                                      : s->opt.closure_mode;
+        j.q->gather_slices = s->opt.gather_slices;
         std::string e;
         int rc = copy_rsm(rsm, &j.q->rsm, &e);
         if (rc) return sfail(s, rc, e);

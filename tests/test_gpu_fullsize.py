@@ -122,3 +122,24 @@ def test_dyck_full_size_properties(C):
         row = np.unpackbits(ans[x].view(np.uint8), bitorder="little")[: g.n].astype(bool)
         row2 = np.unpackbits(ans2[perm[x]].view(np.uint8), bitorder="little")[: g.n].astype(bool)
         assert (row2[perm] == row).all()
+
+
+def test_dyck_sliced_gather_equals_unsliced(C):
+    """n = 16384 (rows of 16384 bits): the row gather splits the nonterminal
+    adjacency columns of a work item over several CTAs that merge with
+    atomics; the answer equals the unsliced gather's and the tensor-core
+    mode's, and the closure rows agree on a sample."""
+    g, r = W.dyck_zipf(16384)
+    outs = []
+    for kw in ({"gather_slices": 1}, {}, {"gather_slices": 3}, {"closure_mode": C.CFPQ_CLOSURE_TC_FP8}):
+        ctx = C.Context(**kw)
+        ctx.load_graph(g)
+        ctx.load_rsm(r)
+        st = ctx.run()
+        rows = [(s, x) for s in range(r.n_states) for x in range(0, g.n, 997)]
+        outs.append((st.iterations, ctx.reachable_words(0), ctx.closure_rows(rows)))
+        ctx.close()
+    for it, words, crows in outs[1:]:
+        assert it == outs[0][0]
+        assert (words == outs[0][1]).all()
+        assert (crows == outs[0][2]).all()
