@@ -96,6 +96,7 @@ struct SrcDesc {
     uint32_t pure_n;
     const uint32_t *pure_off[2];
     const uint32_t *pure_col;
+    const uint64_t *pure_mask[2];  // per label: bit y set iff y has an edge of it (W words)
 };
 
 // Gather work item: rows [row0, row1) of one output block.

@@ -175,6 +175,14 @@ int stage_graph(GraphDev *g, Allocator *A, cudaStream_t st, uint32_t n, uint32_t
     return CFPQ_OK;
 }
 
+int GraphDev::ensure_nonempty(Allocator *A, cudaStream_t st, std::string *err) {
+    if (nonempty.p && nonempty_generation == generation) return CFPQ_OK;
+    if (!nonempty.ensure(A, std::max<size_t>((size_t)n_term * W * 8, 64), err)) return CFPQ_ERR_OUT_OF_MEMORY;
+    ENG_CK(launch_nonempty_bits(csr_off.as<uint32_t>(), n, n_term, W, nonempty.as<uint64_t>(), st));
+    nonempty_generation = generation;
+    return CFPQ_OK;
+}
+
 int GraphDev::ensure_term_bits(Allocator *A, cudaStream_t st, std::string *err) {
     if (term_bits.p && term_bits_generation == generation && term_bits_m == m_unique) return CFPQ_OK;
     const size_t rows = (size_t)n_term * n;
@@ -485,8 +493,15 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
         GraphDev &g = *q.g;
         QCtl *cp = q.ctl();
         hp.push_back(cp);
-        bool need_term_bits = false;
-        for (const auto &sdesc : q.srcs) need_term_bits |= (sdesc.dense && sdesc.label_kind == 0);
+        bool need_term_bits = false, need_nonempty = false;
+        for (const auto &sdesc : q.srcs) {
+            need_term_bits |= (sdesc.dense && sdesc.label_kind == 0);
+            need_nonempty |= sdesc.pure_rb != 0;
+        }
+        if (need_nonempty) {
+            int rc = g.ensure_nonempty(A, st, err);
+            if (rc) return rc;
+        }
         if (need_term_bits) {
             int rc = g.ensure_term_bits(A, st, err);
             if (rc) return rc;
@@ -512,8 +527,10 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
             if (sd.pure_rb) {
                 const size_t rb = (size_t)sd.rblk;
                 d.pure_n = q.blk_pure_n[rb];
-                for (uint32_t p = 0; p < d.pure_n; ++p)
+                for (uint32_t p = 0; p < d.pure_n; ++p) {
                     d.pure_off[p] = g.csr_off.as<uint32_t>() + (size_t)q.blk_pure_lbl[rb * 2 + p] * q.n;
+                    d.pure_mask[p] = g.nonempty.as<uint64_t>() + (size_t)q.blk_pure_lbl[rb * 2 + p] * q.W;
+                }
                 d.pure_col = g.csr_col.as<uint32_t>();
             }
             d.ident = sd.ident;

@@ -54,6 +54,8 @@ cudaError_t launch_stage_unique(const uint32_t *off, uint32_t *col, uint32_t *uc
 cudaError_t launch_stage_compact(const uint32_t *off, const uint32_t *col, const uint32_t *uoff, uint32_t *ucol,
                                  size_t rows, cudaStream_t st);
 cudaError_t launch_popcount(const uint64_t *p, size_t nwords, unsigned long long *out, cudaStream_t st);
+cudaError_t launch_nonempty_bits(const uint32_t *off, uint32_t n, uint32_t n_term, uint32_t W, uint64_t *bits,
+                                 cudaStream_t st);
 cudaError_t launch_copy_rows(const uint64_t *const *ptrs, const uint32_t *rows, uint32_t njobs, uint32_t W,
                              uint64_t *out, cudaStream_t st);
 
@@ -134,6 +136,9 @@ struct GraphDev {
     uint64_t term_bits_generation = ~0ull;
     size_t term_bits_m = 0;
     int ensure_term_bits(Allocator *A, cudaStream_t st, std::string *err);
+    DBuf nonempty;  // [n_term * W] bit y of label l: row (l, y) of the CSR has an edge (pure-terminal reads)
+    uint64_t nonempty_generation = ~0ull;
+    int ensure_nonempty(Allocator *A, cudaStream_t st, std::string *err);
     // staging scratch
     DBuf e_src, e_lbl, e_dst, cnt, off, col, ucnt, scan_tmp, label_map, err;
     std::vector<uint32_t> h_off;  // host copies on demand (paths)

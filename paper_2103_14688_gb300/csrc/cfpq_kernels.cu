@@ -401,6 +401,27 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                                    ? reinterpret_cast<const uint4 *>(adj + (size_t)row * W)[v]
                                    : make_uint4(0, 0, 0, 0);
                     }
+                    if (d.pure_n) {
+                        // a row y of a pure-terminal block is empty unless y
+                        // has an edge of one of its labels
+#pragma unroll
+                        for (int j = 0; j < VPL; ++j) {
+                            const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
+                            if (v >= nvec) continue;
+                            uint4 m = reinterpret_cast<const uint4 *>(d.pure_mask[0])[v];
+                            if (d.pure_n > 1) or4(m, reinterpret_cast<const uint4 *>(d.pure_mask[1])[v]);
+                            a[j] = make_uint4(a[j].x & m.x, a[j].y & m.y, a[j].z & m.z, a[j].w & m.w);
+                        }
+                    }
+                    if (use_ident) {
+                        // product edges into t itself: bit y of the adjacency
+                        // row is bit y of the output row, and the lane that
+                        // holds an adjacency vector holds the same vector of
+                        // the output row -- no enumeration
+#pragma unroll
+                        for (int j = 0; j < VPL; ++j) or4(acc[j], a[j]);
+                        if (d.rblk == nullptr) continue;
+                    }
                     // Each lane proposes the lowest set bit of its part of the
                     // adjacency row per step (ballot/ffs enumeration).
                     while (true) {
@@ -944,6 +965,23 @@ __global__ void k_csr_to_bits(const uint32_t *__restrict__ off, const uint32_t *
     }
 }
 
+// bits[l * W + w] bit b = row (l, 64 w + b) of the CSR has an edge.
+__global__ void k_nonempty_bits(const uint32_t *__restrict__ off, uint32_t n, uint32_t n_term, uint32_t W,
+                                uint64_t *bits) {
+    const size_t total = (size_t)n_term * W;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t l = (uint32_t)(i / W), w = (uint32_t)(i % W);
+        uint64_t word = 0;
+        for (uint32_t b = 0; b < 64u; ++b) {
+            const uint32_t y = w * 64u + b;
+            if (y >= n) break;
+            const size_t r = (size_t)l * n + y;
+            if (off[r + 1] > off[r]) word |= 1ull << b;
+        }
+        bits[i] = word;
+    }
+}
+
 // --------------------------------------------------------------------------
 // Result helpers.
 // --------------------------------------------------------------------------
@@ -1107,6 +1145,13 @@ cudaError_t launch_csr_to_bits(const uint32_t *off, const uint32_t *col, size_t 
                                cudaStream_t st) {
     if (rows == 0) return cudaSuccess;
     k_csr_to_bits<<<grid_for(rows, 128), 128, 0, st>>>(off, col, rows, W, bits);
+    return cudaGetLastError();
+}
+cudaError_t launch_nonempty_bits(const uint32_t *off, uint32_t n, uint32_t n_term, uint32_t W, uint64_t *bits,
+                                 cudaStream_t st) {
+    const size_t total = (size_t)n_term * W;
+    if (total == 0) return cudaSuccess;
+    k_nonempty_bits<<<grid_for(total, 256), 256, 0, st>>>(off, n, n_term, W, bits);
     return cudaGetLastError();
 }
 cudaError_t launch_popcount(const uint64_t *p, size_t nwords, unsigned long long *out, cudaStream_t st) {
