@@ -274,8 +274,9 @@ int QueryDev::plan(std::string *err) {
     // Sources of block (s,t): transitions s -l-> u with u == t or t reachable from u.
     srcs.clear();
     n_tc_src = 0;
-    // compacted inner dimension: up to half of the rows, a multiple of 128
-    kcap = std::max<uint32_t>(128u, ((W * 32u) + 127u) & ~127u);
+    // compacted inner dimension: every row up to n = 8192 (operands of at
+    // most 2 n^2 bytes per source), half of the rows above, a multiple of 128
+    kcap = W * 64u <= 8192u ? W * 64u : std::max<uint32_t>(128u, ((W * 32u) + 127u) & ~127u);
     blk_src0.assign(blocks.size(), 0);
     blk_nsrc.assign(blocks.size(), 0);
     for (size_t b = 0; b < blocks.size(); ++b) {
@@ -563,8 +564,9 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                 // split over several items, so that rows with thousands of new
                 // edges (hubs) spread over several CTAs
                 const uint32_t nvec = q.W / 2u;
-                uint32_t n_slices = (has_nt && q.W >= 256u) ? std::min<uint32_t>(8u, q.W / 64u) : 1u;
-                if (q.gather_slices) n_slices = (has_nt && q.W >= 256u) ? std::min<uint32_t>(q.gather_slices, 16u) : 1u;
+                const bool sliceable = has_nt && q.W >= 128u;
+                uint32_t n_slices = sliceable ? (q.W >= 256u ? std::min<uint32_t>(8u, q.W / 64u) : 4u) : 1u;
+                if (q.gather_slices) n_slices = sliceable ? std::min<uint32_t>(q.gather_slices, 16u) : 1u;
                 for (uint32_t r0 = 0; r0 < q.n; r0 += rpi)
                 for (uint32_t sl = 0; sl < n_slices; ++sl) {
                     GItem it;

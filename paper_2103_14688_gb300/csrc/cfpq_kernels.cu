@@ -200,9 +200,9 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
     const int lpr = (int)it.lpr, grp = lane / lpr, gl = lane % lpr, rpw = 32 / lpr;
     const unsigned gmask = (lpr == 32 ? FULLMASK : ((1u << lpr) - 1u)) << (grp * lpr);
     const uint32_t W = it.W, nvec = W / 2;
-    // column slice of the nonterminal adjacency (general variant, rows of 4+
-    // vectors per lane: the engine slices only those)
-    constexpr bool kSlices = NT && VPL >= 4;
+    // column slice of the nonterminal adjacency (general variant, rows of 2+
+    // vectors per lane: the engine slices only rows of 8192+ bits)
+    constexpr bool kSlices = NT && VPL >= 2;
     const uint32_t sv0 = kSlices ? (it.slice & 0xFFFFu) : 0u, sv1 = kSlices ? (it.slice >> 16) : nvec;
     const bool sliced = kSlices && (sv0 != 0u || sv1 < nvec);
     uint32_t my_changed = 0, my_ors = 0;
