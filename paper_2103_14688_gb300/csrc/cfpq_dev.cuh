@@ -57,6 +57,13 @@ struct QCtl {
     // box b's matrix M2^b holds at least n^2 / kDenseDiv edges; decided at the
     // end of every iteration, so a pass never mixes the two forms of a source.
     unsigned long long *box_edges;    // per box: edges of M2^b (null: no switch)
+    // Boxes some transition of the query reads (bit b; all bits when a box >=
+    // 63 is read) and the per-box iteration mark written by extraction: an
+    // iteration whose new edges all lie in boxes nobody reads is the last one
+    // that changes anything, so the next (which adds nothing) is counted
+    // without running its passes.
+    const uint32_t *box_new_it;
+    unsigned long long nt_read_mask;
     uint32_t dense_mask;
     uint32_t n_boxes;
     uint32_t n;

@@ -293,6 +293,10 @@ int QueryDev::plan(std::string *err) {
         }
         blk_nsrc[b] = (uint32_t)srcs.size() - blk_src0[b];
     }
+    // Boxes read by some transition (bit 63: a box >= 63 is read).
+    nt_read_mask = 0;
+    for (const auto &tr : rsm.tr)
+        if (tr.kind == 1) nt_read_mask |= tr.sym < 63u ? (1ull << tr.sym) : (1ull << 63);
     // Pure-terminal blocks: every source a direct terminal transition u -l-> t
     // (no closure block read), at most two labels.  Such a block equals the
     // union of those adjacencies, so its readers expand CSR rows.
@@ -445,7 +449,7 @@ int QueryDev::enqueue_init(cudaStream_t st, uint32_t max_iter, uint32_t max_roun
     for (uint32_t k = 0; k < n_tc_src; ++k) ENG_CK(cudaMemsetAsync(tc_kcount(k), 0, 8, st));
     ENG_CK(launch_ctl_reset(ctl_ptr_mem.as<QCtl *>(), 1, max_iter, max_rounds, max_passes, n_levels, cyclic_mask,
                             closure_mode == CFPQ_CLOSURE_AUTO ? boxedge_mem.as<unsigned long long>() : nullptr, B, n,
-                            st));
+                            boxit_mem.as<uint32_t>(), nt_read_mask, st));
     ENG_CK(launch_eps_init(eps_mem.p, n_eps, 152, st));
     return CFPQ_OK;
 }

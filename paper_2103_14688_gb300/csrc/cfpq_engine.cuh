@@ -39,7 +39,8 @@ cudaError_t launch_csr_to_bits(const uint32_t *off, const uint32_t *col, size_t 
                                cudaStream_t st);
 cudaError_t launch_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds,
                              uint32_t max_passes, uint32_t n_levels, unsigned long long cyclic_mask,
-                             unsigned long long *box_edges, uint32_t n_boxes, uint32_t n, cudaStream_t st);
+                             unsigned long long *box_edges, uint32_t n_boxes, uint32_t n,
+                             const uint32_t *box_new_it, unsigned long long nt_read_mask, cudaStream_t st);
 cudaError_t launch_eps_init(const void *eds, uint32_t ned, uint32_t grid, cudaStream_t st);
 size_t eps_desc_size();
 void fill_eps_desc(void *dst, uint64_t *m2, uint64_t *a2, uint32_t *a2_it, uint32_t *box_new_it, QCtl *ctl,
@@ -186,6 +187,7 @@ struct QueryDev {
     std::vector<uint32_t> blk_level;           // per block, 0..n_levels-1
     uint32_t n_levels = 1;
     uint64_t cyclic_mask = 0;
+    unsigned long long nt_read_mask = 0;  // boxes read by some transition (bit 63: some box >= 63)
     std::vector<Src> srcs;
     std::vector<uint32_t> box_f0, box_nf;
     std::vector<uint32_t> fblocks;  // per box list of block ids (q0, f)

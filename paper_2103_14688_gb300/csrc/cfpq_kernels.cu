@@ -655,10 +655,21 @@ __device__ void control_body(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaG
                     if (c.box_edges[b] >= dense_at && dense_at > 0ull) m |= 1u << b;
                 c.dense_mask = m;
             }
+            bool read_new = true;  // does some transition read a box that gained edges?
+            if (c.box_new_it && c.n_boxes <= 63u && !((c.nt_read_mask >> 63) & 1ull)) {
+                read_new = false;
+                for (uint32_t b = 0; b < c.n_boxes; ++b)
+                    if (((c.nt_read_mask >> b) & 1ull) && c.box_new_it[b] == c.iter + 1u) read_new = true;
+            }
             if (c.new_edges == 0ull) {
                 c.phase = kPhaseDone;
             } else if (c.max_iter && c.iter >= c.max_iter) {
                 c.status = kStatusIterCap;
+                c.phase = kPhaseDone;
+            } else if (!read_new) {
+                // the next iteration's product equals this one's: it adds no
+                // edge, so it is the last one and is counted without passes
+                c.iters_done = c.iter + 1u;
                 c.phase = kPhaseDone;
             } else {
                 c.iter += 1;
@@ -772,7 +783,8 @@ __global__ void __launch_bounds__(1024) k_control(QCtl *const *ctls, uint32_t nq
 // Reset the loop state of queries [0, nq) (start of a run).
 __global__ void k_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds,
                             uint32_t max_passes, uint32_t n_levels, unsigned long long cyclic_mask,
-                            unsigned long long *box_edges, uint32_t n_boxes, uint32_t n) {
+                            unsigned long long *box_edges, uint32_t n_boxes, uint32_t n,
+                            const uint32_t *box_new_it, unsigned long long nt_read_mask) {
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
         QCtl c;
         memset(&c, 0, sizeof(c));
@@ -791,6 +803,8 @@ __global__ void k_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, u
         c.n_boxes = n_boxes;
         c.n = n;
         c.dense_mask = 0;
+        c.box_new_it = box_new_it;
+        c.nt_read_mask = nt_read_mask;
         *ctls[q] = c;
     }
 }
@@ -1079,9 +1093,10 @@ cudaError_t launch_control(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaGra
 
 cudaError_t launch_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, uint32_t max_rounds,
                              uint32_t max_passes, uint32_t n_levels, unsigned long long cyclic_mask,
-                             unsigned long long *box_edges, uint32_t n_boxes, uint32_t n, cudaStream_t st) {
+                             unsigned long long *box_edges, uint32_t n_boxes, uint32_t n,
+                             const uint32_t *box_new_it, unsigned long long nt_read_mask, cudaStream_t st) {
     k_ctl_reset<<<(nq + 255) / 256, 256, 0, st>>>(ctls, nq, max_iter, max_rounds, max_passes, n_levels, cyclic_mask,
-                                                  box_edges, n_boxes, n);
+                                                  box_edges, n_boxes, n, box_new_it, nt_read_mask);
     return cudaGetLastError();
 }
 

@@ -69,6 +69,23 @@ def test_rpq_small_vs_oracle(cfpq, seed, n, deg):
     assert (ctx.closure_rows(rows) == oracle.closure_rows(g, r, out, rows)).all()
 
 
+@pytest.mark.parametrize("seed", [4, 5])
+def test_rpq_iteration_count_equals_oracle_a(cfpq, seed):
+    """The multi-kernel loop counts the last iteration (the one that adds no
+    edge) exactly as Listing 1 does, including when it skips running it
+    because the new edges lie in boxes no transition reads."""
+    C = cfpq
+    g, r = W.rpq_abc(n=96, out_deg=3, seed=seed)
+    ref = oracle.kron_fixpoint(g, r)
+    for mode in (C.CFPQ_CLOSURE_AUTO, C.CFPQ_CLOSURE_TC_FP8):
+        ctx = C.Context(closure_mode=mode, no_single_cta=1)
+        ctx.load_graph(g)
+        ctx.load_rsm(r)
+        st = ctx.run()
+        assert st.iterations == ref.iterations == 2
+        assert (ctx.reachable_bits(0) == ref.m2[0]).all()
+
+
 def test_rpq_full_size_sampled(cfpq):
     g, r = W.rpq_abc()
     ctx, st, out = _run(cfpq, g, r)
