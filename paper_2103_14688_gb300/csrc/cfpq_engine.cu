@@ -571,7 +571,10 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                 const bool sliceable = has_nt && q.W >= 128u;
                 uint32_t n_slices = sliceable ? (q.W >= 256u ? std::min<uint32_t>(8u, q.W / 64u) : 4u) : 1u;
                 if (q.gather_slices) n_slices = sliceable ? std::min<uint32_t>(q.gather_slices, 16u) : 1u;
-                for (uint32_t r0 = 0; r0 < q.n; r0 += rpi)
+                // nonterminal blocks of wide rows: 128-row items (measured on
+                // Dyck-4; the CSR blocks of the RPQ bench prefer 64)
+                const uint32_t rows_item = (has_nt && q.W >= 256u) ? std::max<uint32_t>(rpi, 128u) : rpi;
+                for (uint32_t r0 = 0; r0 < q.n; r0 += rows_item)
                 for (uint32_t sl = 0; sl < n_slices; ++sl) {
                     GItem it;
                     it.out = q.blk_ptr((uint32_t)b);
@@ -581,7 +584,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                     it.src0 = base + q.blk_src0[b];
                     it.nsrc = q.blk_nsrc[b];
                     it.row0 = r0;
-                    it.row1 = std::min(q.n, r0 + rpi);
+                    it.row1 = std::min(q.n, r0 + rows_item);
                     it.W = q.W;
                     it.lpr = q.lpr;
                     it.level = L;
