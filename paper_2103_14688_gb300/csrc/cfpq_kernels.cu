@@ -123,6 +123,39 @@ struct GatherRing {
     static constexpr size_t bytes = on ? (size_t)8 * depth * 32 * VPL * 16 : 0;  // 8 warps
 };
 
+// The same for a warp that owns one row (lpr = 32, rows of 4+ vectors per
+// lane), with a row-sized shared-memory bitmap `bm` (uint4-aligned, the
+// vectors in row order): every lane sets the columns it finds with a shared
+// atomic -- no broadcast -- and the bitmap is ORed into the accumulators once.
+template <int VPL>
+__device__ __forceinline__ void or_pure_rows_smem(uint4 (&acc)[VPL], const SrcDesc &d, uint32_t y_l, bool keep_l,
+                                                  uint32_t nvec, int lane, uint4 *bm) {
+#pragma unroll
+    for (int j = 0; j < VPL; ++j) {
+        const uint32_t v = (uint32_t)lane + 32u * (uint32_t)j;
+        if (v < nvec) bm[v] = make_uint4(0, 0, 0, 0);
+    }
+    __syncwarp();
+    if (keep_l) {
+        unsigned int *w = reinterpret_cast<unsigned int *>(bm);
+        for (uint32_t p = 0; p < d.pure_n; ++p) {
+            const uint32_t *off = d.pure_off[p];
+            const uint32_t e1 = off[y_l + 1];
+            for (uint32_t e = off[y_l]; e < e1; ++e) {
+                const uint32_t z = d.pure_col[e];
+                atomicOr(w + (z >> 5), 1u << (z & 31u));
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < VPL; ++j) {
+        const uint32_t v = (uint32_t)lane + 32u * (uint32_t)j;
+        if (v < nvec) or4(acc[j], bm[v]);
+    }
+    __syncwarp();  // the bitmap (a ring slot) is reused afterwards
+}
+
 // Lowest set bit of a 128-bit vector, -1 if none; clears it when `clear`.
 __device__ __forceinline__ int lowbit4(uint4 &v, bool clear) {
     if (v.x) { int b = __ffs(v.x) - 1; if (clear) v.x &= v.x - 1; return b; }
@@ -235,6 +268,12 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                     const bool keep = has_l && (d.rblk == nullptr || thr == 0u || d.rstamp[y_l] >= thr);
                     if constexpr (NT) {
                         if (d.pure_n && !use_ident) {
+                            if constexpr (GatherRing<VPL>::on) {
+                                if (lpr == 32) {  // one row per warp: the bitmap in the ring's first slot
+                                    or_pure_rows_smem<VPL>(acc, d, y_l, keep, nvec, lane, ring);
+                                    return;
+                                }
+                            }
                             or_pure_rows<VPL>(acc, d, y_l, keep, lpr, gl, grp, gmask);
                             return;
                         }
