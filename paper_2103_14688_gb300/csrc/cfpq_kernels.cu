@@ -120,7 +120,10 @@ template <int VPL>
 struct GatherRing {
     static constexpr bool on = VPL >= 4;
     static constexpr int depth = VPL <= 8 ? 4 : 3;
-    static constexpr size_t bytes = on ? (size_t)8 * depth * 32 * VPL * 16 : 0;  // 8 warps
+    // narrower rows keep one row-sized slot per warp: the bitmap of
+    // pure-terminal reads (or_pure_rows_smem)
+    static constexpr int slots = on ? depth : 1;
+    static constexpr size_t bytes = (size_t)8 * slots * 32 * VPL * 16;  // 8 warps
 };
 
 // The same for a warp that owns one row (lpr = 32, rows of 4+ vectors per
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
     // general variant: per-warp ring of source rows loaded with cp.async
     extern __shared__ uint4 s_ring[];
     constexpr int P = GatherRing<VPL>::depth;
-    uint4 *ring = s_ring + (size_t)(threadIdx.x >> 5) * P * 32 * VPL;
+    uint4 *ring = s_ring + (size_t)(threadIdx.x >> 5) * GatherRing<VPL>::slots * 32 * VPL;
     // one CTA per live item (the grid covers every item of the class; CTAs
     // past the live count exit at once): a CTA that finishes early frees its
     // slot for the next one, which a persistent loop would not.
@@ -268,11 +271,9 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                     const bool keep = has_l && (d.rblk == nullptr || thr == 0u || d.rstamp[y_l] >= thr);
                     if constexpr (NT) {
                         if (d.pure_n && !use_ident) {
-                            if constexpr (GatherRing<VPL>::on) {
-                                if (lpr == 32) {  // one row per warp: the bitmap in the ring's first slot
-                                    or_pure_rows_smem<VPL>(acc, d, y_l, keep, nvec, lane, ring);
-                                    return;
-                                }
+                            if (lpr == 32) {  // one row per warp: the bitmap in the warp's first slot
+                                or_pure_rows_smem<VPL>(acc, d, y_l, keep, nvec, lane, ring);
+                                return;
                             }
                             or_pure_rows<VPL>(acc, d, y_l, keep, lpr, gl, grp, gmask);
                             return;
