@@ -121,7 +121,12 @@ struct GItem {
     // in 128-bit vectors: [slice & 0xFFFF, slice >> 16).  Items of one row
     // range with different slices share the output rows and merge them with
     // atomicOr; the CSR sources are taken by the slice that starts at 0.
+    // Slices take part only while a box in nt_boxes (the boxes read by the
+    // block's nonterminal sources) is dense (QCtl::dense_mask); otherwise the
+    // first slice covers every column and the others do nothing.
     uint32_t slice;
+    uint32_t nt_boxes;
+    uint32_t pad;
 };
 
 // Final-state block used by extraction: C[q0(b), f] with f final in box b.

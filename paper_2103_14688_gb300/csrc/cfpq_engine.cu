@@ -447,9 +447,10 @@ int QueryDev::enqueue_init(cudaStream_t st, uint32_t max_iter, uint32_t max_roun
     ENG_CK(cudaMemsetAsync(boxit_mem.p, 0, (size_t)B * 4, st));
     ENG_CK(cudaMemsetAsync(boxedge_mem.p, 0, (size_t)B * 8, st));
     for (uint32_t k = 0; k < n_tc_src; ++k) ENG_CK(cudaMemsetAsync(tc_kcount(k), 0, 8, st));
+    // per-box edge counts: the dense-box mask drives AUTO's tile switch and
+    // the column slices of the row gather in every mode
     ENG_CK(launch_ctl_reset(ctl_ptr_mem.as<QCtl *>(), 1, max_iter, max_rounds, max_passes, n_levels, cyclic_mask,
-                            closure_mode == CFPQ_CLOSURE_AUTO ? boxedge_mem.as<unsigned long long>() : nullptr, B, n,
-                            boxit_mem.as<uint32_t>(), nt_read_mask, st));
+                            boxedge_mem.as<unsigned long long>(), B, n, boxit_mem.as<uint32_t>(), nt_read_mask, st));
     ENG_CK(launch_eps_init(eps_mem.p, n_eps, 152, st));
     return CFPQ_OK;
 }
@@ -568,7 +569,12 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                 // split over several items, so that rows with thousands of new
                 // edges (hubs) spread over several CTAs
                 const uint32_t nvec = q.W / 2u;
-                const bool sliceable = has_nt && q.W >= 128u;
+                uint32_t nt_boxes = 0;  // boxes read by the block's nonterminal sources (first 32)
+                for (uint32_t k = 0; k < q.blk_nsrc[b]; ++k) {
+                    const auto &sd = q.srcs[q.blk_src0[b] + k];
+                    if (sd.label_kind != 0 && sd.label < 32u) nt_boxes |= 1u << sd.label;
+                }
+                const bool sliceable = has_nt && q.W >= 128u && nt_boxes != 0u;
                 uint32_t n_slices = sliceable ? (q.W >= 256u ? std::min<uint32_t>(8u, q.W / 64u) : 4u) : 1u;
                 if (q.gather_slices) n_slices = sliceable ? std::min<uint32_t>(q.gather_slices, 16u) : 1u;
                 // nonterminal blocks of wide rows: 128-row items (measured on
@@ -589,6 +595,8 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                     it.lpr = q.lpr;
                     it.level = L;
                     it.slice = (nvec * sl / n_slices) | ((nvec * (sl + 1) / n_slices) << 16);
+                    it.nt_boxes = nt_boxes;
+                    it.pad = 0;
                     hi[cls].push_back(it);
                 }
                 // tile sources of this block: one product job for the dirty-row

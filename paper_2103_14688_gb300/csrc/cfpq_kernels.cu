@@ -239,8 +239,13 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
     // column slice of the nonterminal adjacency (general variant, rows of 2+
     // vectors per lane: the engine slices only rows of 8192+ bits)
     constexpr bool kSlices = NT && VPL >= 2;
-    const uint32_t sv0 = kSlices ? (it.slice & 0xFFFFu) : 0u, sv1 = kSlices ? (it.slice >> 16) : nvec;
-    const bool sliced = kSlices && (sv0 != 0u || sv1 < nvec);
+    const bool slices_on = kSlices && (dmask & it.nt_boxes) != 0u;  // a box the block reads is dense
+    uint32_t sv0 = kSlices ? (it.slice & 0xFFFFu) : 0u, sv1 = kSlices ? (it.slice >> 16) : nvec;
+    if (kSlices && !slices_on) {
+        if (sv0 != 0u) continue;  // the first slice covers every column
+        sv1 = nvec;
+    }
+    const bool sliced = slices_on && (sv0 != 0u || sv1 < nvec);
     uint32_t my_changed = 0, my_ors = 0;
 
     for (uint32_t rbase = it.row0 + (uint32_t)(warp * rpw); rbase < it.row1; rbase += 8u * rpw) {
