@@ -88,7 +88,8 @@ typedef struct {
                                 memory (rows <= 512 bits) runs its fixpoint inside one CTA;
                                 1 = always use the multi-kernel loop */
     uint32_t gather_slices;  /* column slices of the nonterminal adjacency per work item of the
-                                row gather: 0 = automatic (rows of >= 16384 bits: 4-8),
+                                row gather (used only while a box the block reads holds
+                                >= n^2/32 edges): 0 = automatic (rows of >= 8192 bits: 4-8),
                                 k >= 1 = k (capped at 16); the result does not depend on it */
     size_t memory_budget;    /* bytes of device memory a context may hold; 0 = no limit */
     cfpq_alloc_fn alloc;     /* NULL = cudaMallocAsync */
