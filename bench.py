@@ -18,7 +18,8 @@ The other workloads print their own line with ``--workload``:
   dyck     Dyck-4 on a Zipf graph (n = 65536 by default): closure Bool-GOPS,
            bit-packed and tensor-core closure modes;
   batched  512 (graph, RSM) queries in one batch vs one at a time;
-  served   resident 32768-vertex graph, Poisson arrivals, p50/p99 latency.
+  served   resident 32768-vertex graph, Poisson arrivals, p50/p99 latency;
+  sources  multiple-source RPQ (1, 16, 256 sources) against the full run.
 """
 from __future__ import annotations
 
@@ -395,6 +396,28 @@ def run_other(args):
         line.update({"metric": "Dyck-4 index creation time", "unit": "ms", "value": res[names[0]]["ms"],
                      "higher_is_better": False, "n": g.n, "m": g.m, "modes": res,
                      f"modes_equal_{names[0]}": same})
+    elif args.workload == "sources":
+        # multiple-source runs: only rows reachable from the sources
+        out = []
+        for n, deg in ((8192, 8), (65536, 2)):
+            g, r = W.rpq_abc(n=n, out_deg=deg)
+            ctx = cfpq.Context()
+            ctx.load_graph(g)
+            ctx.load_rsm(r)
+            ctx.run()
+            st, ms_full = _ctx_time(ctx, stream, ctx.run)
+            full = ctx.reachable_words(0)
+            rows = {"n": n, "out_degree": deg, "full_ms": ms_full}
+            for k in (1, 16, 256):
+                src = list(range(0, n, n // k))[:k]
+                ctx.run_sources(src)
+                st, ms = _ctx_time(ctx, stream, lambda: ctx.run_sources(src))
+                same = bool((ctx.reachable_words(0)[src] == full[src]).all())
+                rows[f"sources_{k}"] = {"ms": ms, "speedup_vs_full": ms_full / ms, "rows_equal_full": same}
+            out.append(rows)
+            ctx.close()
+        line.update({"metric": "multiple-source RPQ time (rows reachable from the sources only)", "unit": "ms",
+                     "value": out[0]["sources_16"]["ms"], "higher_is_better": False, "graphs": out})
     elif args.workload == "batched":
         qs = W.batched_queries(count=args.batch)
         ctx = cfpq.Context()
@@ -519,7 +542,7 @@ def main():
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--cpu-sources", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="rpq", choices=["rpq", "cycles", "dyck", "batched", "served"])
+    ap.add_argument("--workload", default="rpq", choices=["rpq", "cycles", "dyck", "batched", "served", "sources"])
     ap.add_argument("--dyck-n", type=int, default=65536)
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--lambdas", default="10,30,100,300,1000")

@@ -189,6 +189,21 @@ int cfpq_load_rsm(cfpq_ctx *ctx, const cfpq_rsm *rsm);
  * (the partial index stays readable).  stats may be NULL. */
 int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats);
 
+/* Multiple-source index creation (the multiple-source version named as
+ * future work in Sec. 6).  sources: host array of n_sources vertex ids
+ * (< n_vertices, duplicates allowed; NULL when n_sources is 0).  Like
+ * cfpq_run, but for an RSM whose transitions read only terminals the closure
+ * computes only the rows of C3 reachable in the Kronecker product from
+ * (q0, x), q0 the start state of the start box and x a source: afterwards
+ * the rows x in sources of every nonterminal's M2 are exact (and so are the
+ * other reached rows); a row of an unreached vertex x holds at most (x, x),
+ * the pair the empty word gives when the box's start state is final.  When a
+ * transition reads a nonterminal (M3 grows with M2) every row is computed,
+ * as by cfpq_run.  Errors: CFPQ_ERR_INVALID_ARG (NULL ctx, NULL sources with
+ * n_sources > 0, a source out of range), CFPQ_ERR_STATE (no graph or RSM),
+ * and those of cfpq_run. */
+int cfpq_run_sources(cfpq_ctx *ctx, const uint32_t *sources, uint32_t n_sources, cfpq_run_stats *stats);
+
 /* Count nnz(C3) and nnz(M3) of the last run into *closure_bits / *m3_bits. */
 int cfpq_count_index(cfpq_ctx *ctx, uint64_t *closure_bits, uint64_t *m3_bits);
 

@@ -117,6 +117,7 @@ def _declare(lib):
         "cfpq_load_graph_device_noalloc": (c_int, [P, c_uint32, c_uint32, c_size_t, P, P, P]),
         "cfpq_load_rsm": (c_int, [P, POINTER(cfpq_rsm)]),
         "cfpq_run": (c_int, [P, POINTER(cfpq_run_stats)]),
+        "cfpq_run_sources": (c_int, [P, POINTER(c_uint32), c_uint32, POINTER(cfpq_run_stats)]),
         "cfpq_count_index": (c_int, [P, u64p, u64p]),
         "cfpq_get_reachable": (c_int, [P, c_uint32, u32p, u32p, c_size_t, POINTER(c_size_t)]),
         "cfpq_count_reachable": (c_int, [P, c_uint32, u64p]),
@@ -286,6 +287,14 @@ class Context:
     def run(self) -> cfpq_run_stats:
         st = cfpq_run_stats()
         self._check(self.lib.cfpq_run(self.h, ctypes.byref(st)), "cfpq_run")
+        return st
+
+    def run_sources(self, sources) -> cfpq_run_stats:
+        """Index creation for the source vertices only (exact rows for them)."""
+        src = _u32(np.asarray(sources, dtype=np.uint32).reshape(-1))
+        st = cfpq_run_stats()
+        self._check(self.lib.cfpq_run_sources(self.h, _u32p(src) if len(src) else None, len(src), ctypes.byref(st)),
+                    "cfpq_run_sources")
         return st
 
     def count_index(self) -> Tuple[int, int]:

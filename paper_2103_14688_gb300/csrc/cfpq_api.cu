@@ -133,22 +133,26 @@ int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t 
     return CFPQ_OK;
 }
 
-int ensure_query(cfpq_ctx *ctx) {
+int ensure_query(cfpq_ctx *ctx, bool restricted = false) {
     if (!ctx->has_graph) return fail(ctx, CFPQ_ERR_STATE, "no graph loaded");
     if (!ctx->has_rsm) return fail(ctx, CFPQ_ERR_STATE, "no RSM loaded");
     QueryDev &q = ctx->query;
     q.g = &ctx->graph;
     q.closure_mode = ctx->opt.closure_mode;
     q.gather_slices = ctx->opt.gather_slices;
+    if (q.restricted != restricted) ctx->exec_dirty = true;  // the work items carry the row masks
+    q.restricted = restricted;
     if (!q.prepared || q.graph_generation != ctx->graph.generation || ctx->exec_dirty) {
         std::string e;
         int rc = q.prepare(&ctx->A, &e);
         if (rc) return fail(ctx, rc, e);
+        if (restricted && !q.reach_mem.ensure(&ctx->A, (size_t)q.Q * q.W * 8, &e))
+            return fail(ctx, CFPQ_ERR_OUT_OF_MEMORY, e);
         ctx->exec.qs.assign(1, &q);
         rc = ctx->exec.assemble(&ctx->A, ctx->stream, &e);
         if (rc) return fail(ctx, rc, e);
         q.small_ok = false;
-        if (!ctx->opt.no_single_cta) {
+        if (!ctx->opt.no_single_cta && !restricted) {
             rc = q.prepare_small(&ctx->A, ctx->stream, ctx->opt.max_iterations, kDefaultPassCap, &e);
             if (rc) return fail(ctx, rc, e);
         }
@@ -308,6 +312,45 @@ int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats) {
     const double ms = std::chrono::duration<double, std::milli>(t2 - t0).count();
     if (stats) {
         fill_stats(stats, ctls[0], ctx->query, ms);
+        stats->gpu_launches = launches;
+        stats->ms_closure = ms_cl;
+        stats->closure_launches = claunch;
+        stats->ms_setup = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        stats->ms_loop = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    }
+    const int st = status_of(ctls[0]);
+    if (st) return fail(ctx, st, "iteration, round or pass cap reached before the fixpoint");
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+int cfpq_run_sources(cfpq_ctx *ctx, const uint32_t *sources, uint32_t n_sources, cfpq_run_stats *stats) {
+    if (!ctx || (n_sources && !sources)) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (!ctx->has_graph) return fail(ctx, CFPQ_ERR_STATE, "no graph loaded");
+    if (!ctx->has_rsm) return fail(ctx, CFPQ_ERR_STATE, "no RSM loaded");
+    for (uint32_t i = 0; i < n_sources; ++i)
+        if (sources[i] >= ctx->graph.n) return fail(ctx, CFPQ_ERR_INVALID_ARG, "source vertex out of range");
+    bool reads_nt = false;
+    for (const auto &tr : ctx->query.rsm.tr) reads_nt |= tr.kind == 1;
+    if (reads_nt) return cfpq_run(ctx, stats);  // M3 grows with M2: every row is computed
+    const auto t0 = std::chrono::steady_clock::now();
+    if (int rc = set_device(ctx)) return rc;
+    if (int rc = ensure_query(ctx, true)) return rc;
+    {
+        std::string e;
+        int rc = ctx->query.compute_reach(&ctx->A, ctx->stream, sources, n_sources, &e);
+        if (rc) return fail(ctx, rc, e);
+    }
+    const auto t1 = std::chrono::steady_clock::now();
+    std::vector<QCtl> ctls;
+    uint32_t launches = 0, claunch = 0;
+    double ms_cl = 0.0;
+    if (int rc = run_executor(ctx, ctx->exec, &ctls, &launches, &ms_cl, &claunch)) return rc;
+    ctx->has_result = true;
+    const auto t2 = std::chrono::steady_clock::now();
+    if (stats) {
+        fill_stats(stats, ctls[0], ctx->query, std::chrono::duration<double, std::milli>(t2 - t0).count());
         stats->gpu_launches = launches;
         stats->ms_closure = ms_cl;
         stats->closure_launches = claunch;

@@ -112,6 +112,7 @@ struct GItem {
     uint32_t *out_stamp;
     uint32_t *out_last;
     QCtl *ctl;
+    const uint64_t *rmask;  // multiple-source runs: rows to compute (bit per row), else null
     uint32_t src0, nsrc;
     uint32_t row0, row1;
     uint32_t W;    // words per row

@@ -11,14 +11,6 @@
 
 namespace cfpq {
 
-#define ENG_CK(call)                                                                          \
-    do {                                                                                      \
-        cudaError_t _e = (call);                                                              \
-        if (_e != cudaSuccess) {                                                              \
-            if (err) *err = std::string(#call) + ": " + cudaGetErrorString(_e);               \
-            return CFPQ_ERR_CUDA;                                                             \
-        }                                                                                     \
-    } while (0)
 
 void *Allocator::get(size_t bytes, std::string *err) {
     bytes = (bytes + 255) & ~(size_t)255;
@@ -587,6 +579,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                     it.out_stamp = q.stamp_ptr((uint32_t)b);
                     it.out_last = q.last_mem.as<uint32_t>() + b;
                     it.ctl = cp;
+                    it.rmask = q.restricted ? q.reach_ptr(q.blocks[b].first) : nullptr;
                     it.src0 = base + q.blk_src0[b];
                     it.nsrc = q.blk_nsrc[b];
                     it.row0 = r0;

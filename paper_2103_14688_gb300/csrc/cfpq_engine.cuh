@@ -9,6 +9,16 @@
 #include "../../include/cfpq.h"
 #include "cfpq_dev.cuh"
 
+// CUDA call inside a function returning a CFPQ status (with std::string *err in scope).
+#define ENG_CK(call)                                                                          \
+    do {                                                                                      \
+        cudaError_t _e = (call);                                                              \
+        if (_e != cudaSuccess) {                                                              \
+            if (err) *err = std::string(#call) + ": " + cudaGetErrorString(_e);               \
+            return CFPQ_ERR_CUDA;                                                             \
+        }                                                                                     \
+    } while (0)
+
 namespace cfpq {
 
 // ---- kernel launchers (cfpq_kernels.cu) ----
@@ -161,6 +171,13 @@ struct QueryDev {
     // host descriptors (pointers filled once buffers exist; ctl set by the executor)
     uint32_t closure_mode = CFPQ_CLOSURE_AUTO;
     uint32_t gather_slices = 0;  // cfpq_options::gather_slices
+    // Multiple-source runs: per state the rows reachable from the sources
+    // (compute_reach); the work items of block (s, t) then skip the rows of
+    // state s outside them.
+    bool restricted = false;
+    DBuf reach_mem, reach_f, reach_misc;
+    uint64_t *reach_ptr(uint32_t s) const { return reach_mem.as<uint64_t>() + (size_t)s * W; }
+    int compute_reach(Allocator *A, cudaStream_t st, const uint32_t *h_src, uint32_t ns, std::string *err);
     struct Src {
         uint32_t label_kind, label, ident;
         int32_t rblk;

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
 
     for (uint32_t rbase = it.row0 + (uint32_t)(warp * rpw); rbase < it.row1; rbase += 8u * rpw) {
         const uint32_t row = rbase + grp;
-        const bool valid = row < it.row1;
+        const bool valid = row < it.row1 && (!it.rmask || ((it.rmask[row >> 6] >> (row & 63u)) & 1ull));
         uint4 acc[VPL];
 #pragma unroll
         for (int j = 0; j < VPL; ++j) acc[j] = make_uint4(0, 0, 0, 0);
