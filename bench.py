@@ -19,7 +19,9 @@ The other workloads print their own line with ``--workload``:
            bit-packed and tensor-core closure modes;
   batched  512 (graph, RSM) queries in one batch vs one at a time;
   served   resident 32768-vertex graph, Poisson arrivals, p50/p99 latency;
-  sources  multiple-source RPQ (1, 16, 256 sources) against the full run.
+  sources  multiple-source RPQ (1, 16, 256 sources) against the full run;
+  paths    all-path extraction (vs -> vf, at most L edges) after index
+           creation, against Oracle C on the same calls.
 """
 from __future__ import annotations
 
@@ -418,6 +420,62 @@ def run_other(args):
             ctx.close()
         line.update({"metric": "multiple-source RPQ time (rows reachable from the sources only)", "unit": "ms",
                      "value": out[0]["sources_16"]["ms"], "higher_is_better": False, "graphs": out})
+    elif args.workload == "paths":
+        # all-path extraction after index creation: device backward layers
+        # prune the host enumeration; Oracle C (all paths up to L, words
+        # tested) timed on the same calls where it finishes quickly
+        import oracle
+        from collections import deque
+        out = []
+        for name, (g, r), lens in (("rpq_abc_n8192_deg8", W.rpq_abc(n=8192, out_deg=8), (4, 6, 8)),
+                                   ("dyck4_zipf_n4096", W.dyck_zipf(n=4096), (4, 6, 8))):
+            ctx = cfpq.Context()
+            ctx.load_graph(g)
+            ctx.load_rsm(r)
+            ctx.run()
+            words = ctx.reachable_words(0)
+            adj = [[] for _ in range(g.n)]
+            for a, b in zip(np.asarray(g.src).tolist(), np.asarray(g.dst).tolist()):
+                adj[a].append(b)
+            rng = np.random.Generator(np.random.PCG64(2103_14688))
+            for L in lens:
+                pairs = []
+                for vs in rng.permutation(g.n).tolist():
+                    dist, dq = {vs: 0}, deque([vs])
+                    while dq:
+                        v = dq.popleft()
+                        if dist[v] < L:
+                            for w in adj[v]:
+                                if w not in dist:
+                                    dist[w] = dist[v] + 1
+                                    dq.append(w)
+                    near = [v for v in dist if (int(words[vs, v >> 6]) >> (v & 63)) & 1]
+                    if near:
+                        pairs.append((vs, int(rng.choice(near))))
+                    if len(pairs) == 8:
+                        break
+                ts, npaths, same, ots = [], [], True, []
+                for vs, vf in pairs:
+                    t0 = time.perf_counter()
+                    got, trunc = ctx.extract_paths(0, vs, vf, L)
+                    ts.append(1e3 * (time.perf_counter() - t0))
+                    npaths.append(len(got))
+                    if L <= 8 and sum(ots) < 20e3:
+                        t0 = time.perf_counter()
+                        want = oracle.brute_paths(g, r, 0, vs, vf, L, path_cap=1 << 20, edge_cap=1 << 26)
+                        ots.append(1e3 * (time.perf_counter() - t0))
+                        same &= got == want
+                slow = max(ts) > 10e3
+                out.append({"graph": name, "max_len": L, "pairs": len(pairs), "ms_median": float(np.median(ts)),
+                            "ms_max": float(max(ts)), "paths_median": float(np.median(npaths)),
+                            "paths_max": int(max(npaths)),
+                            "oracle_ms_median": float(np.median(ots)) if ots else None,
+                            "oracle_calls": len(ots), "equal_oracle": bool(same)})
+                if slow:  # longer bounds would take longer still
+                    break
+            ctx.close()
+        line.update({"metric": "all-path extraction time per (vs, vf) call (median, Dyck-4 at the largest bound)",
+                     "unit": "ms", "value": out[-1]["ms_median"], "higher_is_better": False, "runs": out})
     elif args.workload == "batched":
         qs = W.batched_queries(count=args.batch)
         ctx = cfpq.Context()
@@ -542,7 +600,7 @@ def main():
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--cpu-sources", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="rpq", choices=["rpq", "cycles", "dyck", "batched", "served", "sources"])
+    ap.add_argument("--workload", default="rpq", choices=["rpq", "cycles", "dyck", "batched", "served", "sources", "paths"])
     ap.add_argument("--dyck-n", type=int, default=65536)
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--lambdas", default="10,30,100,300,1000")

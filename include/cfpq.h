@@ -238,7 +238,15 @@ int cfpq_get_closure_rows(cfpq_ctx *ctx, uint32_t n_rows, const uint32_t *row_st
  * entries).  *n_paths receives the number of paths returned; *truncated (may
  * be NULL) is set to 1 if max_paths stopped the enumeration.  The empty path
  * is returned for vs == vf when box derives the empty word.
- * CFPQ_ERR_BUFFER_TOO_SMALL if edge_cap (in triples) was too small. */
+ * The product paths of M3 are walked forward on the host.  For every target
+ * (box, vertex) met, the device first computes the backward layers: the
+ * product vertices that can reach the target within k edges, for
+ * k <= max_len.  Partial paths outside them are dropped, so the result does
+ * not depend on them.  Device memory for this call: the reverse terminal CSR,
+ * (max_len + 1) * Q * n_pad / 8 bytes of layers, and n_pad^2 / 8 bytes per
+ * box that a nonterminal transition reads (its M2, transposed).
+ * CFPQ_ERR_BUFFER_TOO_SMALL if edge_cap (in triples) was too small;
+ * CFPQ_ERR_OUT_OF_MEMORY if the device buffers do not fit. */
 int cfpq_extract_paths(cfpq_ctx *ctx, uint32_t box, uint32_t vs, uint32_t vf, uint32_t max_len, size_t max_paths,
                        uint32_t *edge_buf, size_t edge_cap, size_t *path_offsets, size_t *n_paths,
                        int *truncated);

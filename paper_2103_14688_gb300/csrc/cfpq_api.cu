@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <set>
@@ -12,6 +13,7 @@
 #include <vector>
 
 #include "cfpq_ctx.cuh"
+#include "cfpq_paths_host.h"
 
 using namespace cfpq;
 
@@ -247,6 +249,7 @@ static int load_graph_impl(cfpq_ctx *ctx, uint32_t n, uint32_t nt, size_t m, con
     API_TRY
     if (int rc = set_device(ctx)) return rc;
     ctx->has_result = false;
+    ++ctx->result_gen;
     std::string e;
     int rc = stage_graph(&ctx->graph, &ctx->A, ctx->stream, n, nt, m, s, l, d, dev, &e);
     if (rc) {
@@ -282,6 +285,7 @@ int cfpq_load_rsm(cfpq_ctx *ctx, const cfpq_rsm *rsm) {
     ctx->query.rsm = std::move(h);
     ctx->has_rsm = true;
     ctx->has_result = false;
+    ++ctx->result_gen;
     ctx->exec_dirty = true;
     return CFPQ_OK;
     API_CATCH(ctx)
@@ -308,6 +312,7 @@ int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats) {
         return rc;
     }
     ctx->has_result = true;
+    ++ctx->result_gen;
     const auto t2 = std::chrono::steady_clock::now();
     const double ms = std::chrono::duration<double, std::milli>(t2 - t0).count();
     if (stats) {
@@ -348,6 +353,7 @@ int cfpq_run_sources(cfpq_ctx *ctx, const uint32_t *sources, uint32_t n_sources,
     double ms_cl = 0.0;
     if (int rc = run_executor(ctx, ctx->exec, &ctls, &launches, &ms_cl, &claunch)) return rc;
     ctx->has_result = true;
+    ++ctx->result_gen;
     const auto t2 = std::chrono::steady_clock::now();
     if (stats) {
         fill_stats(stats, ctls[0], ctx->query, std::chrono::duration<double, std::milli>(t2 - t0).count());
@@ -530,121 +536,10 @@ int cfpq_get_closure_rows(cfpq_ctx *ctx, uint32_t n_rows, const uint32_t *row_st
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Path extraction (Sec. 3.2, Listing 2), on the host.
+// Path extraction (Sec. 3.2, Listing 2): enumeration in cfpq_paths_host.h,
+// backward layers on the device (cfpq_paths.cu).
 // ---------------------------------------------------------------------------
-// getPaths(vs, vf, N) follows product paths of M3 from (q0_N, vs) to (f, vf),
-// f final in N's box; a product edge over a terminal is a graph edge, one over
-// a nonterminal N' with M2^{N'}[v, v'] = 1 expands into getPaths(v, v', N').
-// The sets are bounded by the number of graph edges (max_len) and computed as
-// the least fixpoint of these equations over keys (N, x, y, length), so that
-// recursion through nonterminals deriving the empty word terminates.
-namespace {
-
-struct PathCtx {
-    const HostRSM *r;
-    uint32_t n;
-    std::vector<uint32_t> es, el, ed;        // unique edges sorted by (src, label, dst)
-    std::vector<uint32_t> eoff;              // per source vertex
-    std::vector<std::vector<uint64_t>> m2;   // per box, n * wn words
-    size_t wn;
-    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, std::set<std::vector<uint32_t>>> memo;
-    size_t stored = 0, cap = 4000000;
-    bool over = false;
-
-    const std::set<std::vector<uint32_t>> &get(uint32_t N, uint32_t x, uint32_t y, uint32_t len) {
-        auto key = std::make_tuple(N, x, y, len);
-        auto it = memo.find(key);
-        if (it == memo.end()) it = memo.emplace(key, std::set<std::vector<uint32_t>>()).first;
-        return it->second;
-    }
-
-    // One evaluation of Paths(N, x, y, len) from the current memo values.
-    std::set<std::vector<uint32_t>> eval(uint32_t N, uint32_t x, uint32_t y, uint32_t len) {
-        using PSet = std::set<std::vector<uint32_t>>;
-        // layer[k]: map (state, vertex) -> paths of k edges from (q0, x)
-        std::vector<std::map<std::pair<uint32_t, uint32_t>, PSet>> layer(len + 1);
-        const uint32_t q0 = r->box_start[N];
-        layer[0][{q0, x}].insert(std::vector<uint32_t>());
-        for (uint32_t k = 0; k <= len; ++k) {
-            bool grew = true;
-            while (grew && !over) {
-                grew = false;
-                auto snapshot = layer[k];
-                for (auto &kv : snapshot) {
-                    const uint32_t s = kv.first.first, v = kv.first.second;
-                    const PSet &S = kv.second;
-                    for (const auto &t : r->tr) {
-                        if (t.from != s) continue;
-                        if (t.kind == 0) {
-                            if (k + 1 > len) continue;
-                            for (uint32_t e = eoff[v]; e < eoff[v + 1]; ++e) {
-                                if (el[e] != t.sym) continue;
-                                PSet &D = layer[k + 1][{t.to, ed[e]}];
-                                for (const auto &p : S) {
-                                    auto q = p;
-                                    q.push_back(e);
-                                    D.insert(std::move(q));
-                                }
-                            }
-                        } else {
-                            const uint64_t *row = m2[t.sym].data() + (size_t)v * wn;
-                            for (size_t w = 0; w < wn; ++w) {
-                                uint64_t b = row[w];
-                                while (b) {
-                                    const uint32_t v2 = (uint32_t)(w * 64 + (uint64_t)__builtin_ctzll(b));
-                                    b &= b - 1;
-                                    for (uint32_t j = 0; k + j <= len; ++j) {
-                                        const PSet &sub = get(t.sym, v, v2, j);
-                                        if (sub.empty()) continue;
-                                        PSet &D = layer[k + j][{t.to, v2}];
-                                        const size_t before = D.size();
-                                        for (const auto &p : S)
-                                            for (const auto &s2 : sub) {
-                                                auto q = p;
-                                                q.insert(q.end(), s2.begin(), s2.end());
-                                                D.insert(std::move(q));
-                                            }
-                                        if (j == 0 && D.size() != before) grew = true;
-                                    }
-                                }
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        PSet out;
-        for (uint32_t f = 0; f < r->Q; ++f) {
-            if (r->state_box[f] != N || !r->final_[f]) continue;
-            auto it = layer[len].find({f, y});
-            if (it != layer[len].end()) out.insert(it->second.begin(), it->second.end());
-        }
-        return out;
-    }
-
-    // Chaotic iteration to the least fixpoint over every key in the memo.
-    void solve() {
-        bool changed = true;
-        while (changed && !over) {
-            changed = false;
-            std::vector<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>> keys;
-            for (auto &kv : memo) keys.push_back(kv.first);
-            for (auto &k : keys) {
-                auto v = eval(std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k));
-                auto &cur = memo[k];
-                if (v.size() != cur.size()) {
-                    stored += v.size() - cur.size();
-                    cur = std::move(v);
-                    changed = true;
-                    if (stored > cap) over = true;
-                }
-            }
-            if (memo.size() != keys.size()) changed = true;
-        }
-    }
-};
-
-}  // namespace
+using PathCtx = cfpq::PathEnum<cfpq::HostRSM>;
 
 extern "C" int cfpq_extract_paths(cfpq_ctx *ctx, uint32_t box, uint32_t vs, uint32_t vf, uint32_t max_len,
                                   size_t max_paths, uint32_t *edge_buf, size_t edge_cap, size_t *path_offsets,
@@ -655,45 +550,97 @@ extern "C" int cfpq_extract_paths(cfpq_ctx *ctx, uint32_t box, uint32_t vs, uint
     QueryDev &q = ctx->query;
     if (box >= q.B || vs >= q.n || vf >= q.n) return fail(ctx, CFPQ_ERR_INVALID_ARG, "box or vertex out of range");
     if (int rc = set_device(ctx)) return rc;
-    PathCtx P;
-    P.r = &q.rsm;
-    P.n = q.n;
-    P.wn = (q.n + 63) / 64;
-    // host copies: unique terminal edges and M2 of every box
-    const GraphDev &g = ctx->graph;
-    std::vector<uint32_t> off((size_t)g.n_term * g.n + 1), col(std::max<size_t>(g.m_unique, 1));
-    CK(ctx, cudaMemcpy(off.data(), g.csr_off.p, off.size() * 4, cudaMemcpyDeviceToHost));
-    if (g.m_unique) CK(ctx, cudaMemcpy(col.data(), g.csr_col.p, g.m_unique * 4, cudaMemcpyDeviceToHost));
-    std::vector<std::tuple<uint32_t, uint32_t, uint32_t>> tri;
-    for (uint32_t l = 0; l < g.n_term; ++l)
-        for (uint32_t x = 0; x < g.n; ++x)
-            for (uint32_t e = off[(size_t)l * g.n + x]; e < off[(size_t)l * g.n + x + 1]; ++e)
-                tri.emplace_back(x, l, col[e]);
-    std::sort(tri.begin(), tri.end());
-    tri.erase(std::unique(tri.begin(), tri.end()), tri.end());
-    P.eoff.assign(g.n + 1, 0);
-    for (auto &t : tri) {
-        P.es.push_back(std::get<0>(t));
-        P.el.push_back(std::get<1>(t));
-        P.ed.push_back(std::get<2>(t));
-        P.eoff[std::get<0>(t) + 1]++;
+    std::string e;
+    // The host copies, the device tables and the memo of path sets stay valid
+    // until the next result (run, graph or RSM change).
+    if (!ctx->penum || ctx->penum_gen != ctx->result_gen) {
+        ctx->penum.reset(new PathCtx());
+        PathCtx &P = *ctx->penum;
+        P.r = &q.rsm;
+        P.n = q.n;
+        P.wn = (q.n + 63) / 64;
+        // host copies: unique terminal edges and M2 of every box
+        const GraphDev &g = ctx->graph;
+        std::vector<uint32_t> off((size_t)g.n_term * g.n + 1), col(std::max<size_t>(g.m_unique, 1));
+        CK(ctx, cudaMemcpy(off.data(), g.csr_off.p, off.size() * 4, cudaMemcpyDeviceToHost));
+        if (g.m_unique) CK(ctx, cudaMemcpy(col.data(), g.csr_col.p, g.m_unique * 4, cudaMemcpyDeviceToHost));
+        std::vector<std::tuple<uint32_t, uint32_t, uint32_t>> tri;
+        for (uint32_t l = 0; l < g.n_term; ++l)
+            for (uint32_t x = 0; x < g.n; ++x)
+                for (uint32_t k = off[(size_t)l * g.n + x]; k < off[(size_t)l * g.n + x + 1]; ++k)
+                    tri.emplace_back(x, l, col[k]);
+        std::sort(tri.begin(), tri.end());
+        tri.erase(std::unique(tri.begin(), tri.end()), tri.end());
+        P.eoff.assign(g.n + 1, 0);
+        for (auto &t : tri) {
+            P.es.push_back(std::get<0>(t));
+            P.el.push_back(std::get<1>(t));
+            P.ed.push_back(std::get<2>(t));
+            P.eoff[std::get<0>(t) + 1]++;
+        }
+        for (uint32_t v = 0; v < g.n; ++v) P.eoff[v + 1] += P.eoff[v];
+        // reverse terminal CSR over (label, target vertex) for the backward layers
+        std::vector<uint32_t> roff((size_t)g.n_term * g.n + 1, 0), rcol(tri.size());
+        for (auto &t : tri) ++roff[(size_t)std::get<1>(t) * g.n + std::get<2>(t) + 1];
+        for (size_t i = 1; i < roff.size(); ++i) roff[i] += roff[i - 1];
+        {
+            std::vector<uint32_t> fill(roff.begin(), roff.end() - 1);
+            for (auto &t : tri) rcol[fill[(size_t)std::get<1>(t) * g.n + std::get<2>(t)]++] = std::get<0>(t);
+        }
+        if (int rc = ctx->paths.prepare(&ctx->A, ctx->stream, q, g.n_term, roff, rcol, &e)) {
+            ctx->penum.reset();
+            return fail(ctx, rc, e);
+        }
+        P.Qd = q.Q;
+        P.Wd = q.W;
+        P.m2.resize(q.B);
+        for (uint32_t b = 0; b < q.B; ++b) {
+            P.m2[b].resize((size_t)q.n * P.wn);
+            if (int rc = bits_to_host(ctx, q.m2_ptr(b), q.n, q.W, P.m2[b].data())) {
+                ctx->penum.reset();
+                return rc;
+            }
+        }
+        ctx->penum_gen = ctx->result_gen;
     }
-    for (uint32_t v = 0; v < g.n; ++v) P.eoff[v + 1] += P.eoff[v];
-    P.m2.resize(q.B);
-    for (uint32_t b = 0; b < q.B; ++b) {
-        P.m2[b].resize((size_t)q.n * P.wn);
-        if (int rc = bits_to_host(ctx, q.m2_ptr(b), q.n, q.W, P.m2[b].data())) return rc;
+    PathCtx &P = *ctx->penum;
+    // layers of a larger bound contain those of a smaller one
+    if (max_len > P.Lmax) {
+        P.Lmax = max_len;
+        P.lay.clear();
+        P.wanted.clear();
+        P.fdist.clear();
     }
+    if (P.stored > P.cap / 2) {
+        P.memo.clear();
+        P.readers.clear();
+        P.stored = 0;
+    }
+    P.over = false;
+    P.dev_rc = 0;
+    const uint32_t L = P.Lmax;
+    P.fetch = [ctx, &q, &e, L](const std::vector<PathCtx::Target> &ts, std::vector<std::vector<uint64_t>> *out) {
+        return ctx->paths.layers(&ctx->A, ctx->stream, q.rsm, ts, L, out, &e);
+    };
     // Paths in order of length, then lexicographic (edge ids follow the triple order).
     std::vector<std::vector<uint32_t>> result;
     bool trunc = false;
     const uint64_t *root = P.m2[box].data() + (size_t)vs * P.wn;
     const bool reachable = (root[vf >> 6] >> (vf & 63)) & 1;
+    // until the fixpoints below complete, the cached memo is not reusable
+    // (an exception leaves it marked stale)
+    ctx->penum_gen = ~0ull;
     if (reachable) {
         for (uint32_t len = 0; len <= max_len && !trunc; ++len) {
             P.get(box, vs, vf, len);
             P.solve();
-            if (P.over) return fail(ctx, CFPQ_ERR_UNSUPPORTED, "path enumeration exceeded its work cap");
+            if (P.dev_rc || P.over) {
+                // an interrupted fixpoint leaves partial sets: drop them
+                const int rc = P.dev_rc;
+                ctx->penum.reset();
+                if (rc) return fail(ctx, rc, "backward layers: " + e);
+                return fail(ctx, CFPQ_ERR_UNSUPPORTED, "path enumeration exceeded its work cap");
+            }
             const auto &S = P.memo[std::make_tuple(box, vs, vf, len)];
             for (const auto &p : S) {
                 if (result.size() == max_paths) { trunc = true; break; }
@@ -701,6 +648,7 @@ extern "C" int cfpq_extract_paths(cfpq_ctx *ctx, uint32_t box, uint32_t vs, uint
             }
         }
     }
+    ctx->penum_gen = ctx->result_gen;
     size_t need = 0;
     for (auto &p : result) need += p.size();
     *n_paths = result.size();

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "cfpq_engine.cuh"
+#include "cfpq_paths_host.h"
 
 struct cfpq_ctx {
     using Allocator = cfpq::Allocator;
@@ -24,6 +25,7 @@ struct cfpq_ctx {
     uint64_t exec_generation = ~0ull;
     bool exec_dirty = true;
     bool has_result = false;
+    uint64_t result_gen = 0;  // bumped whenever the result changes or is dropped
     // batch
     std::vector<std::unique_ptr<GraphDev>> bgraphs;
     std::vector<std::unique_ptr<QueryDev>> bqueries;
@@ -32,6 +34,11 @@ struct cfpq_ctx {
     // scratch for small transfers
     DBuf counter;
     DBuf rows_ptrs, rows_idx, rows_out;
+    // path extraction: backward layers on the device; the enumerator (host
+    // copies and memo) of result result_gen
+    cfpq::PathsDev paths;
+    std::unique_ptr<cfpq::PathEnum<cfpq::HostRSM>> penum;
+    uint64_t penum_gen = ~0ull;
     ~cfpq_ctx() {
         // Buffers are released by their destructors through A (declared first).
     }

@@ -572,6 +572,11 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                 // nonterminal blocks of wide rows: 128-row items (measured on
                 // Dyck-4; the CSR blocks of the RPQ bench prefer 64)
                 const uint32_t rows_item = (has_nt && q.W >= 256u) ? std::max<uint32_t>(rpi, 128u) : rpi;
+                // the gather keeps an item's row mask in 16 words of shared memory
+                if (rows_item > 1024u || rows_item % 64u != 0u) {
+                    *err = "gather items: rows per item must be a multiple of 64 and at most 1024";
+                    return CFPQ_ERR_INVALID_ARG;
+                }
                 for (uint32_t r0 = 0; r0 < q.n; r0 += rows_item)
                 for (uint32_t sl = 0; sl < n_slices; ++sl) {
                     GItem it;

@@ -259,6 +259,30 @@ struct Executor {
     int read_ctls(cudaStream_t st, std::vector<QCtl> *out, int *tc_error = nullptr);
 };
 
+// Backward layers of path extraction (Sec. 3.2): for a target (box N,
+// vertex y), layer k holds the product vertices (s, x) from which some (f, y),
+// f final in N, is reached in M3 over at most k graph edges (a nonterminal
+// edge counts one edge unless it stays on its vertex).  prepare() uploads the
+// reverse terminal CSR and the RSM transitions grouped by target state, and
+// transposes M2 of every box a nonterminal transition reads; layers() runs
+// the search and copies layers 0..L to the host ((L + 1) * Q * W words,
+// layer-major, then state, then the vertex's word).
+struct PathsDev {
+    uint32_t n = 0, W = 0, Q = 0, B = 0, n_nt = 0;
+    const uint64_t *m2 = nullptr;
+    std::vector<uint32_t> host_tab;
+    DBuf tables, rev_off, rev_col, mt, lay, delta, flag;
+    int prepare(Allocator *A, cudaStream_t st, const QueryDev &q, uint32_t n_term, const std::vector<uint32_t> &h_roff,
+                const std::vector<uint32_t> &h_rcol, std::string *err);
+    // Layers of several targets (box, vertex), searched side by side in
+    // batches of at most 1 GiB; out[i] gets target i's layers.
+    int layers(Allocator *A, cudaStream_t st, const HostRSM &rsm,
+               const std::vector<std::pair<uint32_t, uint32_t>> &targets, uint32_t L,
+               std::vector<std::vector<uint64_t>> *out, std::string *err);
+    int layers_batch(Allocator *A, cudaStream_t st, const HostRSM &rsm, const std::pair<uint32_t, uint32_t> *targets,
+                     uint32_t T, uint32_t L, std::vector<uint64_t> *out, std::string *err);
+};
+
 int stage_graph(GraphDev *g, Allocator *A, cudaStream_t st, uint32_t n, uint32_t n_term, size_t m, const uint32_t *src,
                 const uint32_t *lbl, const uint32_t *dst, bool device_ptrs, std::string *err);
 

@@ -209,6 +209,10 @@ template <int VPL, bool NT>
 __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
     k_gather(const GItem *__restrict__ items, const SrcDesc *__restrict__ srcs, ExecTables T, int cls) {
     __shared__ unsigned long long s_changed, s_ors;
+    // rows of the item to compute (multiple-source runs; else all): the item's
+    // rows start at a multiple of 64 and number at most 1024, so its 16 mask
+    // words have distinct indices modulo 16
+    __shared__ unsigned long long s_rmask[16];
     // general variant: per-warp ring of source rows loaded with cp.async
     extern __shared__ uint4 s_ring[];
     constexpr int P = GatherRing<VPL>::depth;
@@ -230,6 +234,10 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
     if (!__syncthreads_or(act)) continue;
 
     if (threadIdx.x == 0) { s_changed = 0; s_ors = 0; }
+    if (threadIdx.x < 16u) {
+        const uint32_t wrow = it.row0 + threadIdx.x * 64u;
+        s_rmask[(wrow >> 6) & 15u] = (it.rmask && wrow < it.row1) ? it.rmask[wrow >> 6] : ~0ull;
+    }
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -250,7 +258,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
 
     for (uint32_t rbase = it.row0 + (uint32_t)(warp * rpw); rbase < it.row1; rbase += 8u * rpw) {
         const uint32_t row = rbase + grp;
-        const bool valid = row < it.row1 && (!it.rmask || ((it.rmask[row >> 6] >> (row & 63u)) & 1ull));
+        const bool valid = row < it.row1 && ((s_rmask[(row >> 6) & 15u] >> (row & 63u)) & 1ull);
         uint4 acc[VPL];
 #pragma unroll
         for (int j = 0; j < VPL; ++j) acc[j] = make_uint4(0, 0, 0, 0);

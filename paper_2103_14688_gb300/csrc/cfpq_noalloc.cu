@@ -109,6 +109,7 @@ extern "C" int cfpq_load_graph_device_noalloc(cfpq_ctx *ctx, uint32_t n, uint32_
         int *errf = reinterpret_cast<int *>(base + kNaErr);
         const cudaStream_t st = ctx->stream;
         ctx->has_result = false;
+        ++ctx->result_gen;
         ctx->has_graph = false;
 #define NA_CK(call)                                                                                 \
     do {                                                                                            \
