@@ -265,8 +265,9 @@ struct Executor {
 // edge counts one edge unless it stays on its vertex).  prepare() uploads the
 // reverse terminal CSR and the RSM transitions grouped by target state, and
 // transposes M2 of every box a nonterminal transition reads; layers() runs
-// the search and copies layers 0..L to the host ((L + 1) * Q * W words,
-// layer-major, then state, then the vertex's word).
+// the search for a list of targets and copies, per target, layers 0..L to
+// the host ((L + 1) * Q * W words: layer-major, then state, then the
+// vertex's word).
 struct PathsDev {
     uint32_t n = 0, W = 0, Q = 0, B = 0, n_nt = 0;
     const uint64_t *m2 = nullptr;
