@@ -343,7 +343,7 @@ def _ctx_time(ctx, stream, fn):
 
 
 def run_other(args):
-    """The other configurations, one JSON line each (not the default line)."""
+    """The other configurations, one JSON line each (besides the default RPQ line)."""
     import torch
     from paper_2103_14688_gb300 import cfpq
     dev = torch.device("cuda", 0)

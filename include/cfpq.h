@@ -48,7 +48,7 @@ extern "C" {
 #define CFPQ_ERR_NOT_READY (-5)        /* result asked for before it exists */
 #define CFPQ_ERR_CUDA (-6)             /* a CUDA runtime call failed */
 #define CFPQ_ERR_STATE (-7)            /* calls in the wrong order (e.g. run before load) */
-#define CFPQ_ERR_UNSUPPORTED (-8)      /* size or mode this build does not handle */
+#define CFPQ_ERR_UNSUPPORTED (-8)      /* size or mode the library does not handle */
 
 typedef struct cfpq_ctx cfpq_ctx;
 
@@ -71,7 +71,7 @@ typedef void (*cfpq_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
 #define CFPQ_CLOSURE_TC_FP8 2
 #define CFPQ_CLOSURE_TC_I8 3     /* 0/1 INT8 tcgen05 products: CFPQ_ERR_UNSUPPORTED on sm_103a (no kind::i8) */
 
-/* Fixpoint loop driver (Listing 1, "while M2 is changing"). */
+/* Fixpoint loop control (Listing 1, "while M2 is changing"). */
 #define CFPQ_LOOP_DEVICE 0 /* one CUDA-graph launch; device-side convergence flags */
 #define CFPQ_LOOP_HOST 1   /* host reads the convergence flags after every pass */
 
