@@ -65,6 +65,45 @@ struct PathEnum {
         }
         return it->second.data();
     }
+    // Word lengths of each box up to Lmax, from the RSM alone: words[b][j] is
+    // set iff box b derives a word of j terminals.  A path of j edges derived
+    // from b needs one, so a subcall of a length b cannot spell is empty.
+    std::vector<std::vector<uint8_t>> words;
+    uint32_t words_L = ~0u;
+    void word_lengths() {
+        if (words_L == Lmax) return;
+        const uint32_t L1 = Lmax + 1;
+        words.assign(r->B, std::vector<uint8_t>(L1, 0));
+        // at[s][j]: state s is reached from its box's start state over j terminals
+        std::vector<std::vector<uint8_t>> at(r->Q, std::vector<uint8_t>(L1, 0));
+        for (uint32_t b = 0; b < r->B; ++b) at[r->box_start[b]][0] = 1;
+        for (bool grew = true; grew;) {
+            grew = false;
+            for (const auto &t : r->tr)
+                for (uint32_t j = 0; j < L1; ++j) {
+                    if (!at[t.from][j]) continue;
+                    for (uint32_t i = t.kind == 0 ? 1u : 0u; j + i < L1; ++i) {
+                        if (t.kind == 0 ? i != 1u : !words[t.sym][i]) {
+                            if (t.kind == 0) break;
+                            continue;
+                        }
+                        if (!at[t.to][j + i]) {
+                            at[t.to][j + i] = 1;
+                            grew = true;
+                        }
+                    }
+                }
+            for (uint32_t f = 0; f < r->Q; ++f)
+                if (r->final_[f])
+                    for (uint32_t j = 0; j < L1; ++j)
+                        if (at[f][j] && !words[r->state_box[f]][j]) {
+                            words[r->state_box[f]][j] = 1;
+                            grew = true;
+                        }
+        }
+        words_L = Lmax;
+    }
+
     // Graph distance from v over any labels, capped at Lmax + 1 (breadth-first,
     // depth Lmax): a subpath v -> v2 of j edges exists only if it is <= j.
     std::map<uint32_t, std::vector<uint16_t>> fdist;
@@ -127,7 +166,8 @@ struct PathEnum {
         // layer[k]: map (state, vertex) -> paths of k edges from (q0, x)
         std::vector<std::map<std::pair<uint32_t, uint32_t>, PSet>> layer(len + 1);
         const uint32_t q0 = r->box_start[N];
-        if (!live(q0, x, len)) return PSet();
+        word_lengths();
+        if (!words[N][len] || !live(q0, x, len)) return PSet();
         layer[0][{q0, x}].insert(std::vector<uint32_t>());
         for (uint32_t k = 0; k <= len; ++k) {
             bool grew = true;
@@ -161,7 +201,7 @@ struct PathEnum {
                                     const uint32_t v2 = (uint32_t)(w * 64 + (uint64_t)__builtin_ctzll(b));
                                     b &= b - 1;
                                     for (uint32_t j = dv[v2]; k + j <= len; ++j) {
-                                        if (!live(t.to, v2, len - k - j)) continue;
+                                        if (!words[t.sym][j] || !live(t.to, v2, len - k - j)) continue;
                                         const PSet &sub = get(t.sym, v, v2, j);
                                         if (sub.empty()) continue;
                                         PSet &Dst = layer[k + j][{t.to, v2}];
