@@ -428,7 +428,7 @@ def run_other(args):
         from collections import deque
         out = []
         for name, (g, r), lens in (("rpq_abc_n8192_deg8", W.rpq_abc(n=8192, out_deg=8), (4, 6, 8)),
-                                   ("dyck4_zipf_n4096", W.dyck_zipf(n=4096), (4, 6, 8))):
+                                   ("dyck4_zipf_n4096", W.dyck_zipf(n=4096), (4, 8, 12))):
             ctx = cfpq.Context()
             ctx.load_graph(g)
             ctx.load_rsm(r)
@@ -460,7 +460,7 @@ def run_other(args):
                     got, trunc = ctx.extract_paths(0, vs, vf, L)
                     ts.append(1e3 * (time.perf_counter() - t0))
                     npaths.append(len(got))
-                    if L <= 8 and sum(ots) < 20e3:
+                    if sum(ots) < 20e3:
                         t0 = time.perf_counter()
                         want = oracle.brute_paths(g, r, 0, vs, vf, L, path_cap=1 << 20, edge_cap=1 << 26)
                         ots.append(1e3 * (time.perf_counter() - t0))
