@@ -388,7 +388,13 @@ def run_other(args):
                          "issued_tensor_tflop": st.tile_kstages * 2.0 * 128 * 256 * 128 / 1e12,
                          "pairs": ctx.count_reachable(0),
                          "executed_bool_gops": st.row_ors * st.row_bytes * 8 / (ms / 1e3) / 1e9,
-                         "device_gb": st.device_bytes / 1e9}
+                         "device_gb": st.device_bytes / 1e9,
+                         "tile_products_per_iteration": st.tile_mmas / max(1, st.iterations)}
+            # Theorem 2's work count, W = (nnz(M3) + nnz(C3)) * |Q|n
+            cbits, m3bits = ctx.count_index()
+            res[name].update({"closure_bits": cbits, "m3_bits": m3bits,
+                              "closure_bool_gops_paper_accounting":
+                                  (cbits + m3bits) * r.n_states * g.n / (ms / 1e3) / 1e9})
             res[name]["words"] = ctx.reachable_words(0)
             ctx.close()
         ref = res[names[0]]["words"]
