@@ -305,7 +305,10 @@ int cfpq_poll(cfpq_server *srv, uint64_t ticket, int *done);
  * cfpq_get_reachable_bits). */
 int cfpq_result_reachable_bits(cfpq_server *srv, uint64_t ticket, uint32_t box, uint64_t *bits);
 
-/* Free a finished query's device state and forget the ticket. */
+/* Forget the ticket and free the query's device state: a finished query is
+ * released, a waiting one is dropped, a running one is cancelled (its passes
+ * run only inside cfpq_server_step, so none is in flight between calls; the
+ * other queries continue unchanged). */
 int cfpq_release(cfpq_server *srv, uint64_t ticket);
 
 /* ---- building block: dense Boolean product on the tensor cores ---------------------- */

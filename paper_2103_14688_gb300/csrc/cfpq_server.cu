@@ -234,7 +234,19 @@ int cfpq_release(cfpq_server *s, uint64_t ticket) {
     if (!s) return CFPQ_ERR_INVALID_ARG;
     auto it = s->jobs.find(ticket);
     if (it == s->jobs.end()) return sfail(s, CFPQ_ERR_INVALID_ARG, "unknown ticket");
-    if (it->second.state == kRunning) return sfail(s, CFPQ_ERR_STATE, "query still running");
+    if (it->second.state == kRunning) {
+        // cancelled: its passes run only inside cfpq_server_step, which
+        // returns with the stream drained, so nothing of it is in flight;
+        // the next step assembles the work lists without it
+        for (auto r = s->running.begin(); r != s->running.end(); ++r)
+            if (*r == ticket) {
+                s->running.erase(r);
+                break;
+            }
+        s->exec_dirty = true;
+        if (cudaSetDevice(s->opt.device) != cudaSuccess || cudaStreamSynchronize(s->stream) != cudaSuccess)
+            return sfail(s, CFPQ_ERR_CUDA, "stream synchronisation failed");
+    }
     if (it->second.state == kWaiting) {
         for (auto w = s->waiting.begin(); w != s->waiting.end(); ++w)
             if (*w == ticket) {

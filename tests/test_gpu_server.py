@@ -102,3 +102,31 @@ def test_server_release_of_waiting_query(C):
     assert (srv.result_bits(t1, 0) == oracle.worklist(g, r)[0]).all()
     with pytest.raises(C.CfpqError):
         srv.poll(t2)
+
+
+def test_server_cancel_running_query(C):
+    """A running query released between steps is cancelled; the queries
+    running beside it finish with their solo answers, and the server takes
+    new work afterwards."""
+    g, r = W.dyck_zipf(512, seed=6)
+    qs = W.serving_workload(n=512, pool_size=6, seed=6)
+    pool = [r] + list(qs.pool[:3])
+    srv = C.Server(g)
+    tickets = [srv.submit(x) for x in pool]
+    run, _ = srv.step()
+    assert run >= 1
+    victim = tickets[0]
+    assert not srv.poll(victim)  # still running: Dyck-4 needs many passes
+    srv.release(victim)
+    with pytest.raises(C.CfpqError):
+        srv.poll(victim)
+    rest = tickets[1:]
+    _drain(srv, rest)
+    for t, x in zip(rest, pool[1:]):
+        want = _solo(C, g, x)
+        for b in range(x.n_boxes):
+            assert (srv.result_bits(t, b) == want[b]).all(), (t, b)
+        srv.release(t)
+    t2 = srv.submit(r)
+    _drain(srv, [t2])
+    assert (srv.result_bits(t2, 0) == oracle.worklist(g, r)[0]).all()
