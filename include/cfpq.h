@@ -354,6 +354,17 @@ int cfpq_load_graph_device_noalloc(cfpq_ctx *ctx, uint32_t n_vertices, uint32_t 
 
 /* ---- diagnostics ----------------------------------------------------------------------- */
 
+/* Diagnostic of failure detection.  Every spin-wait of the library's kernels
+ * (the mbarrier waits of the tensor-core tile pipeline) is bounded: after 2 s
+ * (or 2^26 polls) the kernel gives up, records an error flag, finishes without
+ * the awaited data and the run returns CFPQ_ERR_TIMEOUT, with the context
+ * still usable.  This call runs that same wait in one thread on an mbarrier
+ * that nothing arrives at, bounded by limit_ns (1 ns .. 5 s), on the
+ * context's stream, and sets *timed_out to 1 when it gave up (0 would mean
+ * the barrier completed, which cannot happen).  CFPQ_ERR_INVALID_ARG for a
+ * limit outside that range. */
+int cfpq_check_bounded_wait(cfpq_ctx *ctx, uint64_t limit_ns, int *timed_out);
+
 const char *cfpq_status_string(int status);
 const char *cfpq_last_error(const cfpq_ctx *ctx);
 

@@ -119,6 +119,7 @@ def _declare(lib):
         "cfpq_run": (c_int, [P, POINTER(cfpq_run_stats)]),
         "cfpq_run_sources": (c_int, [P, POINTER(c_uint32), c_uint32, POINTER(cfpq_run_stats)]),
         "cfpq_count_index": (c_int, [P, u64p, u64p]),
+        "cfpq_check_bounded_wait": (c_int, [P, c_uint64, POINTER(c_int)]),
         "cfpq_get_reachable": (c_int, [P, c_uint32, u32p, u32p, c_size_t, POINTER(c_size_t)]),
         "cfpq_count_reachable": (c_int, [P, c_uint32, u64p]),
         "cfpq_get_reachable_bits": (c_int, [P, c_uint32, P]),
@@ -296,6 +297,14 @@ class Context:
         self._check(self.lib.cfpq_run_sources(self.h, _u32p(src) if len(src) else None, len(src), ctypes.byref(st)),
                     "cfpq_run_sources")
         return st
+
+    def check_bounded_wait(self, limit_ns: int) -> bool:
+        """Run the kernels' bounded mbarrier wait on a barrier nothing
+        arrives at; True when it gave up after ``limit_ns``."""
+        t = c_int()
+        self._check(self.lib.cfpq_check_bounded_wait(self.h, c_uint64(limit_ns), ctypes.byref(t)),
+                    "cfpq_check_bounded_wait")
+        return bool(t.value)
 
     def count_index(self) -> Tuple[int, int]:
         a, b = c_uint64(), c_uint64()

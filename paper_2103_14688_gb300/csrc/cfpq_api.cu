@@ -369,6 +369,24 @@ int cfpq_run_sources(cfpq_ctx *ctx, const uint32_t *sources, uint32_t n_sources,
     API_CATCH(ctx)
 }
 
+int cfpq_check_bounded_wait(cfpq_ctx *ctx, uint64_t limit_ns, int *timed_out) {
+    if (!ctx || !timed_out || limit_ns == 0 || limit_ns > 5000000000ull) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (int rc = set_device(ctx)) return rc;
+    std::string e;
+    if (!ctx->counter.ensure(&ctx->A, 64, &e)) return fail(ctx, CFPQ_ERR_OUT_OF_MEMORY, e);
+    int *d = ctx->counter.as<int>();
+    CK(ctx, cudaMemsetAsync(d, 0xff, 4, ctx->stream));
+    CK(ctx, launch_wait_selftest(limit_ns, d, ctx->stream));
+    int h = -1;
+    CK(ctx, cudaMemcpyAsync(&h, d, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (h != 0 && h != 1) return fail(ctx, CFPQ_ERR_CUDA, "wait self-check did not report");
+    *timed_out = h;
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
 int cfpq_count_index(cfpq_ctx *ctx, uint64_t *closure_bits, uint64_t *m3_bits) {
     if (!ctx) return CFPQ_ERR_INVALID_ARG;
     API_TRY

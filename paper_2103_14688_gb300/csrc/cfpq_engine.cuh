@@ -44,6 +44,9 @@ cudaError_t launch_tc_product_tma(const TcJob *jobs, const void *maps, uint32_t 
 size_t tc_map_bytes();
 cudaError_t tc_encode_maps(const TcJob *jobs, uint32_t n_jobs, void *out);
 cudaError_t prepare_tc_launch();
+// One thread waits on an mbarrier nothing arrives at, with the tile kernels'
+// bounded wait (limit limit_ns); *timed_out (device) = 1 when it gave up.
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int *timed_out, cudaStream_t st);
 cudaError_t prepare_gather_launch();
 cudaError_t launch_csr_to_bits(const uint32_t *off, const uint32_t *col, size_t rows, uint32_t W, uint64_t *bits,
                                cudaStream_t st);

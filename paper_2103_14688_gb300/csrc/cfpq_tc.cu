@@ -39,7 +39,8 @@ constexpr int kStageB = kBN * kBK;
 constexpr int kStageBytes = kStageA + kStageB;        // 48 KiB
 constexpr int kThreads = 256;
 constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kWaitLimit = 1u << 26;             // bounded spin on mbarriers
+constexpr uint32_t kWaitLimit = 1u << 26;             // bounded spin on mbarriers: polls ...
+constexpr uint64_t kWaitNs = 2000000000ull;           // ... and nanoseconds of %globaltimer
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -90,11 +91,35 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
     return ok != 0u;
 }
 
-// Bounded wait; returns false if the limit was reached.
-__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: false once limit_ns of %globaltimer or kWaitLimit polls have
+// passed (the callers then record an error status and finish their work
+// without the awaited data).
+__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity, uint64_t limit_ns = kWaitNs) {
+    if (mbar_try_wait(m, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
         if (mbar_try_wait(m, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
     return false;
+}
+
+// Self-check of the bounded wait: one thread waits on an mbarrier that no
+// thread ever arrives at, so the wait must give up after limit_ns.
+__global__ void k_wait_selftest(uint64_t limit_ns, int *timed_out) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *timed_out = mbar_wait(&bar, 0u, limit_ns) ? 0 : 1;
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
+    }
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -935,6 +960,11 @@ cudaError_t launch_tc_product_tma(const TcJob *jobs, const void *maps, uint32_t 
     if (max_tiles < grid) grid = max_tiles;
     k_tc_product_tma<<<grid, tc2::kThreads, tc2::kRing * tc2::kStage + 1024u, st>>>(
         jobs, static_cast<const unsigned char *>(maps), T, err_flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int *timed_out, cudaStream_t st) {
+    tc::k_wait_selftest<<<1, 32, 0, st>>>(limit_ns, timed_out);
     return cudaGetLastError();
 }
 
