@@ -242,11 +242,19 @@ int cfpq_get_closure_rows(cfpq_ctx *ctx, uint32_t n_rows, const uint32_t *row_st
  * (box, vertex) met, the device first computes the backward layers: the
  * product vertices that can reach the target within k edges, for
  * k <= max_len.  Partial paths outside them are dropped, so the result does
- * not depend on them.  Device memory for this call: the reverse terminal CSR,
- * (max_len + 1) * Q * n_pad / 8 bytes of layers, and n_pad^2 / 8 bytes per
- * box that a nonterminal transition reads (its M2, transposed).
+ * not depend on them.  Targets are searched in batches.  Device memory kept
+ * by the context for these calls:
+ *   - the reverse terminal CSR;
+ *   - (max_len + 1) * Q * n_pad / 8 bytes of layers per target of a batch,
+ *     at most 1 GiB;
+ *   - n_pad^2 / 8 bytes per box that a nonterminal transition reads (its M2,
+ *     transposed).
+ * The host copies and the memo of subpath sets are kept between calls
+ * until the result changes (a run, or a new graph or RSM).
  * CFPQ_ERR_BUFFER_TOO_SMALL if edge_cap (in triples) was too small;
- * CFPQ_ERR_OUT_OF_MEMORY if the device buffers do not fit. */
+ * CFPQ_ERR_OUT_OF_MEMORY if the device buffers do not fit; CFPQ_ERR_UNSUPPORTED
+ * if the enumeration exceeds its work cap (4e6 stored paths or 2^20 subpath
+ * sets). */
 int cfpq_extract_paths(cfpq_ctx *ctx, uint32_t box, uint32_t vs, uint32_t vf, uint32_t max_len, size_t max_paths,
                        uint32_t *edge_buf, size_t edge_cap, size_t *path_offsets, size_t *n_paths,
                        int *truncated);
