@@ -204,6 +204,26 @@ int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats);
  * and those of cfpq_run. */
 int cfpq_run_sources(cfpq_ctx *ctx, const uint32_t *sources, uint32_t n_sources, cfpq_run_stats *stats);
 
+/* Checkpoint and resume (the fixpoint of Listing 1 is monotone).  The
+ * checkpoint of a result is its M2, read with cfpq_get_reachable_bits for
+ * every box.  cfpq_set_start(ctx, bits, n_boxes, n_vertices) makes the next
+ * cfpq_run calls start from such pairs.
+ *   - Layout: n_boxes blocks of n_vertices rows of ceil(n_vertices/64)
+ *     words, box-major, the cfpq_get_reachable_bits layout.  The bits are
+ *     copied.
+ *   - What a run does with them: the pairs are added to M2 after the epsilon
+ *     rows and enter the first iteration as new edges (A2 := M2 on their
+ *     rows).  The run then reaches the least fixpoint containing them.
+ *   - When the result equals a run without them: whenever the pairs belong to
+ *     this graph's answer, e.g. the answer of an earlier run on a subset of
+ *     its edges, or of this graph.  The run then needs fewer iterations.
+ *   - Pairs outside the answer stay in the result.
+ *   - bits = NULL clears the start.
+ * A run returns CFPQ_ERR_INVALID_ARG while the start's n_boxes and
+ * n_vertices differ from the loaded RSM and graph.  cfpq_run_sources returns
+ * CFPQ_ERR_STATE while a start is set.  Seeded pairs count in edges_added. */
+int cfpq_set_start(cfpq_ctx *ctx, const uint64_t *bits, uint32_t n_boxes, uint32_t n_vertices);
+
 /* Count nnz(C3) and nnz(M3) of the last run into *closure_bits / *m3_bits. */
 int cfpq_count_index(cfpq_ctx *ctx, uint64_t *closure_bits, uint64_t *m3_bits);
 

@@ -120,6 +120,7 @@ def _declare(lib):
         "cfpq_run_sources": (c_int, [P, POINTER(c_uint32), c_uint32, POINTER(cfpq_run_stats)]),
         "cfpq_count_index": (c_int, [P, u64p, u64p]),
         "cfpq_check_bounded_wait": (c_int, [P, c_uint64, POINTER(c_int)]),
+        "cfpq_set_start": (c_int, [P, P, c_uint32, c_uint32]),
         "cfpq_get_reachable": (c_int, [P, c_uint32, u32p, u32p, c_size_t, POINTER(c_size_t)]),
         "cfpq_count_reachable": (c_int, [P, c_uint32, u64p]),
         "cfpq_get_reachable_bits": (c_int, [P, c_uint32, P]),
@@ -297,6 +298,19 @@ class Context:
         self._check(self.lib.cfpq_run_sources(self.h, _u32p(src) if len(src) else None, len(src), ctypes.byref(st)),
                     "cfpq_run_sources")
         return st
+
+    def set_start(self, words=None):
+        """Start the next runs from the given M2 per box (uint64 words
+        [n_boxes, n, ceil(n/64)], as reachable_words returns them per box);
+        None clears the start."""
+        if words is None:
+            self._check(self.lib.cfpq_set_start(self.h, None, 0, 0), "cfpq_set_start")
+            return
+        w = np.ascontiguousarray(np.asarray(words, dtype=np.uint64))
+        if w.ndim != 3:
+            raise ValueError("start words must be [n_boxes, n, ceil(n/64)]")
+        self._check(self.lib.cfpq_set_start(self.h, c_void_p(w.ctypes.data), w.shape[0], w.shape[1]),
+                    "cfpq_set_start")
 
     def check_bounded_wait(self, limit_ns: int) -> bool:
         """Run the kernels' bounded mbarrier wait on a barrier nothing

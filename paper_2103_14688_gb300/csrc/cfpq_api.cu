@@ -144,6 +144,11 @@ int ensure_query(cfpq_ctx *ctx, bool restricted = false) {
     q.gather_slices = ctx->opt.gather_slices;
     if (q.restricted != restricted) ctx->exec_dirty = true;  // the work items carry the row masks
     q.restricted = restricted;
+    const bool seeded = ctx->has_start;
+    if (seeded && (ctx->start_B != q.rsm.B || ctx->start_n != ctx->graph.n))
+        return fail(ctx, CFPQ_ERR_INVALID_ARG, "the start answer does not match the graph and RSM");
+    if (q.seeded != seeded) ctx->exec_dirty = true;  // the prologue captured in the loop's graph changes
+    q.seeded = seeded;
     if (!q.prepared || q.graph_generation != ctx->graph.generation || ctx->exec_dirty) {
         std::string e;
         int rc = q.prepare(&ctx->A, &e);
@@ -154,7 +159,7 @@ int ensure_query(cfpq_ctx *ctx, bool restricted = false) {
         rc = ctx->exec.assemble(&ctx->A, ctx->stream, &e);
         if (rc) return fail(ctx, rc, e);
         q.small_ok = false;
-        if (!ctx->opt.no_single_cta && !restricted) {
+        if (!ctx->opt.no_single_cta && !restricted && !seeded) {
             rc = q.prepare_small(&ctx->A, ctx->stream, ctx->opt.max_iterations, kDefaultPassCap, &e);
             if (rc) return fail(ctx, rc, e);
         }
@@ -297,6 +302,17 @@ int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats) {
     const auto t0 = std::chrono::steady_clock::now();
     if (int rc = set_device(ctx)) return rc;
     if (int rc = ensure_query(ctx)) return rc;
+    if (ctx->has_start) {
+        // the start answer, in the device's row layout (padding words zero)
+        QueryDev &q = ctx->query;
+        std::string e;
+        const size_t wn = (q.n + 63) / 64, bytes = (size_t)q.B * q.n * q.W * 8;
+        if (!q.seed_mem.ensure(&ctx->A, bytes, &e)) return fail(ctx, CFPQ_ERR_OUT_OF_MEMORY, e);
+        CK(ctx, cudaMemsetAsync(q.seed_mem.p, 0, bytes, ctx->stream));
+        CK(ctx, cudaMemcpy2DAsync(q.seed_mem.p, (size_t)q.W * 8, ctx->start_bits.data(), wn * 8, wn * 8,
+                                  (size_t)q.B * q.n, cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
     const auto t1 = std::chrono::steady_clock::now();
     std::vector<QCtl> ctls;
     uint32_t launches = 0, claunch = 0;
@@ -332,6 +348,8 @@ int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats) {
 int cfpq_run_sources(cfpq_ctx *ctx, const uint32_t *sources, uint32_t n_sources, cfpq_run_stats *stats) {
     if (!ctx || (n_sources && !sources)) return CFPQ_ERR_INVALID_ARG;
     API_TRY
+    if (ctx->has_start)
+        return fail(ctx, CFPQ_ERR_STATE, "a start answer is set (cfpq_set_start); clear it for multiple-source runs");
     if (!ctx->has_graph) return fail(ctx, CFPQ_ERR_STATE, "no graph loaded");
     if (!ctx->has_rsm) return fail(ctx, CFPQ_ERR_STATE, "no RSM loaded");
     for (uint32_t i = 0; i < n_sources; ++i)
@@ -365,6 +383,29 @@ int cfpq_run_sources(cfpq_ctx *ctx, const uint32_t *sources, uint32_t n_sources,
     }
     const int st = status_of(ctls[0]);
     if (st) return fail(ctx, st, "iteration, round or pass cap reached before the fixpoint");
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+int cfpq_set_start(cfpq_ctx *ctx, const uint64_t *bits, uint32_t n_boxes, uint32_t n_vertices) {
+    if (!ctx) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (!bits) {
+        ctx->has_start = false;
+        ctx->start_bits.clear();
+        ctx->start_bits.shrink_to_fit();
+        return CFPQ_OK;
+    }
+    if (n_boxes == 0 || n_vertices == 0) return fail(ctx, CFPQ_ERR_INVALID_ARG, "empty start answer");
+    const size_t wn = (n_vertices + 63) / 64;
+    ctx->start_bits.assign(bits, bits + (size_t)n_boxes * n_vertices * wn);
+    // bits past n_vertices in a row's last word are not pairs of the graph
+    if (n_vertices % 64)
+        for (size_t r = 0; r < (size_t)n_boxes * n_vertices; ++r)
+            ctx->start_bits[r * wn + wn - 1] &= (1ull << (n_vertices % 64)) - 1ull;
+    ctx->start_B = n_boxes;
+    ctx->start_n = n_vertices;
+    ctx->has_start = true;
     return CFPQ_OK;
     API_CATCH(ctx)
 }

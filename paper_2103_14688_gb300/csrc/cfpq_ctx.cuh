@@ -26,6 +26,11 @@ struct cfpq_ctx {
     bool exec_dirty = true;
     bool has_result = false;
     uint64_t result_gen = 0;  // bumped whenever the result changes or is dropped
+    // resume: M2 to start the next runs from (cfpq_set_start), host layout
+    // start_B x start_n rows of ceil(start_n / 64) words
+    std::vector<uint64_t> start_bits;
+    bool has_start = false;
+    uint32_t start_B = 0, start_n = 0;
     // batch
     std::vector<std::unique_ptr<GraphDev>> bgraphs;
     std::vector<std::unique_ptr<QueryDev>> bqueries;

@@ -444,6 +444,10 @@ int QueryDev::enqueue_init(cudaStream_t st, uint32_t max_iter, uint32_t max_roun
     ENG_CK(launch_ctl_reset(ctl_ptr_mem.as<QCtl *>(), 1, max_iter, max_rounds, max_passes, n_levels, cyclic_mask,
                             boxedge_mem.as<unsigned long long>(), B, n, boxit_mem.as<uint32_t>(), nt_read_mask, st));
     ENG_CK(launch_eps_init(eps_mem.p, n_eps, 152, st));
+    if (seeded)
+        ENG_CK(launch_seed_apply(seed_mem.as<uint64_t>(), m2_mem.as<uint64_t>(), a2_mem.as<uint64_t>(),
+                                 a2it_mem.as<uint32_t>(), boxit_mem.as<uint32_t>(), ctl(),
+                                 boxedge_mem.as<unsigned long long>(), n, W, B, st));
     return CFPQ_OK;
 }
 

@@ -55,6 +55,11 @@ cudaError_t launch_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, 
                              unsigned long long *box_edges, uint32_t n_boxes, uint32_t n,
                              const uint32_t *box_new_it, unsigned long long nt_read_mask, cudaStream_t st);
 cudaError_t launch_eps_init(const void *eds, uint32_t ned, uint32_t grid, cudaStream_t st);
+// Resume: OR seed (n_boxes x n rows of W words) into M2, A2 := M2 on the
+// rows it touches, those rows new in iteration 1.
+cudaError_t launch_seed_apply(const uint64_t *seed, uint64_t *m2, uint64_t *a2, uint32_t *a2_it, uint32_t *box_new_it,
+                              QCtl *ctl, unsigned long long *box_edges, uint32_t n, uint32_t W, uint32_t n_boxes,
+                              cudaStream_t st);
 size_t eps_desc_size();
 void fill_eps_desc(void *dst, uint64_t *m2, uint64_t *a2, uint32_t *a2_it, uint32_t *box_new_it, QCtl *ctl,
                    unsigned long long *box_edges, uint32_t n, uint32_t W);
@@ -179,6 +184,10 @@ struct QueryDev {
     // state s outside them.
     bool restricted = false;
     DBuf reach_mem, reach_f, reach_misc;
+    // Resume: a given M2 (B x n rows of W words) applied after the epsilon
+    // rows by every enqueue_init while `seeded`.
+    bool seeded = false;
+    DBuf seed_mem;
     uint64_t *reach_ptr(uint32_t s) const { return reach_mem.as<uint64_t>() + (size_t)s * W; }
     int compute_reach(Allocator *A, cudaStream_t st, const uint32_t *h_src, uint32_t ns, std::string *err);
     struct Src {
