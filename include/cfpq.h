@@ -270,7 +270,9 @@ int cfpq_get_closure_rows(cfpq_ctx *ctx, uint32_t n_rows, const uint32_t *row_st
  *   - n_pad^2 / 8 bytes per box that a nonterminal transition reads (its M2,
  *     transposed).
  * The host copies and the memo of subpath sets are kept between calls
- * until the result changes (a run, or a new graph or RSM).
+ * until the result changes (a run, or a new graph or RSM).  After
+ * cfpq_run_sources only the sources' rows are exact, so vs must be one of
+ * its sources (CFPQ_ERR_INVALID_ARG otherwise).
  * CFPQ_ERR_BUFFER_TOO_SMALL if edge_cap (in triples) was too small;
  * CFPQ_ERR_OUT_OF_MEMORY if the device buffers do not fit; CFPQ_ERR_UNSUPPORTED
  * if the enumeration exceeds its work cap (4e6 stored paths or 2^20 subpath

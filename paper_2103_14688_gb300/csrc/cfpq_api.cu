@@ -329,6 +329,7 @@ int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats) {
     }
     ctx->has_result = true;
     ++ctx->result_gen;
+    ctx->result_sources.clear();
     const auto t2 = std::chrono::steady_clock::now();
     const double ms = std::chrono::duration<double, std::milli>(t2 - t0).count();
     if (stats) {
@@ -372,6 +373,8 @@ int cfpq_run_sources(cfpq_ctx *ctx, const uint32_t *sources, uint32_t n_sources,
     if (int rc = run_executor(ctx, ctx->exec, &ctls, &launches, &ms_cl, &claunch)) return rc;
     ctx->has_result = true;
     ++ctx->result_gen;
+    ctx->result_sources.assign(ctx->graph.n, 0);
+    for (uint32_t i = 0; i < n_sources; ++i) ctx->result_sources[sources[i]] = 1;
     const auto t2 = std::chrono::steady_clock::now();
     if (stats) {
         fill_stats(stats, ctls[0], ctx->query, std::chrono::duration<double, std::milli>(t2 - t0).count());
@@ -608,6 +611,8 @@ extern "C" int cfpq_extract_paths(cfpq_ctx *ctx, uint32_t box, uint32_t vs, uint
     if (!ctx->has_result) return fail(ctx, CFPQ_ERR_NOT_READY, "no result");
     QueryDev &q = ctx->query;
     if (box >= q.B || vs >= q.n || vf >= q.n) return fail(ctx, CFPQ_ERR_INVALID_ARG, "box or vertex out of range");
+    if (!ctx->result_sources.empty() && !ctx->result_sources[vs])
+        return fail(ctx, CFPQ_ERR_INVALID_ARG, "vs was not a source of the last multiple-source run");
     if (int rc = set_device(ctx)) return rc;
     std::string e;
     // The host copies, the device tables and the memo of path sets stay valid

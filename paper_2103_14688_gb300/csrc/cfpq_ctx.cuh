@@ -26,6 +26,9 @@ struct cfpq_ctx {
     bool exec_dirty = true;
     bool has_result = false;
     uint64_t result_gen = 0;  // bumped whenever the result changes or is dropped
+    // after a multiple-source run: per vertex 1 if it was a source (only those
+    // rows of the result are exact); empty after a full run
+    std::vector<uint8_t> result_sources;
     // resume: M2 to start the next runs from (cfpq_set_start), host layout
     // start_B x start_n rows of ceil(start_n / 64) words
     std::vector<uint64_t> start_bits;

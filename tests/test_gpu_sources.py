@@ -77,3 +77,21 @@ def test_sources_cfpq_computes_everything(C):
     full = _ctx(C, g, r)
     full.run()
     assert (ctx.reachable_bits(0) == full.reachable_bits(0)).all()
+
+
+def test_paths_after_a_multiple_source_run(C):
+    """After cfpq_run_sources only the sources' rows are exact: paths from a
+    source equal Oracle C's, from another vertex the call is refused until a
+    full run."""
+    g, r = W.rpq_abc(n=24, out_deg=4, seed=3)
+    ctx = _ctx(C, g, r)
+    ctx.run_sources([3, 5])
+    for vf in range(0, g.n, 3):
+        got, _ = ctx.extract_paths(0, 3, vf, 6)
+        assert got == oracle.brute_paths(g, r, 0, 3, vf, 6), vf
+    with pytest.raises(C.CfpqError) as e:
+        ctx.extract_paths(0, 4, 6, 6)
+    assert e.value.status == C.CFPQ_ERR_INVALID_ARG
+    ctx.run()
+    got, _ = ctx.extract_paths(0, 4, 6, 6)
+    assert got == oracle.brute_paths(g, r, 0, 4, 6, 6)
