@@ -127,9 +127,10 @@ int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t 
     if (tc_error)
         return fail(ctx, CFPQ_ERR_TIMEOUT, "a tile-product kernel gave up (bounded wait on its MMAs or on a counter)");
     if (ctx->opt.loop_mode != CFPQ_LOOP_HOST && launches) {
+        // the graph's loop body holds kLoopUnroll passes
         uint32_t passes = 0;
         for (const auto &c : *ctls) passes = std::max(passes, c.passes);
-        *launches = passes * per_pass + 2;
+        *launches = (passes + kLoopUnroll - 1) / kLoopUnroll * kLoopUnroll * per_pass + 2;
     }
     CK(ctx, cudaGetLastError());
     return CFPQ_OK;

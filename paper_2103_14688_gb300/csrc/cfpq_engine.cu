@@ -813,6 +813,7 @@ int Executor::build_graph(cudaStream_t st, uint32_t max_iter, uint32_t max_round
     cudaGraph_t prologue = nullptr;
     ENG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int rc = enqueue_prologue(cs, max_iter, max_rounds, max_passes);
+    const uint32_t kPassesPerLoop = kLoopUnroll;
     cudaError_t ce = cudaStreamEndCapture(cs, &prologue);
     if (rc || ce != cudaSuccess) {
         if (prologue) cudaGraphDestroy(prologue);
@@ -837,7 +838,9 @@ int Executor::build_graph(cudaStream_t st, uint32_t max_iter, uint32_t max_round
     ENG_CK(cudaGraphAddNode(&loop_node, graph, &pro_node, nullptr, 1, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     ENG_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    rc = enqueue_pass(cs, handle, 1, nullptr);
+    // kPassesPerLoop passes per evaluation of the while node: a pass after the
+    // loop finished finds no live work and leaves the control state unchanged
+    for (uint32_t p = 0; p < kPassesPerLoop && rc == 0; ++p) rc = enqueue_pass(cs, handle, 1, nullptr);
     cudaGraph_t body_out = body;
     ce = cudaStreamEndCapture(cs, &body_out);
     if (rc || ce != cudaSuccess) {

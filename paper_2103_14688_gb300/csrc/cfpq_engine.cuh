@@ -239,6 +239,9 @@ struct QueryDev {
     uint64_t *a2_ptr(uint32_t b) const { return a2_mem.as<uint64_t>() + (size_t)b * n * W; }
 };
 
+// Closure passes per iteration of the CUDA graph's while node.
+constexpr uint32_t kLoopUnroll = 2;
+
 // Runs the fixpoint of a set of queries with shared launches.
 struct Executor {
     std::vector<QueryDev *> qs;
