@@ -149,3 +149,24 @@ extern "C" int phd_paths(uint32_t n, uint64_t m, const uint32_t *tri, uint32_t Q
     }
     return 0;
 }
+
+// The enumerator's table of word lengths: out[b * (L + 1) + j] = 1 iff box b
+// derives a word of j terminals (j <= L).
+extern "C" int phd_word_lengths(uint32_t Q, uint32_t B, const uint32_t *box_start, const uint32_t *state_box,
+                                const uint8_t *fin, uint32_t T, const uint32_t *tr_from, const uint32_t *tr_kind,
+                                const uint32_t *tr_sym, const uint32_t *tr_to, uint32_t L, uint8_t *out) {
+    Rsm r;
+    r.Q = Q;
+    r.B = B;
+    r.box_start.assign(box_start, box_start + B);
+    r.state_box.assign(state_box, state_box + Q);
+    r.final_.assign(fin, fin + Q);
+    for (uint32_t i = 0; i < T; ++i) r.tr.push_back({tr_from[i], tr_kind[i], tr_sym[i], tr_to[i]});
+    cfpq::PathEnum<Rsm> P;
+    P.r = &r;
+    P.Lmax = L;
+    P.word_lengths();
+    for (uint32_t b = 0; b < B; ++b)
+        for (uint32_t j = 0; j <= L; ++j) out[(size_t)b * (L + 1) + j] = P.words[b][j];
+    return 0;
+}

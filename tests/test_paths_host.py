@@ -103,3 +103,27 @@ def test_dyck_and_rpq(lib):
     _check(lib, g, r, [(0, int(rng.integers(0, g.n)), int(rng.integers(0, g.n)), 6) for _ in range(12)])
     g, r = W.rpq_abc(n=40, out_deg=3, seed=5)
     _check(lib, g, r, [(0, vs, vf, 5) for vs in range(0, 40, 7) for vf in range(0, 40, 5)])
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_word_lengths_against_brute_force(lib, seed):
+    """The lengths the enumerator lets a box spell are exactly those of the
+    words (over two terminals, up to length 7) that the RSM accepts."""
+    import itertools
+    g, r = W.small_random_instance(700 + seed, n=4, m=6, n_labels=2, max_states=12)
+    L = 7
+    u32 = lambda a: np.ascontiguousarray(np.asarray(a), dtype=np.uint32)
+    fin = np.ascontiguousarray(np.asarray(r.state_final), dtype=np.uint8)
+    out = np.zeros(r.n_boxes * (L + 1), dtype=np.uint8)
+    args = [u32(x) for x in (r.box_start, r.state_box)]
+    tr = [u32(x) for x in (r.tr_from, r.tr_kind, r.tr_sym, r.tr_to)]
+    rc = lib.phd_word_lengths(ctypes.c_uint32(r.n_states), ctypes.c_uint32(r.n_boxes), _p(args[0]), _p(args[1]),
+                              _p(fin), ctypes.c_uint32(r.n_trans), _p(tr[0]), _p(tr[1]), _p(tr[2]), _p(tr[3]),
+                              ctypes.c_uint32(L), _p(out))
+    assert rc == 0
+    got = out.reshape(r.n_boxes, L + 1).astype(bool)
+    for b in range(r.n_boxes):
+        for j in range(L + 1):
+            want = any(oracle.rsm_accepts(r, g.n_terminals, b, list(w))
+                       for w in itertools.product(range(g.n_terminals), repeat=j))
+            assert got[b, j] == want, (b, j)
