@@ -220,7 +220,8 @@ def rpq_abc(n: int = 8192, out_deg: int = 8, seed: Optional[int] = None) -> Tupl
 
 def zipf_kmax_for_mean(alpha: float = 2.1, mean: float = 3.0, limit: int = 100000) -> int:
     """Smallest truncation point k_max of Zipf(alpha) on {1..k_max} whose mean
-    is at least ``mean`` (2.1 and 3 give 191)."""
+    is at least ``mean`` (2.1 and 3 give 192: the mean is 2.9997 at 191 and
+    3.0017 at 192)."""
     k = np.arange(1, limit + 1, dtype=np.float64)
     w = k ** (-alpha)
     m = np.cumsum(w * k) / np.cumsum(w)
