@@ -150,6 +150,14 @@ int ensure_query(cfpq_ctx *ctx, bool restricted = false) {
         return fail(ctx, CFPQ_ERR_INVALID_ARG, "the start answer does not match the graph and RSM");
     if (q.seeded != seeded) ctx->exec_dirty = true;  // the prologue captured in the loop's graph changes
     q.seeded = seeded;
+    if (q.prepared && q.graph_generation == ctx->graph.generation && !ctx->exec_dirty) {
+        // Same plan and work lists: a graph of the same shape may have been
+        // loaded since, so rebuild what was derived from the old edges.
+        std::string e;
+        bool moved = false;
+        if (int rc = q.refresh_graph_caches(&ctx->A, ctx->stream, &e, &moved)) return fail(ctx, rc, e);
+        if (moved) ctx->exec_dirty = true;
+    }
     if (!q.prepared || q.graph_generation != ctx->graph.generation || ctx->exec_dirty) {
         std::string e;
         int rc = q.prepare(&ctx->A, &e);

@@ -157,6 +157,7 @@ int stage_graph(GraphDev *g, Allocator *A, cudaStream_t st, uint32_t n, uint32_t
         return CFPQ_ERR_INVALID_ARG;
     }
     if (realloc || g->n != n || g->n_term != n_term) g->generation += 1;
+    g->content += 1;
     g->n = n;
     g->n_pad = n_pad;
     g->W = W;
@@ -168,21 +169,20 @@ int stage_graph(GraphDev *g, Allocator *A, cudaStream_t st, uint32_t n, uint32_t
 }
 
 int GraphDev::ensure_nonempty(Allocator *A, cudaStream_t st, std::string *err) {
-    if (nonempty.p && nonempty_generation == generation) return CFPQ_OK;
+    if (nonempty.p && nonempty_content == content) return CFPQ_OK;
     if (!nonempty.ensure(A, std::max<size_t>((size_t)n_term * W * 8, 64), err)) return CFPQ_ERR_OUT_OF_MEMORY;
     ENG_CK(launch_nonempty_bits(csr_off.as<uint32_t>(), n, n_term, W, nonempty.as<uint64_t>(), st));
-    nonempty_generation = generation;
+    nonempty_content = content;
     return CFPQ_OK;
 }
 
 int GraphDev::ensure_term_bits(Allocator *A, cudaStream_t st, std::string *err) {
-    if (term_bits.p && term_bits_generation == generation && term_bits_m == m_unique) return CFPQ_OK;
+    if (term_bits.p && term_bits_content == content) return CFPQ_OK;
     const size_t rows = (size_t)n_term * n;
     if (!term_bits.ensure(A, rows * W * 8, err)) return CFPQ_ERR_OUT_OF_MEMORY;
     ENG_CK(cudaMemsetAsync(term_bits.p, 0, rows * W * 8, st));
     ENG_CK(launch_csr_to_bits(csr_off.as<uint32_t>(), csr_col.as<uint32_t>(), rows, W, term_bits.as<uint64_t>(), st));
-    term_bits_generation = generation;
-    term_bits_m = m_unique;
+    term_bits_content = content;
     return CFPQ_OK;
 }
 
@@ -379,6 +379,21 @@ int QueryDev::prepare(Allocator *A, std::string *err) {
     return CFPQ_OK;
 }
 
+int QueryDev::refresh_graph_caches(Allocator *A, cudaStream_t st, std::string *err, bool *moved) {
+    bool need_term_bits = false, need_nonempty = false;
+    for (const auto &sdesc : srcs) {
+        need_term_bits |= (sdesc.dense && sdesc.label_kind == 0);
+        need_nonempty |= sdesc.pure_rb != 0;
+    }
+    const void *p_ne = g->nonempty.p, *p_tb = g->term_bits.p;
+    if (need_nonempty)
+        if (int rc = g->ensure_nonempty(A, st, err)) return rc;
+    if (need_term_bits)
+        if (int rc = g->ensure_term_bits(A, st, err)) return rc;
+    *moved = (need_nonempty && g->nonempty.p != p_ne) || (need_term_bits && g->term_bits.p != p_tb);
+    return CFPQ_OK;
+}
+
 int QueryDev::prepare_small(Allocator *A, cudaStream_t st, uint32_t max_iter, uint32_t max_passes,
                             std::string *err) {
     small_ok = false;
@@ -495,19 +510,8 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
         GraphDev &g = *q.g;
         QCtl *cp = q.ctl();
         hp.push_back(cp);
-        bool need_term_bits = false, need_nonempty = false;
-        for (const auto &sdesc : q.srcs) {
-            need_term_bits |= (sdesc.dense && sdesc.label_kind == 0);
-            need_nonempty |= sdesc.pure_rb != 0;
-        }
-        if (need_nonempty) {
-            int rc = g.ensure_nonempty(A, st, err);
-            if (rc) return rc;
-        }
-        if (need_term_bits) {
-            int rc = g.ensure_term_bits(A, st, err);
-            if (rc) return rc;
-        }
+        bool moved = false;
+        if (int rc = q.refresh_graph_caches(A, st, err, &moved)) return rc;
         const uint32_t base = (uint32_t)hs.size();
         for (const auto &sd : q.srcs) {
             SrcDesc d;

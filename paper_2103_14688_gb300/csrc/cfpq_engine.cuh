@@ -151,19 +151,24 @@ struct GraphDev {
     size_t m_in = 0, m_unique = 0;
     DBuf csr_off;  // [n_term * n + 1]
     DBuf csr_col;  // [m_unique]
+    // Row bitmaps derived from the CSR, rebuilt when `content` moves on:
     DBuf term_bits;  // [n_term * n * W] bit rows of the terminal labels (tensor-core sources only)
-    uint64_t term_bits_generation = ~0ull;
-    size_t term_bits_m = 0;
+    uint64_t term_bits_content = ~0ull;
     int ensure_term_bits(Allocator *A, cudaStream_t st, std::string *err);
     DBuf nonempty;  // [n_term * W] bit y of label l: row (l, y) of the CSR has an edge (pure-terminal reads)
-    uint64_t nonempty_generation = ~0ull;
+    uint64_t nonempty_content = ~0ull;
     int ensure_nonempty(Allocator *A, cudaStream_t st, std::string *err);
     // staging scratch
     DBuf e_src, e_lbl, e_dst, cnt, off, col, ucnt, scan_tmp, label_map, err;
     std::vector<uint32_t> h_off;  // host copies on demand (paths)
     std::vector<uint32_t> h_col;
     bool host_valid = false;
+    // `generation` moves on when the shape of the staged graph changes (n,
+    // n_terminals, reallocated buffers): plans and work lists hold its
+    // pointers and sizes.  `content` moves on with every successful load,
+    // also a same-size one: everything derived from the edges is stale then.
     uint64_t generation = 0;
+    uint64_t content = 0;
 };
 
 // Device state and descriptors of one query (graph + RSM).
@@ -225,6 +230,10 @@ struct QueryDev {
     int plan(std::string *err);                    // blocks, sources, extraction lists (host only)
     uint64_t footprint() const;                    // device bytes prepare() will hold
     int prepare(Allocator *A, std::string *err);  // plan + buffers
+    // The row bitmaps this query's sources read (pure-terminal masks, terminal
+    // bit rows), rebuilt for the graph's current content; *moved is set when a
+    // buffer was reallocated (the work lists hold its address).
+    int refresh_graph_caches(Allocator *A, cudaStream_t st, std::string *err, bool *moved);
     // Reset this query's device state and loop control (start of its fixpoint).
     int enqueue_init(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes);
     // single-CTA path: eligible when rows are <= 512 bits and the state fits one SM

@@ -138,6 +138,7 @@ extern "C" int cfpq_load_graph_device_noalloc(cfpq_ctx *ctx, uint32_t n, uint32_
             return fail(CFPQ_ERR_INVALID_ARG, "an edge names a vertex >= n_vertices or a label >= n_terminals");
         }
         if (g.n != n || g.n_term != n_term) g.generation += 1;
+        g.content += 1;  // the row bitmaps derived from the old edges are stale
         g.n = n;
         g.n_pad = n_pad;
         g.W = W;
@@ -146,8 +147,8 @@ extern "C" int cfpq_load_graph_device_noalloc(cfpq_ctx *ctx, uint32_t n, uint32_
         g.m_unique = total;
         g.host_valid = false;
         ctx->has_graph = true;
-        if (ctx->has_rsm && ctx->query.rsm.max_terminal_plus1 > n_term)
-            return fail(CFPQ_ERR_INVALID_ARG, "the loaded RSM reads a terminal >= n_terminals");
+        // an RSM reading more terminals than this graph has is reported by
+        // cfpq_run, as after cfpq_load_graph_device
         return CFPQ_OK;
     } catch (...) {
         ctx->err = "unexpected exception";

@@ -69,3 +69,37 @@ def test_noalloc_staging_rejects_what_it_cannot_hold():
     rc = lib.cfpq_load_graph_device_noalloc(ctx.h, 65536, 16, int(s.numel()), ctypes.c_void_p(s.data_ptr()),
                                             ctypes.c_void_p(l.data_ptr()), ctypes.c_void_p(d.data_ptr()))
     assert rc == C.CFPQ_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("mode", [1, 2])  # bit-packed rows; tensor-core tiles (0/1 FP8)
+def test_noalloc_same_size_swap_context_free(mode):
+    """A same-size swap under context-free queries.  The a^n b^n and Dyck-4
+    RSMs read pure-terminal blocks (per-label bitmaps of rows with an edge)
+    and, with tiles, the terminal bit rows: both come from the edges, so the
+    run after an allocation-free swap must rebuild them for the new graph."""
+    import oracle
+    from paper_2103_14688_gb300 import cfpq as C
+    lib = C.load()
+    gs = sorted((W.dyck_zipf(2048, seed=s)[0] for s in (41, 42)), key=lambda g: -g.m)
+    for r in (W.anbn_rsm(), W.dyck_rsm()):
+        na = C.Context(closure_mode=mode, no_single_cta=1)
+        s0, l0, d0 = _dev(gs[0])
+        na.load_graph_device(gs[0].n, gs[0].n_terminals, s0, l0, d0)  # the larger edge list sizes the buffers
+        na.load_rsm(r)
+        na.run()
+        for g in (gs[1], gs[0]):  # swap in the other graph, then the first one back
+            s, l, d = _dev(g)
+            rc = lib.cfpq_load_graph_device_noalloc(na.h, g.n, g.n_terminals, int(s.numel()),
+                                                    ctypes.c_void_p(s.data_ptr()), ctypes.c_void_p(l.data_ptr()),
+                                                    ctypes.c_void_p(d.data_ptr()))
+            assert rc == C.CFPQ_OK, lib.cfpq_last_error(na.h)
+            na.run()
+            got = _answer(na, r)
+            ref = C.Context(closure_mode=mode, no_single_cta=1)
+            ref.load_graph(g)
+            ref.load_rsm(r)
+            ref.run()
+            assert (got == _answer(ref, r)).all()
+            ref.close()
+            assert (got == oracle.worklist(g, r)).all()
+        na.close()
