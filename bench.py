@@ -1,27 +1,39 @@
-"""Benchmark: index creation (Kronecker-product RPQ/CFPQ) on GB300.
+"""Benchmark: index creation (Kronecker-product CFPQ/RPQ) on GB300.
 
-A step is one complete index creation -- graph staging from a device-resident
-edge list, epsilon initialisation, and the fixpoint loop of Kronecker product,
-incremental closure and extraction -- for the regular query (ab)*c | a*b* on
-a random graph with n = 8192 vertices and 8 uniform out-edges per vertex
-(labels uniform over a, b, c).  ``value`` is queries per second over all
-ranks; ``e2e`` is the same metric through the public C ABI with host buffers
-(edge list copied in, the answer's bit matrix copied out, every step).
+The default line (default): Dyck-4 CFPQ on a Zipf graph, n = 65536 -- the
+largest of the five workloads, and the one whose closure has dense label
+matrices, so that it compares the closure forms.  A step is one complete
+index creation -- staging the edge list (device-resident), epsilon
+initialisation and the fixpoint loop of Kronecker product, incremental
+closure and extraction (Listing 1) -- with the default closure (AUTO:
+bit-packed rows, tensor-core tiles for a nonterminal once its matrix is
+dense).  ``value`` is queries per second over all ranks.  The same line
+carries:
+
+* ``closure_modes``: the bit-packed-only and tensor-core closures timed on
+  the same query, each answer compared bit for bit with AUTO's;
+* ``e2e``: the metric through the public C ABI with host buffers (edge list
+  in, the answer's bit matrix out, every step);
+* ``roofline`` (dominant kernel) and ``roofline_other``: the row gather
+  against measured HBM bandwidth and the tile products against the FP8
+  tensor peak, from CUDA events in a host-driven run of the same query;
+* ``cpu_baseline``: Oracle B (the worklist oracle) on the same recipe at
+  small n, extrapolated (the oracle cannot run this size in minutes).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun (N > 1) every rank runs its own query (independent queries,
 no collective on the data path) and rank 0 prints the line.
 
 The other workloads print their own line with ``--workload``:
-  cycles   two coprime cycles (126 vertices, S -> a S b | a b): latency,
-           microseconds per fixpoint iteration;
-  dyck     Dyck-4 on a Zipf graph (n = 65536 by default): closure Bool-GOPS,
-           bit-packed and tensor-core closure modes;
-  batched  512 (graph, RSM) queries in one batch vs one at a time;
-  served   resident 32768-vertex graph, Poisson arrivals, p50/p99 latency;
-  sources  multiple-source RPQ (1, 16, 256 sources) against the full run;
-  paths    all-path extraction (vs -> vf, at most L edges) after index
-           creation, against Oracle C on the same calls.
+  rpq        the regular query (ab)*c | a*b*, n = 8192, 8 out-edges;
+  cycles     two coprime cycles (126 vertices, S -> a S b | a b): latency,
+             microseconds per fixpoint iteration;
+  dyck_modes Dyck-4 at any n (--dyck-n), closure modes side by side;
+  batched    512 (graph, RSM) queries in one batch vs one at a time;
+  served     resident 32768-vertex graph, Poisson arrivals, p50/p99 latency;
+  sources    multiple-source RPQ (1, 16, 256 sources) against the full run;
+  paths      all-path extraction (vs -> vf, at most L edges) after index
+             creation, against Oracle C on the same calls.
 """
 from __future__ import annotations
 
@@ -45,6 +57,8 @@ from paper_2103_14688_gb300 import workloads as W  # noqa: E402
 METRIC = "CFPQ queries/s & closure Bool-GOPS, tensor-core/batched vs bit-packed, bit-exact"
 UNIT = "queries/s"
 WORKLOAD = "rpq_abc_n8192_deg8"
+FP8_PER_BF16 = 2.0  # nominal dense tensor rates: FP8 4.5 PFLOP/s vs bf16 2.25 PFLOP/s
+TILE_FLOP_PER_KSTAGE = 2.0 * 128 * 256 * 128  # one K stage of a 128 x 256 tile, 128 deep
 
 
 def _config(n, deg, flush):
@@ -53,12 +67,40 @@ def _config(n, deg, flush):
             "l2": flush, "step": "stage edge list (device) + full fixpoint"}
 
 
+def _dyck_config(n, flush):
+    return {"workload": f"dyck4_zipf_n{n}", "query": "S -> S S | o_i c_i | o_i S c_i (i = 1..4)",
+            "rsm_states": 11, "n": n, "out_degree": "Zipf(2.1) on 1..192, mean 3", "labels": 8,
+            "graph": "uniform targets, labels uniform over o1..o4, c1..c4, seeded PCG64",
+            "closure": "AUTO", "l2": flush, "step": "stage edge list (device) + full fixpoint"}
+
+
 def _peaks():
+    """Measured device peaks (MEASURED_PEAKS.json), else the fallback figures."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "kind": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "kind": "fallback"}
+
+
+def _host_info():
+    """Host cores and CPU model of the machine the CPU baseline runs on."""
+    model = None
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    try:
+        import platform
+        arch = platform.machine()
+    except Exception:
+        arch = None
+    return {"nproc": os.cpu_count(), "cpu_model": model, "arch": arch}
 
 
 class ClockSampler:
@@ -120,7 +162,7 @@ def _dist():
     return ws, rank, local
 
 
-def run_gpu(args):
+def run_rpq(args):
     import torch
     from paper_2103_14688_gb300 import cfpq
 
@@ -242,8 +284,9 @@ def run_gpu(args):
     per_launch_bytes = alg_bytes / launches
     per_launch_s = ps.ms_closure / 1000.0 / launches
     achieved = per_launch_bytes / per_launch_s / 1e9
-    peak, peak_kind = _peaks()
-    traffic = _traffic_from_profiles()
+    pk = _peaks()
+    peak, peak_kind = pk["hbm_gbs"], pk["kind"]
+    traffic = _traffic_from_profiles("k_gather_rpq_abc_n8192")
     staging_kernels = 10
     gpu_launches = args.steps * (stats.gpu_launches + staging_kernels)
 
@@ -290,7 +333,7 @@ def run_gpu(args):
         "wall_s": wall,
     }
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(g, r, args.cpu_sources)
+        line["cpu_baseline"] = cpu_baseline_rpq(g, r)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -299,17 +342,212 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def _traffic_from_profiles():
-    """dram read+write bytes per launch of the closure kernel from the committed
-    ncu summary, when it was taken on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "k_gather_rpq_abc_n8192.json")
+def _roofline_gather(st, peaks, n):
+    """Row gather: algorithmic bytes = every source row ORed read once, every
+    changed output row read and written once, over the gather launches' event
+    time, against the measured HBM copy bandwidth."""
+    alg = (st.row_ors + 2 * st.rows_changed) * st.row_bytes
+    launches = max(1, st.gather_launches)
+    sec = max(st.ms_gather, 1e-9) / 1e3
+    achieved = alg / sec / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": _traffic_from_profiles(f"k_gather_dyck4_n{n}"),
+            "kernel": "cfpq::k_gather (row gather)", "peak_source": f"{peaks['kind']} hbm_gbs (burst copy)",
+            "launches_timed": launches, "algorithmic_bytes_per_launch": alg / launches,
+            "ms_per_launch": st.ms_gather / launches,
+            "accounting": "(source rows ORed + 2 x output rows changed) x row bytes"}
+
+
+def _roofline_tiles(st, peaks, n):
+    """Tile products: dense 0/1 FP8 multiply-adds over the compacted inner
+    dimension (2 x 128 x 256 x 128 per K stage) over the product launches'
+    event time, against the FP8 peak (measured sustained bf16 x the nominal
+    FP8/bf16 ratio: the kernel runs inside a long step)."""
+    flop = st.tile_kstages * TILE_FLOP_PER_KSTAGE
+    launches = max(1, st.tile_launches)
+    sec = max(st.ms_tile_products, 1e-9) / 1e3
+    achieved = flop / sec / 1e12
+    peak = peaks["bf16_tflops_sustained"] * FP8_PER_BF16
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": _traffic_from_profiles(f"k_tc_product_tma_dyck4_n{n}"),
+            "kernel": "cfpq::k_tc_product_tma (tcgen05 kind::f8f6f4)",
+            "peak_source": f"{peaks['kind']} bf16_tflops_sustained x {FP8_PER_BF16} (nominal FP8/bf16)",
+            "launches_timed": launches, "flop_per_launch": flop / launches,
+            "ms_per_launch": st.ms_tile_products / launches,
+            "accounting": "tile K stages x 2 x 128 x 256 x 128 (inner dimension compacted to the dirty rows)"}
+
+
+def run_dyck(args):
+    """The default line: Dyck-4 CFPQ on the Zipf graph (n = 65536 by default)."""
+    import ctypes
+    import torch
+    from paper_2103_14688_gb300 import cfpq, shard
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n = args.dyck_n
+    # independent queries per rank (weak scaling; no collective on the data path)
+    g, r = W.dyck_zipf(n, seed=shard.rank_seed(W.SEED_BASE + 3, rank))
+    m, nt = g.m, g.n_terminals
+    d_src, d_lbl, d_dst = (torch.from_numpy(np.asarray(a).astype(np.int32)).to(dev) for a in (g.src, g.lbl, g.dst))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    ctx = cfpq.Context(device=local)  # AUTO closure, device-side loop
+    ctx.load_rsm(r)
+
+    def step_device():
+        ctx.load_graph_device(n, nt, d_src, d_lbl, d_dst)
+        return ctx.run()
+
+    for _ in range(args.warmup):
+        step_device()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, last = [], None
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = step_device()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = float(np.mean(times))
+    total_ms = shard.max_over_ranks(float(np.sum(times)), dist, dev)
+    value = ws * args.steps / (total_ms / 1000.0)
+    stats = last
+    words = ctx.reachable_words(0)
+    pairs = int(ctx.count_reachable(0))
+    cbits, m3bits = ctx.count_index()
+    Nq = r.n_states * n
+
+    # end to end through the ABI: pinned host edge list in, answer bits out
+    h = [torch.from_numpy(np.asarray(a).astype(np.int32)).pin_memory() for a in (g.src, g.lbl, g.dst)]
+    wn = (n + 63) // 64
+    out_bits = torch.empty(n * wn, dtype=torch.int64).pin_memory()
+    lib = ctx.lib
+    u32 = ctypes.POINTER(ctypes.c_uint32)
+
+    def step_e2e():
+        rc = lib.cfpq_load_graph(ctx.h, n, nt, m, *(ctypes.cast(a.data_ptr(), u32) for a in h))
+        assert rc == 0, rc
+        st = cfpq.cfpq_run_stats()
+        rc = lib.cfpq_run(ctx.h, ctypes.byref(st))
+        assert rc == 0, rc
+        rc = lib.cfpq_get_reachable_bits(ctx.h, 0, ctypes.c_void_p(out_bits.data_ptr()))
+        assert rc == 0, rc
+
+    e_steps = max(1, min(args.steps, args.e2e_steps))
+    step_e2e()
+    barrier()
+    e_times = []
+    for _ in range(e_steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step_e2e()
+        e_times.append((time.perf_counter() - t0) * 1000.0)
+    barrier()
+    e_total = shard.max_over_ranks(float(np.sum(e_times)), dist, dev)
+    e2e_value = ws * e_steps / (e_total / 1000.0)
+    e2e_equal = bool((out_bits.numpy().view(np.uint64).reshape(n, wn) == words).all())
+    ctx.close()
+
+    # the same query with the other closure forms, each compared bit for bit
+    modes = None
+    if not args.no_extras:
+        modes = {"auto_ms_per_query": step_ms, "auto_tile_products": stats.tile_mmas}
+        for name, mode in (("bitpacked", cfpq.CFPQ_CLOSURE_BITPACKED), ("tc_fp8", cfpq.CFPQ_CLOSURE_TC_FP8)):
+            mctx = cfpq.Context(device=local, closure_mode=mode)
+            mctx.load_rsm(r)
+            mctx.load_graph_device(n, nt, d_src, d_lbl, d_dst)
+            mctx.run()  # warm-up: buffers, plan, CUDA graph
+            flush.fill_(1)
+            _, ms = _ctx_time(mctx, stream, lambda: (mctx.load_graph_device(n, nt, d_src, d_lbl, d_dst), mctx.run()))
+            modes[f"{name}_ms_per_query"] = ms
+            modes[f"{name}_equals_auto"] = bool((mctx.reachable_words(0) == words).all())
+            mctx.close()
+        modes["auto_speedup_vs_bitpacked"] = modes["bitpacked_ms_per_query"] / step_ms
+
+    # rooflines: per-kernel CUDA events in a host-driven run of the same query
+    pctx = cfpq.Context(device=local, loop_mode=cfpq.CFPQ_LOOP_HOST, profile=1)
+    pctx.load_rsm(r)
+    pctx.load_graph_device(n, nt, d_src, d_lbl, d_dst)
+    pctx.run()
+    ps = pctx.run()
+    prof_equal = bool((pctx.reachable_words(0) == words).all())
+    pctx.close()
+    peaks = _peaks()
+    roof_g = _roofline_gather(ps, peaks, n)
+    roof_t = _roofline_tiles(ps, peaks, n) if ps.tile_launches else None
+    dominant, other = (roof_g, roof_t)
+    if roof_t is not None and ps.ms_tile_products > ps.ms_gather:
+        dominant, other = roof_t, roof_g
+    staging_kernels = 10
+    gpu_launches = args.steps * (stats.gpu_launches + staging_kernels)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": _dyck_config(n, f"inputs larger than L2: {stats.device_bytes / 1e9:.1f} GB of closure state "
+                                  f"per query (L2 129 MB), and a 256 MiB L2 flush before every timed step"),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 4 * m, "d2h_bytes_per_step": n * wn * 8,
+                "steps": e_steps, "matches_device_result": e2e_equal},
+        "roofline": dominant,
+        "roofline_other": other,
+        "closure_modes": modes,
+        "closure_time_split_ms": {"gather": ps.ms_gather, "tile_operands": ps.ms_tile_operands,
+                                  "tile_products": ps.ms_tile_products, "host_loop_result_equal": prof_equal},
+        "closure_bool_gops": stats.row_ors * stats.row_bytes * 8 / (step_ms / 1000.0) / 1e9,
+        "closure_bool_gops_paper_accounting": (cbits + m3bits) * Nq / (step_ms / 1000.0) / 1e9,
+        "tensor_tflops_issued": stats.tile_kstages * TILE_FLOP_PER_KSTAGE / (step_ms / 1000.0) / 1e12,
+        "index": {"closure_bits": cbits, "m3_bits": m3bits, "answer_pairs": pairs, "edges": m,
+                  "iterations": stats.iterations, "passes": stats.rounds, "blocks": stats.closure_blocks,
+                  "row_ors": stats.row_ors, "rows_changed": stats.rows_changed, "tile_products": stats.tile_mmas,
+                  "device_gb": stats.device_bytes / 1e9},
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline_dyck(n)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _traffic_from_profiles(name):
+    """DRAM read + write bytes per launch from the committed ncu summary
+    profiles/<name>.json, when it was taken on the current source of the
+    kernel's file; else None."""
+    p = os.path.join(ROOT, "profiles", f"{name}.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p))
         from paper_2103_14688_gb300 import build as B
         import hashlib
-        src = open(os.path.join(B.CSRC, "cfpq_kernels.cu"), "rb").read()
+        src = open(os.path.join(B.CSRC, d.get("source_file", "cfpq_kernels.cu")), "rb").read()
         if d.get("kernel_source_sha1") != hashlib.sha1(src).hexdigest():
             return None
         return d.get("dram_bytes_per_launch")
@@ -317,18 +555,48 @@ def _traffic_from_profiles():
         return None
 
 
-def cpu_baseline(g, r, n_sources):
-    """The oracle (worklist CFL-reachability, one thread) on a sample of source
-    vertices of the same query, scaled to queries/s."""
+def cpu_baseline_rpq(g, r):
+    """Oracle A (Listing 1 with the closure recomputed from scratch every
+    iteration) on the whole RPQ workload, its closure rows spread over every
+    host core with OpenMP."""
     import oracle
-    srcs = list(range(0, g.n, max(1, g.n // n_sources)))[:n_sources]
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
     t0 = time.perf_counter()
-    oracle.worklist(g, r, sources=srcs)
+    oracle.kron_fixpoint(g, r)
     dt = time.perf_counter() - t0
-    frac = len(srcs) / g.n
-    return {"value": frac / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"Oracle B (worklist) from {len(srcs)} of {g.n} source vertices, {dt:.2f} s; "
-                      f"value = sampled fraction / time"}
+    oracle.set_threads(1)
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"Oracle A on the whole query (n = {g.n}), closure rows over {cores} threads, {dt:.1f} s",
+            **_host_info()}
+
+
+def dyck_oracle_seconds(n_target, sizes=(2048, 4096)):
+    """Oracle B (worklist, one thread) on the Dyck-4 Zipf recipe at the given
+    sizes, and the time extrapolated to n_target by the power law through
+    the two largest: (seconds at n_target, per-size seconds, exponent)."""
+    import oracle
+    ts = {}
+    for n in sizes:
+        g, r = W.dyck_zipf(n)
+        t0 = time.perf_counter()
+        oracle.worklist_words(g, r)
+        ts[n] = time.perf_counter() - t0
+    a, b = sizes[-2], sizes[-1]
+    k = float(np.log(ts[b] / ts[a]) / np.log(b / a))
+    return ts[b] * (n_target / b) ** k, ts, k
+
+
+def cpu_baseline_dyck(n):
+    """The oracle on a bounded sample of the Dyck-4 workload: Oracle B cannot
+    be restricted to a few source rows of a context-free query (every box
+    call enters new vertices), so it runs the same recipe at n = 2048 and
+    4096 and its time is extrapolated to n."""
+    t, ts, k = dyck_oracle_seconds(n)
+    return {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"Oracle B on the same recipe at n = 2048 ({ts[2048]:.2f} s) and 4096 ({ts[4096]:.2f} s); "
+                      f"time extrapolated to n = {n} as n^{k:.2f}: {t:.0f} s per query",
+            **_host_info()}
 
 
 def _ctx_time(ctx, stream, fn):
@@ -369,7 +637,7 @@ def run_other(args):
                      "value": ms, "higher_is_better": False, "iterations": st.iterations,
                      "us_per_iteration": 1000.0 * ms / st.iterations, "passes": st.rounds,
                      "pairs": int(ans.sum()), "closed_form_pairs": 4032})
-    elif args.workload == "dyck":
+    elif args.workload == "dyck_modes":
         g, r = W.dyck_zipf(args.dyck_n)
         res = {}
         all_modes = {"auto": cfpq.CFPQ_CLOSURE_AUTO, "bitpacked": cfpq.CFPQ_CLOSURE_BITPACKED,
@@ -567,32 +835,49 @@ def run_other(args):
 
 
 def run_reference(args):
-    """The oracle as the reference arm: each step a bounded sample of the
-    workload (source vertices), on the host cores."""
+    """The oracle as the reference arm, on the host cores, for the same
+    workload, metric and unit as the GPU line.  Each step is a bounded sample:
+    for the Dyck-4 line, Oracle B on the same recipe at n = 2048 and 4096 with
+    its time extrapolated to the benchmark's n; for the RPQ line, Oracle B
+    from a random sample of source vertices (facts of different sources are
+    independent), scaled by the sampled fraction."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     import oracle
-    g, r = W.rpq_abc(n=args.n, out_deg=8)
-    n_s = args.cpu_sources
-    srcs_all = list(range(g.n))
-    rng = np.random.Generator(np.random.PCG64(1))
-    def one():
-        srcs = sorted(rng.choice(srcs_all, size=n_s, replace=False).tolist())
-        t0 = time.perf_counter()
-        oracle.worklist(g, r, sources=srcs)
-        return time.perf_counter() - t0
+    if args.workload == "rpq":
+        g, r = W.rpq_abc(n=args.n, out_deg=8)
+        n_s = args.cpu_sources
+        rng = np.random.Generator(np.random.PCG64(1))
+
+        def one():
+            srcs = sorted(rng.choice(g.n, size=n_s, replace=False).tolist())
+            t0 = time.perf_counter()
+            oracle.worklist(g, r, sources=srcs)
+            return (time.perf_counter() - t0) * g.n / n_s  # seconds per whole query
+
+        sample = f"Oracle B from {n_s} random source vertices per step of {g.n}, scaled by the sampled fraction"
+        config = _config(args.n, 8, "n/a (host)")
+    else:
+        n = args.dyck_n
+
+        def one():
+            return dyck_oracle_seconds(n)[0]
+
+        sample = (f"Oracle B on the Dyck-4 Zipf recipe at n = 2048 and 4096 per step, time extrapolated to "
+                  f"n = {n} by the power law through the two")
+        config = _dyck_config(n, "n/a (host)")
     for _ in range(args.warmup):
         one()
     ts = [one() for _ in range(args.steps)]
     total = float(np.sum(ts))
-    value = args.steps * (n_s / g.n) / total
+    value = args.steps / total
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": _config(args.n, 8, "n/a (host)"), "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"Oracle B from {n_s} random source vertices per step of {g.n}"},
+            "config": config, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             **_host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -600,27 +885,31 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--n", type=int, default=8192, help="rpq workload: vertices")
     ap.add_argument("--cpu-sources", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="rpq", choices=["rpq", "cycles", "dyck", "batched", "served", "sources", "paths"])
+    ap.add_argument("--workload", default="dyck",
+                    choices=["dyck", "rpq", "cycles", "dyck_modes", "batched", "served", "sources", "paths"])
     ap.add_argument("--dyck-n", type=int, default=65536)
+    ap.add_argument("--e2e-steps", type=int, default=5, help="end-to-end steps (at most --steps)")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--lambdas", default="10,30,100,300,1000")
     ap.add_argument("--horizon", type=float, default=5.0)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--loop", default="device", choices=["device", "host"],
-                    help="dyck workload: fixpoint loop in a CUDA graph (device) or one launch per pass (host)")
+                    help="dyck_modes workload: fixpoint loop in a CUDA graph (device) or one launch per pass (host)")
     ap.add_argument("--modes", default="auto,bitpacked,tc_fp8",
-                    help="dyck workload: closure modes to run (the first is the line's value)")
+                    help="dyck_modes workload: closure modes to run (the first is the line's value)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "dyck":
+        run_dyck(args)
     elif args.workload == "rpq":
-        run_gpu(args)
+        run_rpq(args)
     else:
         run_other(args)
 

@@ -143,6 +143,13 @@ typedef struct {
     uint32_t pad_;
     uint64_t tile_kstages;     /* K stages of 128 multiplied by the tile products; each stage is
                                   128 x 256 x 128 tensor-core multiply-adds */
+    /* profile = 1: the closure time of ms_closure split by kernel, from CUDA
+     * events on the context's stream around each group of launches of a pass */
+    double ms_gather;          /* row-gather launches (k_gather, every row-width class) */
+    double ms_tile_operands;   /* tile jobs' dirty-row lists and 0/1 FP8 operand expansion */
+    double ms_tile_products;   /* tcgen05 tile-product launches */
+    uint32_t gather_launches;  /* row-gather launches timed */
+    uint32_t tile_launches;    /* passes whose tile-product launches were timed */
 } cfpq_run_stats;
 
 /* ---- context ---------------------------------------------------------------- */

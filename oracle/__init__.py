@@ -35,9 +35,18 @@ def build() -> str:
     so = os.path.join(_BUILD, f"libcfpq_oracle_{digest}.so")
     if not os.path.exists(so):
         tmp = so + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC]
+        # OpenMP only spreads Oracle A's closure rows over threads when asked
+        # (set_threads); without it the pragmas are ignored
+        if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, so)
     return so
+
+
+def set_threads(k: int) -> None:
+    """Threads for the rows of Oracle A's closure (1 = sequential, the default)."""
+    _load().orc_set_threads(ctypes.c_int(int(k)))
 
 
 def _load():
@@ -241,6 +250,25 @@ def closure_rows(g, r, m2_nt: np.ndarray, rows: Sequence[Tuple[int, int]]) -> np
     pad[:, :n] = m2
     words = np.packbits(pad, axis=1, bitorder="little").view(np.uint64).reshape(-1)
     words = np.ascontiguousarray(words)
+    rs = _u32([a for a, _ in rows])
+    rv = _u32([b for _, b in rows])
+    out = np.zeros(len(rows) * wN, dtype=np.uint64)
+    rc = lib.orc_closure_rows(*k.graph(g), *k.rsm(r), _p(words), ctypes.c_uint32(len(rows)), _p(rs), _p(rv),
+                              _p(out))
+    _check(rc, "orc_closure_rows")
+    return _unpack(out, len(rows), N)
+
+
+def closure_rows_words(g, r, m2_words: np.ndarray, rows: Sequence[Tuple[int, int]]) -> np.ndarray:
+    """``closure_rows`` with the nonterminal matrices given as bit rows,
+    uint64 [B, n, ceil(n/64)] (bit y of row x = word y/64, bit y%64): the
+    form a large answer is read in.  Result bool [len(rows), Q*n]."""
+    lib = _load()
+    k = _Keep(g, r)
+    n, Q, B = g.n, r.n_states, r.n_boxes
+    N = Q * n
+    wn, wN = _wn(n), _wn(N)
+    words = np.ascontiguousarray(np.asarray(m2_words, dtype=np.uint64).reshape(B * n * wn))
     rs = _u32([a for a, _ in rows])
     rv = _u32([b for _, b in rows])
     out = np.zeros(len(rows) * wN, dtype=np.uint64)

@@ -85,28 +85,47 @@ static inline uint32_t label_of(const orc_rsm *r, uint32_t n_term, uint32_t t) {
 /* Transitive closure of a Boolean matrix given as adjacency lists:          */
 /* C[u] = set of vertices reachable from u by a path of one or more edges.   */
 /* ------------------------------------------------------------------------ */
+/* Threads of closure_from_lists (rows are independent).  1 = the plain
+ * sequential loop; the CPU baseline of the benchmark may raise it.  The
+ * result does not depend on it. */
+static int orc_threads = 1;
+int orc_set_threads(int k) {
+    orc_threads = k < 1 ? 1 : k;
+    return 0;
+}
+
 static int closure_from_lists(uint64_t N, const uint64_t *off, const uint32_t *adj, uint64_t *C) {
     uint64_t wN = words_for(N);
-    uint32_t *stack = (uint32_t *)malloc(sizeof(uint32_t) * (N + 1));
-    if (!stack) return -3;
+    int failed = 0;
     memset(C, 0, sizeof(uint64_t) * N * wN);
-    for (uint64_t u = 0; u < N; ++u) {
-        uint64_t *row = C + u * wN;
-        uint64_t sp = 0;
-        for (uint64_t e = off[u]; e < off[u + 1]; ++e) {
-            uint32_t v = adj[e];
-            if (!bget(row, v)) { bset(row, v); stack[sp++] = v; }
+#pragma omp parallel num_threads(orc_threads)
+    {
+        uint32_t *stack = (uint32_t *)malloc(sizeof(uint32_t) * (N + 1));
+        if (!stack) {
+#pragma omp atomic write
+            failed = 1;
         }
-        while (sp) {
-            uint32_t w = stack[--sp];
-            for (uint64_t e = off[w]; e < off[w + 1]; ++e) {
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t uu = 0; uu < (int64_t)N; ++uu) {
+            if (!stack) continue;
+            uint64_t u = (uint64_t)uu;
+            uint64_t *row = C + u * wN;
+            uint64_t sp = 0;
+            for (uint64_t e = off[u]; e < off[u + 1]; ++e) {
                 uint32_t v = adj[e];
                 if (!bget(row, v)) { bset(row, v); stack[sp++] = v; }
             }
+            while (sp) {
+                uint32_t w = stack[--sp];
+                for (uint64_t e = off[w]; e < off[w + 1]; ++e) {
+                    uint32_t v = adj[e];
+                    if (!bget(row, v)) { bset(row, v); stack[sp++] = v; }
+                }
+            }
         }
+        free(stack);
     }
-    free(stack);
-    return 0;
+    return failed ? -3 : 0;
 }
 
 /* Row-major dense N x N bit matrix -> adjacency lists. */

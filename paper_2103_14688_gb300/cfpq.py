@@ -63,7 +63,8 @@ class cfpq_run_stats(Structure):
                 ("device_bytes", c_uint64), ("ms_total", c_double), ("ms_closure", c_double),
                 ("ms_setup", c_double), ("ms_loop", c_double),
                 ("closure_launches", c_uint32), ("pad_", c_uint32),
-                ("tile_kstages", c_uint64)]
+                ("tile_kstages", c_uint64), ("ms_gather", c_double), ("ms_tile_operands", c_double),
+                ("ms_tile_products", c_double), ("gather_launches", c_uint32), ("tile_launches", c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -463,13 +464,18 @@ class Server:
             raise CfpqError(rc, "cfpq_poll: " + status_string(rc))
         return bool(d.value)
 
-    def result_bits(self, ticket: int, box: int = 0) -> np.ndarray:
+    def result_words(self, ticket: int, box: int = 0) -> np.ndarray:
+        """M2^box of a finished query as bit rows, uint64 [n, ceil(n/64)]."""
         wn = (self.n + 63) // 64
         out = np.zeros(self.n * wn, dtype=np.uint64)
         rc = self.lib.cfpq_result_reachable_bits(self.h, ticket, box, c_void_p(out.ctypes.data))
         if rc != CFPQ_OK:
             raise CfpqError(rc, "cfpq_result_reachable_bits: " + status_string(rc))
-        return np.unpackbits(out.reshape(self.n, wn).view(np.uint8), axis=1, bitorder="little")[:, : self.n].astype(bool)
+        return out.reshape(self.n, wn)
+
+    def result_bits(self, ticket: int, box: int = 0) -> np.ndarray:
+        w = self.result_words(ticket, box)
+        return np.unpackbits(w.view(np.uint8), axis=1, bitorder="little")[:, : self.n].astype(bool)
 
     def release(self, ticket: int):
         rc = self.lib.cfpq_release(self.h, ticket)

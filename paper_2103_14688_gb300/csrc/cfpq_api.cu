@@ -68,11 +68,27 @@ void fill_stats(cfpq_run_stats *s, const QCtl &c, const QueryDev &q, double ms) 
     s->ms_total = ms;
 }
 
+// Per-kernel closure time of a profiled (host-loop) run.
+struct ClosureProfile {
+    double ms_closure = 0.0, ms_gather = 0.0, ms_operands = 0.0, ms_products = 0.0;
+    uint32_t closure_launches = 0, gather_launches = 0, tile_launches = 0;
+};
+
+void put_profile(cfpq_run_stats *s, const ClosureProfile &p) {
+    s->ms_closure = p.ms_closure;
+    s->closure_launches = p.closure_launches;
+    s->ms_gather = p.ms_gather;
+    s->ms_tile_operands = p.ms_operands;
+    s->ms_tile_products = p.ms_products;
+    s->gather_launches = p.gather_launches;
+    s->tile_launches = p.tile_launches;
+}
+
 int status_of(const QCtl &c) { return c.status == kStatusOk ? CFPQ_OK : CFPQ_ERR_TIMEOUT; }
 
 // Run the executor's queries to their fixpoint.
 int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t *launches,
-                 double *ms_closure = nullptr, uint32_t *closure_launches = nullptr) {
+                 ClosureProfile *prof_out = nullptr) {
     const cudaStream_t st = ctx->stream;
     const uint32_t mi = ctx->opt.max_iterations, mr = ctx->opt.max_rounds, mp = pass_cap(ctx->opt);
     uint32_t n_gather = 0, n_extract = 0;
@@ -87,32 +103,39 @@ int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t 
         int running = 1;
         uint32_t passes = 0;
         const bool prof = ctx->opt.profile != 0;
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (prof) {
-            CK(ctx, cudaEventCreate(&e0));
-            CK(ctx, cudaEventCreate(&e1));
-        }
-        double tot = 0.0;
+        cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+        auto drop_events = [&]() {
+            for (auto &e : ev)
+                if (e) cudaEventDestroy(e);
+        };
+        if (prof)
+            for (auto &e : ev) CK(ctx, cudaEventCreate(&e));
+        ClosureProfile P;
         while (running) {
-            if (ex.enqueue_pass(st, 0, 0, ex.running.as<int>(), e0, e1)) {
-                if (e0) cudaEventDestroy(e0);
-                if (e1) cudaEventDestroy(e1);
+            if (ex.enqueue_pass(st, 0, 0, ex.running.as<int>(), prof ? ev : nullptr)) {
+                drop_events();
                 return fail(ctx, CFPQ_ERR_CUDA, "pass launch failed");
             }
             CK(ctx, cudaMemcpyAsync(&running, ex.running.p, sizeof(int), cudaMemcpyDeviceToHost, st));
             CK(ctx, cudaStreamSynchronize(st));
             if (prof) {
-                float ms = 0.f;
-                CK(ctx, cudaEventElapsedTime(&ms, e0, e1));
-                tot += ms;
+                float a = 0.f, b = 0.f, c = 0.f;
+                CK(ctx, cudaEventElapsedTime(&a, ev[0], ev[1]));
+                CK(ctx, cudaEventElapsedTime(&b, ev[1], ev[2]));
+                CK(ctx, cudaEventElapsedTime(&c, ev[2], ev[3]));
+                P.ms_gather += a;
+                P.ms_operands += b;
+                P.ms_products += c;
             }
             ++passes;
         }
         if (prof) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            if (ms_closure) *ms_closure = tot;
-            if (closure_launches) *closure_launches = passes * n_gather;
+            drop_events();
+            P.ms_closure = P.ms_gather + P.ms_operands + P.ms_products;
+            P.closure_launches = passes * n_gather;
+            P.gather_launches = passes * n_gather;
+            P.tile_launches = ex.n_tcjobs ? passes : 0;
+            if (prof_out) *prof_out = P;
         }
         if (launches) *launches = passes * per_pass + 2;
     } else {
@@ -324,8 +347,8 @@ int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats) {
     }
     const auto t1 = std::chrono::steady_clock::now();
     std::vector<QCtl> ctls;
-    uint32_t launches = 0, claunch = 0;
-    double ms_cl = 0.0;
+    uint32_t launches = 0;
+    ClosureProfile prof;
     if (ctx->query.small_ok && ctx->opt.loop_mode == CFPQ_LOOP_DEVICE) {
         // the whole fixpoint in one CTA (state in shared memory)
         CK(ctx, launch_small_fixpoint(ctx->query.small_desc.p, 1, ctx->query.small_smem, ctx->stream));
@@ -333,7 +356,7 @@ int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats) {
         CK(ctx, cudaMemcpyAsync(ctls.data(), ctx->query.ctl(), sizeof(QCtl), cudaMemcpyDeviceToHost, ctx->stream));
         CK(ctx, cudaStreamSynchronize(ctx->stream));
         launches = 1;
-    } else if (int rc = run_executor(ctx, ctx->exec, &ctls, &launches, &ms_cl, &claunch)) {
+    } else if (int rc = run_executor(ctx, ctx->exec, &ctls, &launches, &prof)) {
         return rc;
     }
     ctx->has_result = true;
@@ -344,8 +367,7 @@ int cfpq_run(cfpq_ctx *ctx, cfpq_run_stats *stats) {
     if (stats) {
         fill_stats(stats, ctls[0], ctx->query, ms);
         stats->gpu_launches = launches;
-        stats->ms_closure = ms_cl;
-        stats->closure_launches = claunch;
+        put_profile(stats, prof);
         stats->ms_setup = std::chrono::duration<double, std::milli>(t1 - t0).count();
         stats->ms_loop = std::chrono::duration<double, std::milli>(t2 - t1).count();
     }
@@ -377,9 +399,9 @@ int cfpq_run_sources(cfpq_ctx *ctx, const uint32_t *sources, uint32_t n_sources,
     }
     const auto t1 = std::chrono::steady_clock::now();
     std::vector<QCtl> ctls;
-    uint32_t launches = 0, claunch = 0;
-    double ms_cl = 0.0;
-    if (int rc = run_executor(ctx, ctx->exec, &ctls, &launches, &ms_cl, &claunch)) return rc;
+    uint32_t launches = 0;
+    ClosureProfile prof;
+    if (int rc = run_executor(ctx, ctx->exec, &ctls, &launches, &prof)) return rc;
     ctx->has_result = true;
     ++ctx->result_gen;
     ctx->result_sources.assign(ctx->graph.n, 0);
@@ -388,8 +410,7 @@ int cfpq_run_sources(cfpq_ctx *ctx, const uint32_t *sources, uint32_t n_sources,
     if (stats) {
         fill_stats(stats, ctls[0], ctx->query, std::chrono::duration<double, std::milli>(t2 - t0).count());
         stats->gpu_launches = launches;
-        stats->ms_closure = ms_cl;
-        stats->closure_launches = claunch;
+        put_profile(stats, prof);
         stats->ms_setup = std::chrono::duration<double, std::milli>(t1 - t0).count();
         stats->ms_loop = std::chrono::duration<double, std::milli>(t2 - t1).count();
     }

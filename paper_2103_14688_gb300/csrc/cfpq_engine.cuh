@@ -277,8 +277,10 @@ struct Executor {
     int assemble(Allocator *A, cudaStream_t st, std::string *err);
     int enqueue_prologue(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes);
     int enqueue_lists(cudaStream_t st);  // recompute the live lists without advancing any query
+    // ev (profiling, may be null): four events recorded before the row
+    // gathers, after them, after the tile operands and after the tile products.
     int enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int use_handle, int *running_out,
-                     cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);
+                     const cudaEvent_t *ev = nullptr);
     int build_graph(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes, std::string *err);
     int read_ctls(cudaStream_t st, std::vector<QCtl> *out, int *tc_error = nullptr);
 };

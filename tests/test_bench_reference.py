@@ -8,10 +8,9 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_reference_arm_prints_the_contract_line():
+def _line(*extra):
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0", "--cpu-sources", "16"], cwd=ROOT, capture_output=True, text=True,
-                         timeout=600)
+                          "--warmup", "0", *extra], cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -20,7 +19,19 @@ def test_reference_arm_prints_the_contract_line():
               "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
-    assert d["config"]["workload"] == "rpq_abc_n8192_deg8"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["nproc"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"]
+    return d
+
+
+def test_reference_arm_prints_the_contract_line():
+    """The default line: the Dyck-4 workload at n = 65536."""
+    d = _line()
+    assert d["config"]["workload"] == "dyck4_zipf_n65536"
+
+
+def test_reference_arm_rpq_line():
+    d = _line("--workload", "rpq", "--cpu-sources", "16")
+    assert d["config"]["workload"] == "rpq_abc_n8192_deg8"

@@ -340,3 +340,45 @@ def test_rejects_bad_input():
     bad = W.Graph(2, 2, np.array([0], np.uint32), np.array([0], np.uint32), np.array([2], np.uint32))
     with pytest.raises(oracle.OracleError):
         oracle.worklist(bad, r)
+
+
+def _fixpoint_row(g, r, words, x):
+    q0 = int(r.box_start[r.start_box])
+    crow = oracle.closure_rows_words(g, r, words.reshape(1, g.n, -1), [(q0, x)])[0]
+    row = np.zeros(g.n, dtype=bool)
+    for f in range(r.n_states):
+        if r.state_final[f] and r.state_box[f] == r.start_box:
+            row |= crow[f * g.n:(f + 1) * g.n]
+    return row
+
+
+def test_fixpoint_row_check_accepts_the_answer_and_catches_dropped_pairs():
+    """The full-size check of the GPU answer (one more iteration of Listing 1
+    at a row, from a given M2) holds on Oracle B's answer and fails when
+    pairs derivable from the rest are dropped (a mistake planted on the CPU),
+    and closure_rows_words agrees with closure_rows."""
+    g, r = W.dyck_zipf(512, seed=3)
+    words = oracle.worklist_words(g, r)[0].copy()
+    bits = oracle.worklist(g, r)
+    rng = np.random.default_rng(0)
+    xs = [int(x) for x in rng.integers(0, g.n, 12)]
+    caught = 0
+    for x in xs:
+        row = np.unpackbits(words[x].view(np.uint8), bitorder="little")[: g.n].astype(bool)
+        assert (_fixpoint_row(g, r, words, x) == row).all()
+        ys = np.flatnonzero(row)
+        if len(ys) < 4:
+            continue
+        # drop a quarter of the row's pairs; a dropped pair that another
+        # derivation still yields from the remaining M2 shows up again
+        drop = rng.choice(ys, size=len(ys) // 4, replace=False)
+        bad = words.copy()
+        for y in drop:
+            bad[x, y >> 6] &= ~np.uint64(1 << (int(y) & 63))
+        bad_row = np.unpackbits(bad[x].view(np.uint8), bitorder="little")[: g.n].astype(bool)
+        caught += int((_fixpoint_row(g, r, bad, x) != bad_row).any())
+    assert caught >= 1
+    q0 = int(r.box_start[0])
+    rows = [(q0, x) for x in xs[:3]] + [(1, xs[0])]
+    assert (oracle.closure_rows_words(g, r, words.reshape(1, g.n, -1), rows) ==
+            oracle.closure_rows(g, r, bits, rows)).all()
