@@ -585,8 +585,11 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                     *err = "gather items: rows per item must be a multiple of 64 and at most 1024";
                     return CFPQ_ERR_INVALID_ARG;
                 }
-                for (uint32_t r0 = 0; r0 < q.n; r0 += rows_item)
-                for (uint32_t sl = 0; sl < n_slices; ++sl) {
+                // slice-major: CTAs running side by side enumerate the same
+                // columns of the adjacency, so the closure rows they read (a
+                // 1/n_slices share of the block read) stay in L2
+                for (uint32_t sl = 0; sl < n_slices; ++sl)
+                for (uint32_t r0 = 0; r0 < q.n; r0 += rows_item) {
                     GItem it;
                     it.out = q.blk_ptr((uint32_t)b);
                     it.out_stamp = q.stamp_ptr((uint32_t)b);
@@ -779,18 +782,20 @@ int Executor::enqueue_lists(cudaStream_t st) {
 }
 
 int Executor::enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int use_handle, int *running_out,
-                           cudaEvent_t ev_before, cudaEvent_t ev_after) {
+                           const cudaEvent_t *ev) {
     std::string *err = nullptr;
-    if (ev_before) ENG_CK(cudaEventRecord(ev_before, st));
+    if (ev) ENG_CK(cudaEventRecord(ev[0], st));
     for (int c = 0; c < kClasses; ++c)
         ENG_CK(launch_gather(kVplOf[c / 2], (c & 1) != 0, items[c].as<GItem>(), max_live[c], srcs.as<SrcDesc>(), T, c,
                              st));
+    if (ev) ENG_CK(cudaEventRecord(ev[1], st));
+    if (n_tcjobs) ENG_CK(launch_tc_compact(tcjobs.as<TcJob>(), T, max_tc_w, tc_err.as<int>(), st));
+    if (ev) ENG_CK(cudaEventRecord(ev[2], st));
     if (n_tcjobs) {
-        ENG_CK(launch_tc_compact(tcjobs.as<TcJob>(), T, max_tc_w, tc_err.as<int>(), st));
         ENG_CK(launch_tc_product(false, tcjobs.as<TcJob>(), max_tc_tiles, T, tc_err.as<int>(), st));
         ENG_CK(launch_tc_product_tma(tcjobs.as<TcJob>(), tcmaps.p, max_tc_tiles, T, tc_err.as<int>(), st));
     }
-    if (ev_after) ENG_CK(cudaEventRecord(ev_after, st));
+    if (ev) ENG_CK(cudaEventRecord(ev[3], st));
     // the last extraction launch of the pass also runs the loop control
     int last_x = -1;
     for (int c = 0; c < kClasses; c += 2)
