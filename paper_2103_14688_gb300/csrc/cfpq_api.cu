@@ -96,8 +96,8 @@ int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t 
         n_gather += ex.n_items[v] ? 1 : 0;
         n_extract += ex.n_xitems[v] ? 1 : 0;
     }
-    // tile products: row list, column gather, product
-    const uint32_t per_pass = n_gather + n_extract + (ex.n_tcjobs ? 3 : 0) + (n_extract ? 0 : 1);
+    // tile jobs: new-edge columns, row list, A and B operands, the two product kernels
+    const uint32_t per_pass = n_gather + n_extract + (ex.n_tcjobs ? 6 : 0) + (n_extract ? 0 : 1);
     if (ctx->opt.loop_mode == CFPQ_LOOP_HOST) {
         if (ex.enqueue_prologue(st, mi, mr, mp)) return fail(ctx, CFPQ_ERR_CUDA, "prologue launch failed");
         int running = 1;
@@ -123,8 +123,8 @@ int run_executor(cfpq_ctx *ctx, Executor &ex, std::vector<QCtl> *ctls, uint32_t 
                 CK(ctx, cudaEventElapsedTime(&a, ev[0], ev[1]));
                 CK(ctx, cudaEventElapsedTime(&b, ev[1], ev[2]));
                 CK(ctx, cudaEventElapsedTime(&c, ev[2], ev[3]));
-                P.ms_gather += a;
-                P.ms_operands += b;
+                P.ms_operands += a;
+                P.ms_gather += b;
                 P.ms_products += c;
             }
             ++passes;
@@ -166,6 +166,7 @@ int ensure_query(cfpq_ctx *ctx, bool restricted = false) {
     q.g = &ctx->graph;
     q.closure_mode = ctx->opt.closure_mode;
     q.gather_slices = ctx->opt.gather_slices;
+    q.full_kcap = true;
     if (q.restricted != restricted) ctx->exec_dirty = true;  // the work items carry the row masks
     q.restricted = restricted;
     const bool seeded = ctx->has_start;

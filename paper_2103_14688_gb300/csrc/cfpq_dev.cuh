@@ -104,6 +104,17 @@ struct SrcDesc {
     const uint32_t *pure_off[2];
     const uint32_t *pure_col;
     const uint64_t *pure_mask[2];  // per label: bit y set iff y has an edge of it (W words)
+    // Tile source with a product job for the iteration's new edges
+    // (TcJob::covers_new): while its tiles are on and that job runs in this
+    // pass (new_tiles_pay on its counts: tc_kcount, tagged with the pass, at
+    // most tc_kcap rows; tc_mcount; tc_ecount), the row gather leaves the new
+    // edges' row ORs to the tiles and keeps only the product edges
+    // themselves (ident).
+    uint32_t tile_new;
+    uint32_t tc_kcap;
+    const unsigned long long *tc_kcount;
+    const unsigned long long *tc_mcount;
+    const unsigned long long *tc_ecount;
 };
 
 // Gather work item: rows [row0, row1) of one output block.
@@ -185,8 +196,35 @@ struct TcJob {
     uint8_t *a8;
     uint8_t *b8;
     uint32_t map;               // index of the job's pair of tensor maps (a8, b8)
-    uint32_t pad3;
+    // Channel-1 job (covers_new): the iteration's new edges A2 (A = A2 rows,
+    // a_it = their iteration marks) times whole rows of B, compacted on both
+    // sides: M to the rows x with a new edge (xs, count *mcount), K to the
+    // columns y of some new edge (newcols, a bitmap of W words, then ys).
+    // *ecount = the number of new edges.  mcount, ecount and newcols are
+    // zeroed before every pass.  The job runs only when new_tiles_pay says
+    // the tiles beat the row gather on those counts; the gather then skips
+    // the channel's row ORs.
+    uint32_t covers_new;
+    uint64_t *newcols;
+    uint32_t *xs;
+    unsigned long long *mcount;
+    unsigned long long *ecount;
 };
+
+// Does the channel-1 tile job beat the row gather?  The gather reads one
+// closure row (n/8 bytes) per new edge (e of them); the compacted product
+// issues 2 * M * K * n multiply-adds (M and K rounded up to whole 128-row
+// tiles).  With the gather's measured ~3.5 TB/s and the tiles' ~2.5 PFLOP/s
+// (0/1 FP8), the tiles win when M * K < e * 2.5e15 / (16 * 3.5e12), i.e.
+// about 44 * e; n cancels.  listed_k = K for this pass (0 if the list was not
+// built), kcap = the job's room for it.
+constexpr unsigned long long kTileEdgeRatio = 44;
+__host__ __device__ inline bool new_tiles_pay(uint32_t listed_k, uint32_t kcap, unsigned long long m,
+                                              unsigned long long e) {
+    if (listed_k == 0 || listed_k > kcap || m == 0) return false;
+    const unsigned long long pm = (m + 127ull) & ~127ull, pk = ((unsigned long long)listed_k + 127ull) & ~127ull;
+    return pm * pk < kTileEdgeRatio * e;
+}
 
 constexpr uint32_t kDenseDiv = 32;  // a box is dense from n^2 / 32 edges on (one bit in two words)
 constexpr uint32_t kAutoTilesMinN = 2048;  // AUTO switches boxes to tile products only from this n on
@@ -211,6 +249,7 @@ struct ExecTables {
     const uint32_t *t_lvl_tiles;             // [nq * maxL1] TC tiles of the jobs at (q, level)
     // written by the control kernel for the next pass
     uint32_t *g_total;                       // [kClasses]
+    uint32_t *g_next;                        // [kClasses] dynamic gather units taken in the pass
     uint32_t *g_pre[kClasses];               // [nq] exclusive prefix of live items
     uint32_t *g_beg[kClasses];               // [nq] first live item
     uint32_t *x_total;                       // [kClasses]

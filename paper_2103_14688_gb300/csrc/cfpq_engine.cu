@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <type_traits>
 
 #include "cfpq_engine.cuh"
 
@@ -268,7 +269,9 @@ int QueryDev::plan(std::string *err) {
     n_tc_src = 0;
     // compacted inner dimension: every row up to n = 8192 (operands of at
     // most 2 n^2 bytes per source), half of the rows above, a multiple of 128
-    kcap = W * 64u <= 8192u ? W * 64u : std::max<uint32_t>(128u, ((W * 32u) + 127u) & ~127u);
+    // (full_kcap: every row, so that a product covering the new edges, whose
+    // list can grow to n, stays compacted)
+    kcap = (W * 64u <= 8192u || full_kcap) ? W * 64u : std::max<uint32_t>(128u, ((W * 32u) + 127u) & ~127u);
     blk_src0.assign(blocks.size(), 0);
     blk_nsrc.assign(blocks.size(), 0);
     for (size_t b = 0; b < blocks.size(); ++b) {
@@ -316,6 +319,9 @@ int QueryDev::plan(std::string *err) {
         sd.box_switch =
             (closure_mode == CFPQ_CLOSURE_AUTO && sd.label_kind == 1 && tiles_ok && n >= kAutoTilesMinN) ? 1u : 0u;
         sd.tc_slot = (sd.dense || sd.box_switch) ? (int32_t)n_tc_src++ : -1;
+        // the new edges of a nonterminal tile source get a job of their own
+        // (channel 1, run when the tiles beat the gather: new_tiles_pay)
+        sd.tc_slot_new = (sd.tc_slot >= 0 && sd.label_kind == 1 && !sd.same_level) ? (int32_t)n_tc_src++ : -1;
     }
     // Extraction blocks: (q0_b, f) for f final in box b.
     fblocks.clear();
@@ -335,7 +341,7 @@ int QueryDev::plan(std::string *err) {
 }
 
 uint64_t QueryDev::tc_slot_bytes() const {
-    return (uint64_t)W * 64 * 4 + 256 + ((uint64_t)n + (uint64_t)W * 64) * kcap;
+    return (uint64_t)W * 64 * 8 + 256 + ((uint64_t)n + (uint64_t)W * 64) * kcap;
 }
 
 uint64_t QueryDev::footprint() const {
@@ -504,6 +510,8 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     max_tc_tiles = 0;
     max_tc_w = 0;
     uint32_t n_maps = 0;
+    size_t n_newcols = 0;  // words of the channel-1 jobs' column bitmaps and counts
+    std::vector<size_t> newcols_of;
     uint32_t live_bound[kClasses] = {0};
     for (uint32_t qi = 0; qi < nq; ++qi) {
         QueryDev &q = *qs[qi];
@@ -544,6 +552,17 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
             d.dense = sd.dense;
             d.box_switch = sd.box_switch;
             d.label_box = sd.label_kind == 1 ? sd.label : 0u;
+            if (sd.tc_slot_new >= 0) {
+                // the channel-1 job's column bitmap and counts: W + 8 words of
+                // the executor's newcols buffer (offsets, made pointers below)
+                d.tile_new = 1u;
+                d.tc_kcap = q.kcap;
+                d.tc_kcount = q.tc_kcount((uint32_t)sd.tc_slot_new);
+                d.tc_mcount = reinterpret_cast<const unsigned long long *>((size_t)(n_newcols + q.W));
+                d.tc_ecount = reinterpret_cast<const unsigned long long *>((size_t)(n_newcols + q.W + 1));
+                newcols_of.push_back(n_newcols);
+                n_newcols += q.W + 8u;
+            }
             hs.push_back(d);
         }
         const int vi = vpl_index(q.vpl);
@@ -575,7 +594,9 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                     if (sd.label_kind != 0 && sd.label < 32u) nt_boxes |= 1u << sd.label;
                 }
                 const bool sliceable = has_nt && q.W >= 128u && nt_boxes != 0u;
-                uint32_t n_slices = sliceable ? (q.W >= 256u ? std::min<uint32_t>(8u, q.W / 64u) : 4u) : 1u;
+                // 4 slices: measured on Dyck-4 n = 65536 (1: 2.93 s, 2: 2.56, 3: 2.53,
+                // 4: 2.50, 8: 2.72, 16: 3.33); more slices cost atomic merges
+                uint32_t n_slices = sliceable ? 4u : 1u;
                 if (q.gather_slices) n_slices = sliceable ? std::min<uint32_t>(q.gather_slices, 16u) : 1u;
                 // nonterminal blocks of wide rows: 128-row items (measured on
                 // Dyck-4; the CSR blocks of the RPQ bench prefer 64)
@@ -651,6 +672,27 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                     lvl_tiles += tiles_m * tiles_n;
                     hj.push_back(j);
                     max_tc_w = std::max(max_tc_w, q.W);
+                    if (sd.tc_slot_new >= 0) {
+                        // channel 1: A2 rows (new in the iteration) x whole rows of B
+                        const size_t off = reinterpret_cast<size_t>(d.tc_mcount) - q.W;
+                        j.chan = 1u;
+                        j.A = q.a2_ptr(sd.label);
+                        j.a_it = q.a2it_mem.as<uint32_t>() + (size_t)sd.label * q.n;
+                        j.b_stamp = nullptr;
+                        j.covers_new = 1u;
+                        j.newcols = reinterpret_cast<uint64_t *>(off);
+                        j.mcount = reinterpret_cast<unsigned long long *>(off + q.W);
+                        j.ecount = reinterpret_cast<unsigned long long *>(off + q.W + 1);
+                        j.xs = q.tc_xs((uint32_t)sd.tc_slot_new);
+                        j.ys = q.tc_ys((uint32_t)sd.tc_slot_new);
+                        j.kcount = q.tc_kcount((uint32_t)sd.tc_slot_new);
+                        j.a8 = q.tc_a8((uint32_t)sd.tc_slot_new);
+                        j.b8 = q.tc_b8((uint32_t)sd.tc_slot_new);
+                        j.map = n_maps++;
+                        j.tile0 = lvl_tiles;
+                        lvl_tiles += tiles_m * tiles_n;
+                        hj.push_back(j);
+                    }
                 }
             }
             t_lvl_tiles[(size_t)qi * maxL1 + L] = lvl_tiles;
@@ -699,6 +741,26 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
         return CFPQ_OK;
     };
     int rc;
+    newcols_words = n_newcols;
+    if (n_newcols) {
+        if (!newcols.ensure(A, n_newcols * 8, err)) return CFPQ_ERR_OUT_OF_MEMORY;
+        uint64_t *nb = newcols.as<uint64_t>();
+        auto fix = [nb](auto *&p) {
+            using T = std::remove_pointer_t<std::remove_reference_t<decltype(p)>>;
+            p = reinterpret_cast<T *>(nb + reinterpret_cast<size_t>(p));
+        };
+        for (auto &j : hj)
+            if (j.covers_new) {
+                fix(j.newcols);
+                fix(j.mcount);
+                fix(j.ecount);
+            }
+        for (auto &d : hs)
+            if (d.tile_new) {
+                fix(d.tc_mcount);
+                fix(d.tc_ecount);
+            }
+    }
     if ((rc = upload(ctl_ptrs, hp.data(), hp.size() * sizeof(QCtl *)))) return rc;
     if ((rc = upload(srcs, hs.data(), hs.size() * sizeof(SrcDesc)))) return rc;
     if ((rc = upload(fds, hf.data(), hf.size() * sizeof(FDesc)))) return rc;
@@ -720,7 +782,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     // tables: one buffer, static part then the per-pass part
     const size_t nqa = std::max<uint32_t>(nq, 1), lv = nqa * maxL1;
     const size_t words = kClasses * lv + kClasses * (nqa + 1) + 2 * lv  // static
-                         + kClasses + 2 * kClasses * nqa                  // gather lists
+                         + 2 * kClasses + 2 * kClasses * nqa              // gather lists and unit counters
                          + kClasses + 2 * kClasses * nqa                  // extraction lists
                          + 1 + 3 * nqa;                                   // tensor-core lists
     std::vector<uint32_t> ht(words, 0);
@@ -749,6 +811,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     std::copy(t_lvl_tiles.begin(), t_lvl_tiles.end(), ht.begin() + o);
     T.t_lvl_tiles = take(lv);
     T.g_total = take(kClasses);
+    T.g_next = take(kClasses);
     for (int v = 0; v < kClasses; ++v) T.g_pre[v] = take(nqa);
     for (int v = 0; v < kClasses; ++v) T.g_beg[v] = take(nqa);
     T.x_total = take(kClasses);
@@ -784,12 +847,18 @@ int Executor::enqueue_lists(cudaStream_t st) {
 int Executor::enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int use_handle, int *running_out,
                            const cudaEvent_t *ev) {
     std::string *err = nullptr;
+    // Tile operands first: the rows the tile jobs multiply were final before
+    // this pass (lower levels, or the previous pass of a cyclic level), and a
+    // gather whose source's new edges the tiles take needs the job's list.
     if (ev) ENG_CK(cudaEventRecord(ev[0], st));
+    if (n_tcjobs) {
+        if (newcols_words) ENG_CK(cudaMemsetAsync(newcols.p, 0, newcols_words * 8, st));
+        ENG_CK(launch_tc_compact(tcjobs.as<TcJob>(), T, max_tc_w, tc_err.as<int>(), st));
+    }
+    if (ev) ENG_CK(cudaEventRecord(ev[1], st));
     for (int c = 0; c < kClasses; ++c)
         ENG_CK(launch_gather(kVplOf[c / 2], (c & 1) != 0, items[c].as<GItem>(), max_live[c], srcs.as<SrcDesc>(), T, c,
                              st));
-    if (ev) ENG_CK(cudaEventRecord(ev[1], st));
-    if (n_tcjobs) ENG_CK(launch_tc_compact(tcjobs.as<TcJob>(), T, max_tc_w, tc_err.as<int>(), st));
     if (ev) ENG_CK(cudaEventRecord(ev[2], st));
     if (n_tcjobs) {
         ENG_CK(launch_tc_product(false, tcjobs.as<TcJob>(), max_tc_tiles, T, tc_err.as<int>(), st));

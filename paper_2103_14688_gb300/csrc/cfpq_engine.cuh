@@ -200,22 +200,26 @@ struct QueryDev {
         int32_t rblk;
         uint32_t same_level, dense, box_switch;
         int32_t tc_slot;  // compaction buffers of the source's product job, or -1
+        int32_t tc_slot_new;  // ... of its channel-1 job (new edges; nonterminal, not same level), or -1
         uint32_t pure_rb; // the block read is pure-terminal: expand CSR rows
     };
     std::vector<uint32_t> blk_pure_n, blk_pure_lbl;  // per block: labels of a pure-terminal block (<= 2)
-    // Product jobs' compaction buffers, one slot per tile source: the dirty
-    // row list (n_pad entries), its pass-stamped count, A's columns at the
-    // listed rows as FP8 bytes (n rows of kcap) and the listed B rows
-    // transposed (n_pad rows of kcap).  Every part starts 128-byte aligned.
+    // Product jobs' compaction buffers, one slot per tile job: the dirty
+    // row list (n_pad entries), its pass-stamped count, the row list of a
+    // channel-1 job (n_pad entries), A's columns at the listed rows as FP8
+    // bytes (n rows of kcap) and the listed B rows transposed (n_pad rows of
+    // kcap).  Every part starts 128-byte aligned.
     DBuf tc_mem;
     uint32_t n_tc_src = 0, kcap = 0;
+    bool full_kcap = false;  // tile jobs' inner dimension may hold every row (else half above n = 8192)
     uint64_t tc_slot_bytes() const;
     unsigned char *tc_slot(uint32_t k) const { return tc_mem.as<unsigned char>() + (size_t)k * tc_slot_bytes(); }
     uint32_t *tc_ys(uint32_t k) const { return reinterpret_cast<uint32_t *>(tc_slot(k)); }
     unsigned long long *tc_kcount(uint32_t k) const {
         return reinterpret_cast<unsigned long long *>(tc_slot(k) + (size_t)W * 64 * 4);
     }
-    uint8_t *tc_a8(uint32_t k) const { return tc_slot(k) + (size_t)W * 64 * 4 + 256; }
+    uint32_t *tc_xs(uint32_t k) const { return reinterpret_cast<uint32_t *>(tc_slot(k) + (size_t)W * 64 * 4 + 256); }
+    uint8_t *tc_a8(uint32_t k) const { return tc_slot(k) + (size_t)W * 64 * 8 + 256; }
     uint8_t *tc_b8(uint32_t k) const { return tc_a8(k) + (size_t)n * kcap; }
     std::vector<uint32_t> blk_src0, blk_nsrc;  // per block
     std::vector<uint32_t> blk_level;           // per block, 0..n_levels-1
@@ -256,6 +260,8 @@ struct Executor {
     std::vector<QueryDev *> qs;
     DBuf ctl_ptrs, mirror, items[kClasses], xitems[kClasses], srcs, fds, running;
     DBuf tcjobs, tcmaps, tables, tc_err, done_counter;
+    DBuf newcols;              // new-edge column bitmaps of the jobs covering new edges (zeroed every pass)
+    size_t newcols_words = 0;
     ExecTables T;
     uint32_t n_items[kClasses] = {0}, n_xitems[kClasses] = {0};
     uint32_t max_live[kClasses] = {0};  // bound on live items of a pass: sum over queries of the largest level
@@ -277,8 +283,9 @@ struct Executor {
     int assemble(Allocator *A, cudaStream_t st, std::string *err);
     int enqueue_prologue(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes);
     int enqueue_lists(cudaStream_t st);  // recompute the live lists without advancing any query
-    // ev (profiling, may be null): four events recorded before the row
-    // gathers, after them, after the tile operands and after the tile products.
+    // ev (profiling, may be null): four events recorded before the tile
+    // operands, after them (before the row gathers), after the gathers and
+    // after the tile products.
     int enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int use_handle, int *running_out,
                      const cudaEvent_t *ev = nullptr);
     int build_graph(cudaStream_t st, uint32_t max_iter, uint32_t max_rounds, uint32_t max_passes, std::string *err);

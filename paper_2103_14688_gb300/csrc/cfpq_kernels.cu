@@ -20,6 +20,8 @@
 //   k_control  advances each query's loop state and sets the CUDA-graph
 //              conditional (Listing 1: "while M2 is changing").
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "cfpq_dev.cuh"
@@ -176,7 +178,12 @@ __device__ __forceinline__ int lowbit4(uint4 &v, bool clear) {
 //   4  all edges, source rows of this level changed in the previous pass
 //      (REPEAT pass of a cyclic level).
 // Channels 2 and 4 of a tensor-core source (and of a switchable source while
-// its box is dense) run as tile products over the dirty rows instead.
+// its box is dense) run as tile products over the dirty rows instead.  When
+// the source's channel-1 tile job (SrcDesc::tile_new) runs in this pass,
+// channel 1's row ORs go to the tiles too: the result keeps channel 1 only
+// for the product edges themselves (ident), flagged by bit 8 (read no
+// closure rows).
+template <bool NT>
 __device__ __forceinline__ uint32_t src_channels(const SrcDesc &d, uint32_t mode, uint32_t iter, uint32_t g,
                                                  uint32_t g0, uint32_t dense_mask) {
     const bool tiles = d.dense || (d.box_switch && d.csr_off == nullptr && d.label_box < 32u &&
@@ -189,7 +196,14 @@ __device__ __forceinline__ uint32_t src_channels(const SrcDesc &d, uint32_t mode
     } else {
         if (d.rblk && d.same_level && *d.rlast + 1u >= g) ch |= 4u;
     }
-    return tiles ? (ch & 1u) : ch;
+    if (!tiles) return ch;
+    ch &= 1u;
+    if (NT && ch && d.tile_new && d.tc_kcount) {
+        const unsigned long long kc = *reinterpret_cast<const volatile unsigned long long *>(d.tc_kcount);
+        const uint32_t listed = ((uint32_t)(kc >> 32) == g) ? (uint32_t)kc : 0u;
+        if (new_tiles_pay(listed, d.tc_kcap, *d.tc_mcount, *d.tc_ecount)) ch = d.ident ? 9u : 0u;
+    }
+    return ch;
 }
 
 // --------------------------------------------------------------------------
@@ -205,9 +219,24 @@ struct GatherOcc {
     static constexpr int value = VPL <= 2 ? 4 : (VPL == 4 ? 2 : 1);
 };
 
+// Scheduling.  Narrow rows: one CTA per live item (the grid covers every
+// item of the class; CTAs past the live count exit at once).  Wide rows of
+// the general variant (one warp per row, VPL >= 4, at most one or two CTAs
+// per SM for the shared-memory ring): the grid is persistent and each warp
+// takes units of kGatherParts row ranges of a live item from a counter of the
+// pass (ExecTables::g_next, zeroed by the loop control), so that a warp held
+// by a row with thousands of new edges leaves the other warps of its CTA free
+// to take more work instead of waiting for it at a barrier.
+template <int VPL, bool NT>
+struct GatherDyn {
+    static constexpr bool on = NT && VPL >= 4;
+};
+constexpr uint32_t kGatherParts = 4;
+
 template <int VPL, bool NT>
 __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
     k_gather(const GItem *__restrict__ items, const SrcDesc *__restrict__ srcs, ExecTables T, int cls) {
+    constexpr bool kDyn = GatherDyn<VPL, NT>::on;
     __shared__ unsigned long long s_changed, s_ors;
     // rows of the item to compute (multiple-source runs; else all): the item's
     // rows start at a multiple of 64 and number at most 1024, so its 16 mask
@@ -217,28 +246,46 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
     extern __shared__ uint4 s_ring[];
     constexpr int P = GatherRing<VPL>::depth;
     uint4 *ring = s_ring + (size_t)(threadIdx.x >> 5) * GatherRing<VPL>::slots * 32 * VPL;
-    // one CTA per live item (the grid covers every item of the class; CTAs
-    // past the live count exit at once): a CTA that finishes early frees its
-    // slot for the next one, which a persistent loop would not.
     const uint32_t total = T.g_total[cls];
-    for (uint32_t li = blockIdx.x; li < total; li += gridDim.x) {
+    uint32_t li = blockIdx.x;
+    if (kDyn) li = 0u;
+    for (bool first = true;; first = false) {
+    uint32_t part = 0u;
+    if constexpr (kDyn) {
+        uint32_t u = 0u;
+        if ((threadIdx.x & 31) == 0) u = atomicAdd(T.g_next + cls, 1u);
+        u = __shfl_sync(FULLMASK, u, 0);
+        if (u >= total * kGatherParts) break;
+        li = u / kGatherParts;
+        part = u % kGatherParts;
+    } else {
+        if (!first) li += gridDim.x;
+        if (li >= total) break;
+    }
     const uint32_t q = find_owner(T.g_pre[cls], T.nq, li);
     const GItem it = items[T.g_beg[cls][q] + (li - T.g_pre[cls][q])];
     const QCtl *c = it.ctl;
     if (c->phase != kPhaseRun || c->level != it.level) continue;
     const uint32_t g = c->g, iter = c->iter, mode = c->mode, g0 = c->g_iter_start, dmask = c->dense_mask;
 
-    int act = 0;
-    for (uint32_t k = threadIdx.x; k < it.nsrc; k += blockDim.x)
-        act |= src_channels(srcs[it.src0 + k], mode, iter, g, g0, dmask) != 0u;
-    if (!__syncthreads_or(act)) continue;
+    if constexpr (kDyn) {
+        bool act = false;
+        for (uint32_t k = threadIdx.x & 31; k < it.nsrc; k += 32u)
+            act |= src_channels<NT>(srcs[it.src0 + k], mode, iter, g, g0, dmask) != 0u;
+        if (!__any_sync(FULLMASK, act)) continue;
+    } else {
+        int act = 0;
+        for (uint32_t k = threadIdx.x; k < it.nsrc; k += blockDim.x)
+            act |= src_channels<NT>(srcs[it.src0 + k], mode, iter, g, g0, dmask) != 0u;
+        if (!__syncthreads_or(act)) continue;
 
-    if (threadIdx.x == 0) { s_changed = 0; s_ors = 0; }
-    if (threadIdx.x < 16u) {
-        const uint32_t wrow = it.row0 + threadIdx.x * 64u;
-        s_rmask[(wrow >> 6) & 15u] = (it.rmask && wrow < it.row1) ? it.rmask[wrow >> 6] : ~0ull;
+        if (threadIdx.x == 0) { s_changed = 0; s_ors = 0; }
+        if (threadIdx.x < 16u) {
+            const uint32_t wrow = it.row0 + threadIdx.x * 64u;
+            s_rmask[(wrow >> 6) & 15u] = (it.rmask && wrow < it.row1) ? it.rmask[wrow >> 6] : ~0ull;
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lpr = (int)it.lpr, grp = lane / lpr, gl = lane % lpr, rpw = 32 / lpr;
@@ -256,21 +303,36 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
     const bool sliced = slices_on && (sv0 != 0u || sv1 < nvec);
     uint32_t my_changed = 0, my_ors = 0;
 
-    for (uint32_t rbase = it.row0 + (uint32_t)(warp * rpw); rbase < it.row1; rbase += 8u * rpw) {
+    // rows of this warp: the unit's range of rpw-row steps (dynamic), or
+    // every eighth step of the item (one CTA per item)
+    uint32_t r_first = it.row0 + (uint32_t)(warp * rpw), r_end = it.row1, r_step = 8u * rpw;
+    if constexpr (kDyn) {
+        const uint32_t steps = (it.row1 - it.row0 + (uint32_t)rpw - 1u) / (uint32_t)rpw;
+        const uint32_t per = (steps + kGatherParts - 1u) / kGatherParts;
+        r_first = it.row0 + part * per * (uint32_t)rpw;
+        r_end = min(it.row1, r_first + per * (uint32_t)rpw);
+        r_step = (uint32_t)rpw;
+    }
+    for (uint32_t rbase = r_first; rbase < r_end; rbase += r_step) {
         const uint32_t row = rbase + grp;
-        const bool valid = row < it.row1 && ((s_rmask[(row >> 6) & 15u] >> (row & 63u)) & 1ull);
+        bool valid = row < r_end;
+        if constexpr (kDyn) valid = valid && (!it.rmask || ((it.rmask[row >> 6] >> (row & 63u)) & 1ull));
+        else valid = valid && ((s_rmask[(row >> 6) & 15u] >> (row & 63u)) & 1ull);
         uint4 acc[VPL];
 #pragma unroll
         for (int j = 0; j < VPL; ++j) acc[j] = make_uint4(0, 0, 0, 0);
 
         for (uint32_t k = 0; k < it.nsrc; ++k) {
             const SrcDesc d = srcs[it.src0 + k];
-            const uint32_t chans = src_channels(d, mode, iter, g, g0, dmask);
+            const uint32_t chans = src_channels<NT>(d, mode, iter, g, g0, dmask);
+            // closure rows read by this source (none when the tiles OR them:
+            // only the product edges themselves are left here)
+            const uint64_t *const rblk = (NT && (chans & 8u)) ? nullptr : d.rblk;
             for (uint32_t cbit = 1u; cbit <= 4u; cbit <<= 1) {
                 if (!(chans & cbit)) continue;
                 const bool new_edges = cbit == 1u;
                 const bool use_ident = new_edges && d.ident;
-                if (!use_ident && d.rblk == nullptr) continue;
+                if (!use_ident && rblk == nullptr) continue;
                 // a source row takes part when its stamp is >= thr
                 const uint32_t thr = new_edges ? 0u : (cbit == 2u ? g0 : g - 1u);
 
@@ -281,7 +343,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                 // in flight.
                 constexpr int U = VPL >= 4 ? 1 : 4 / VPL;
                 auto take_batch = [&](uint32_t y_l, bool has_l) {
-                    const bool keep = has_l && (d.rblk == nullptr || thr == 0u || d.rstamp[y_l] >= thr);
+                    const bool keep = has_l && (rblk == nullptr || thr == 0u || d.rstamp[y_l] >= thr);
                     if constexpr (NT) {
                         if (d.pure_n && !use_ident) {
                             if (lpr == 32) {  // one row per warp: the bitmap in the warp's first slot
@@ -291,7 +353,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                             or_pure_rows<VPL>(acc, d, y_l, keep, lpr, gl, grp, gmask);
                             return;
                         }
-                        if (GatherRing<VPL>::on && d.rblk && !d.pure_n) {
+                        if (GatherRing<VPL>::on && rblk && !d.pure_n) {
                             // Rows through the warp's shared-memory ring, P in
                             // flight: row i is copied into slot i % P by
                             // cp.async (each lane its own 16-byte pieces, so a
@@ -314,7 +376,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                                 const uint32_t sidx = issued % (uint32_t)P;
                                 if (h) {
                                     uint4 *sl = ring + sidx * 32u * VPL;
-                                    const uint4 *r = reinterpret_cast<const uint4 *>(d.rblk + (size_t)y * W);
+                                    const uint4 *r = reinterpret_cast<const uint4 *>(rblk + (size_t)y * W);
 #pragma unroll
                                     for (int j = 0; j < VPL; ++j) {
                                         const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
@@ -367,11 +429,11 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                                 }
                             }
                         }
-                        if (d.rblk && (!NT || !d.pure_n)) {
+                        if (rblk && (!NT || !d.pure_n)) {
                             uint4 rv[U][VPL];
 #pragma unroll
                             for (int u = 0; u < U; ++u) {
-                                const uint4 *r = reinterpret_cast<const uint4 *>(d.rblk + (size_t)ys[u] * W);
+                                const uint4 *r = reinterpret_cast<const uint4 *>(rblk + (size_t)ys[u] * W);
 #pragma unroll
                                 for (int j = 0; j < VPL; ++j) {
                                     const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
@@ -413,11 +475,11 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                                 ident_bit(y0);
                                 if (two) ident_bit(y1);
                             }
-                            if (d.rblk) {
+                            if (rblk) {
                                 const bool k0 = !thr || d.rstamp[y0] >= thr;
                                 const bool k1 = two && (!thr || d.rstamp[y1] >= thr);
-                                const uint4 *r0 = reinterpret_cast<const uint4 *>(d.rblk + (size_t)y0 * W);
-                                const uint4 *r1 = reinterpret_cast<const uint4 *>(d.rblk + (size_t)y1 * W);
+                                const uint4 *r0 = reinterpret_cast<const uint4 *>(rblk + (size_t)y0 * W);
+                                const uint4 *r1 = reinterpret_cast<const uint4 *>(rblk + (size_t)y1 * W);
                                 uint4 a0[VPL], a1[VPL];
 #pragma unroll
                                 for (int j = 0; j < VPL; ++j) {
@@ -473,7 +535,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                         // the output row -- no enumeration
 #pragma unroll
                         for (int j = 0; j < VPL; ++j) or4(acc[j], a[j]);
-                        if (d.rblk == nullptr) continue;
+                        if (rblk == nullptr) continue;
                     }
                     // Each lane proposes the lowest set bit of its part of the
                     // adjacency row per step (ballot/ffs enumeration).
@@ -532,18 +594,30 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
             ++my_changed;
         }
     }
-    if (my_changed) atomicAdd(&s_changed, (unsigned long long)my_changed);
-    if (my_ors) atomicAdd(&s_ors, (unsigned long long)my_ors);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        QCtl *cw = it.ctl;
-        if (s_changed) {
-            *it.out_last = g;
-            atomicAdd(&cw->changed_rows, s_changed);
+    if constexpr (kDyn) {
+        const uint32_t wc = __reduce_add_sync(FULLMASK, my_changed), wo = __reduce_add_sync(FULLMASK, my_ors);
+        if (lane == 0) {
+            QCtl *cw = it.ctl;
+            if (wc) {
+                *it.out_last = g;
+                atomicAdd(&cw->changed_rows, (unsigned long long)wc);
+            }
+            if (wo) atomicAdd(&cw->row_ors, (unsigned long long)wo);
         }
-        if (s_ors) atomicAdd(&cw->row_ors, s_ors);
+    } else {
+        if (my_changed) atomicAdd(&s_changed, (unsigned long long)my_changed);
+        if (my_ors) atomicAdd(&s_ors, (unsigned long long)my_ors);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            QCtl *cw = it.ctl;
+            if (s_changed) {
+                *it.out_last = g;
+                atomicAdd(&cw->changed_rows, s_changed);
+            }
+            if (s_ors) atomicAdd(&cw->row_ors, s_ors);
+        }
+        __syncthreads();
     }
-    __syncthreads();
     }
 }
 
@@ -817,6 +891,7 @@ __device__ void control_body(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaG
     }
     if (threadIdx.x < K) {
         const int k = threadIdx.x;
+        if (k < kClasses) T.g_next[k] = 0u;  // dynamic gather units of the next pass
         if (k < kClasses) T.g_total[k] = s_carry[k];
         else if (k < 2 * kClasses) T.x_total[k - kClasses] = s_carry[k];
         else *T.t_total = s_carry[k];
@@ -1083,11 +1158,23 @@ int vpl_for_words(uint32_t W) {
     return 0;
 }
 
+static int g_gather_sms[64];
+
 cudaError_t launch_gather(int vpl, bool nt, const GItem *items, uint32_t n_items, const SrcDesc *srcs,
                           const ExecTables &T, int cls, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
-#define CFPQ_GATHER(V)                                                                         \
-    if (nt) k_gather<V, true><<<n_items, 256, GatherRing<V>::bytes, st>>>(items, srcs, T, cls); \
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint32_t sms = (dev >= 0 && dev < 64 && g_gather_sms[dev]) ? (uint32_t)g_gather_sms[dev] : 0u;
+    // dynamic scheduling: a persistent grid (resident CTAs), at most one warp per unit
+    auto grid_of = [&](bool dyn, int occ) -> uint32_t {
+        if (!dyn || !sms) return n_items;
+        const uint32_t want = (n_items * kGatherParts + 7u) / 8u;
+        return std::max<uint32_t>(1u, std::min<uint32_t>(want, sms * (uint32_t)occ));
+    };
+#define CFPQ_GATHER(V)                                                                                          \
+    if (nt) k_gather<V, true><<<grid_of(GatherDyn<V, true>::on, GatherOcc<V>::value), 256, GatherRing<V>::bytes, \
+                                st>>>(items, srcs, T, cls);                                                     \
     else k_gather<V, false><<<n_items, 256, 0, st>>>(items, srcs, T, cls);
     switch (vpl) {
         case 1: CFPQ_GATHER(1) break;
@@ -1112,6 +1199,14 @@ cudaError_t prepare_gather_launch() {
     }
     CFPQ_RING(4) CFPQ_RING(8) CFPQ_RING(16)
 #undef CFPQ_RING
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    g_gather_sms[dev] = sms;
     return cudaSuccess;
 }
 

@@ -225,11 +225,14 @@ struct KDim {
     bool compact;
 };
 
+// A channel-1 job (covers_new) is always compacted, and runs (kdim > 0)
+// only when new_tiles_pay: otherwise the row gather ORs the new edges' rows.
 __device__ __forceinline__ KDim job_kdim(const TcJob &J, uint32_t g) {
     KDim k{J.B ? J.n : 0u, false};
     if (J.ys && J.kcount) {
         const unsigned long long kc = *reinterpret_cast<volatile unsigned long long *>(J.kcount);
         const uint32_t d = ((uint32_t)(kc >> 32) == g) ? (uint32_t)kc : 0u;
+        if (J.covers_new) return KDim{new_tiles_pay(d, J.kcap, *J.mcount, *J.ecount) ? d : 0u, true};
         if (d <= J.kcap) k = KDim{d, true};
     }
     return k;
@@ -527,17 +530,64 @@ __device__ __forceinline__ void for_job_chunks(const TcJob *jobs, const ExecTabl
     }
 }
 
-// List the rows y of B with stamp >= thr (order irrelevant: the product sums
-// over them).
+// Channel-1 jobs (TcJob::covers_new), before their row lists: for the A2
+// rows x new in the iteration, newcols (zeroed before the pass) |= row x,
+// x is appended to xs, and *ecount += the row's edges.  Unit: 512 rows;
+// thread t ORs words t, t + 256, ... of those rows in registers and merges
+// them with one atomicOr per word.
+constexpr uint32_t kNewColRows = 512;
+__global__ void __launch_bounds__(256) k_tc_newcols(const TcJob *__restrict__ jobs, ExecTables T) {
+    __shared__ unsigned long long s_edges;
+    for_job_chunks(jobs, T, kNewColRows, [&](const TcJob &J, uint32_t c) {
+        uint32_t thr, iter, g;
+        if (!J.covers_new || !tc_job_active(J, &thr, &iter, &g)) return;
+        const uint32_t W = J.W, x_end = min(J.n, (c + 1u) * kNewColRows);
+        constexpr int kWordsPerThread = (int)(kColMaxW / 256u);
+        uint64_t acc[kWordsPerThread];
+#pragma unroll
+        for (int i = 0; i < kWordsPerThread; ++i) acc[i] = 0ull;
+        unsigned long long edges = 0ull;
+        for (uint32_t x = c * kNewColRows; x < x_end; ++x) {
+            if (J.a_it[x] != iter) continue;
+            if (threadIdx.x == 0) J.xs[atomicAdd(J.mcount, 1ull)] = x;
+            const uint64_t *row = J.A + (size_t)x * W;
+#pragma unroll
+            for (int i = 0; i < kWordsPerThread; ++i) {
+                const uint32_t w = threadIdx.x + 256u * (uint32_t)i;
+                if (w < W) {
+                    const uint64_t v = row[w];
+                    acc[i] |= v;
+                    edges += (unsigned long long)__popcll(v);
+                }
+            }
+        }
+        if (threadIdx.x == 0) s_edges = 0ull;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kWordsPerThread; ++i) {
+            const uint32_t w = threadIdx.x + 256u * (uint32_t)i;
+            if (w < W && acc[i]) atomicOr(reinterpret_cast<unsigned long long *>(J.newcols + w), acc[i]);
+        }
+        edges = __reduce_add_sync(0xffffffffu, (uint32_t)edges);
+        if ((threadIdx.x & 31) == 0 && edges) atomicAdd(&s_edges, edges);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_edges) atomicAdd(J.ecount, s_edges);
+        __syncthreads();
+    });
+}
+
+// List the rows y of B with stamp >= thr; for a channel-1 job the columns
+// of its newcols (order irrelevant: the product sums over them).
 __global__ void __launch_bounds__(256) k_tc_rows(const TcJob *__restrict__ jobs, ExecTables T, int *err_flag) {
     const int lane = threadIdx.x & 31;
     for_job_chunks(jobs, T, kRowChunk, [&](const TcJob &J, uint32_t c) {
         uint32_t thr, iter, g;
-        if (!tc_job_active(J, &thr, &iter, &g) || !J.b_stamp) return;
+        if (!tc_job_active(J, &thr, &iter, &g) || (!J.b_stamp && !J.covers_new)) return;
         const uint32_t y_end = min(J.n, (c + 1u) * kRowChunk);
         for (uint32_t y0 = c * kRowChunk; y0 < y_end; y0 += blockDim.x) {
             const uint32_t y = y0 + threadIdx.x;
-            const bool dirty = y < y_end && J.b_stamp[y] >= thr;
+            const bool dirty = y < y_end && (J.covers_new ? ((J.newcols[y >> 6] >> (y & 63u)) & 1ull) != 0ull
+                                                          : J.b_stamp[y] >= thr);
             const unsigned bal = __ballot_sync(0xffffffffu, dirty);
             if (!bal) continue;
             uint32_t base = 0;
@@ -560,8 +610,10 @@ __global__ void __launch_bounds__(256) k_tc_a8(const TcJob *__restrict__ jobs, E
         if (!tc_job_active(J, &thr, &iter, &g)) return;
         const KDim K = job_kdim(J, g);
         if (!K.compact || K.kdim == 0u) return;
-        const uint32_t x = c * kColRows + (uint32_t)warp;
-        if (x >= J.n) return;
+        // row m of a8: A's row m, or for a channel-1 job A2's row xs[m]
+        const uint32_t m = c * kColRows + (uint32_t)warp;
+        if (m >= (J.covers_new ? (uint32_t)*J.mcount : J.n)) return;
+        const uint32_t x = J.covers_new ? J.xs[m] : m;
         const uint32_t W = J.W, D = K.kdim, dpad = (D + 127u) & ~127u;
         const uint4 *src = reinterpret_cast<const uint4 *>(J.A + (size_t)x * W);
         bool nz = false;
@@ -572,7 +624,7 @@ __global__ void __launch_bounds__(256) k_tc_a8(const TcJob *__restrict__ jobs, E
         }
         nz = __any_sync(0xffffffffu, nz);
         __syncwarp();
-        uint32_t *dst = reinterpret_cast<uint32_t *>(J.a8 + (size_t)x * J.kcap);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(J.a8 + (size_t)m * J.kcap);
         for (uint32_t k0 = 0; k0 < dpad; k0 += 128u) {
             const uint32_t kb = k0 + 4u * (uint32_t)lane;
             uint32_t word = 0u;
@@ -694,11 +746,12 @@ __device__ __forceinline__ void tma_load(void *dst, const void *map, int32_t c0,
 struct Tile {
     const TcJob *J;
     uint32_t m0, n0, ks, g;
+    uint32_t mlim;  // rows of a8 (a channel-1 job's row count; else n)
 };
 struct JobCache {
     const TcJob *J = nullptr;
     uint32_t li0 = 1u, li1 = 0u;  // live-tile indices of the job: [li0, li1)
-    uint32_t ks = 0, g = 0;
+    uint32_t ks = 0, g = 0, mlim = 0;
     bool ok = false;
 };
 
@@ -711,11 +764,16 @@ __device__ __forceinline__ bool next_tile(const TcJob *jobs, const ExecTables &T
                 continue;
             }
             const uint32_t t = li - jc.li0;
-            tl.J = jc.J;
             tl.m0 = (t / jc.J->tiles_n) * 128u;
+            if (tl.m0 >= jc.mlim) {  // past a channel-1 job's rows: the rest of the job too
+                li += ((jc.li1 - 1u - li) / gridDim.x) * gridDim.x;
+                continue;
+            }
+            tl.J = jc.J;
             tl.n0 = (t % jc.J->tiles_n) * 256u;
             tl.ks = jc.ks;
             tl.g = jc.g;
+            tl.mlim = jc.mlim;
             return true;
         }
         const uint32_t q = find_owner(T.t_pre, T.nq, li);
@@ -742,6 +800,7 @@ __device__ __forceinline__ bool next_tile(const TcJob *jobs, const ExecTables &T
         jc.ok = ok;
         jc.ks = (K.kdim + 127u) / 128u;
         jc.g = g;
+        jc.mlim = ok && J.covers_new ? (uint32_t)*J.mcount : J.n;
         li -= gridDim.x;  // re-enter through the cache
     }
     return false;
@@ -840,7 +899,9 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
             if (__any_sync(0xffffffffu, to)) { to = true; break; }
             tc_after();
             const TcJob &J = *tl.J;
-            const uint32_t r = quarter * 32u + (uint32_t)lane, x = tl.m0 + r;
+            // output row: tile row m0 + r, through xs for a channel-1 job
+            const uint32_t r = quarter * 32u + (uint32_t)lane, mr = tl.m0 + r;
+            const uint32_t x = mr >= tl.mlim ? J.n : (J.covers_new ? J.xs[mr] : mr);
             uint32_t mask[4];
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
@@ -939,8 +1000,11 @@ cudaError_t launch_tc_compact(const TcJob *jobs, const ExecTables &T, uint32_t m
     cudaGetDevice(&dev);
     const int sms = (dev >= 0 && dev < 64 && g_tc_sms[dev]) ? g_tc_sms[dev] : 0;
     if (!sms) return cudaErrorNotReady;  // prepare_tc_launch was not called
-    k_tc_rows<<<(unsigned)sms * 4u, 256, 0, st>>>(jobs, T, err_flag);
+    k_tc_newcols<<<(unsigned)sms * 2u, 256, 0, st>>>(jobs, T);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_tc_rows<<<(unsigned)sms * 4u, 256, 0, st>>>(jobs, T, err_flag);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_tc_a8<<<(unsigned)sms * 4u, 256, (size_t)max_w * 8u * 8u, st>>>(jobs, T, max_w);
     e = cudaGetLastError();
