@@ -528,12 +528,97 @@ def run_dyck(args):
         "clocks": clk,
         "wall_s": wall,
     }
+    if rank == 0 and not args.no_extras:
+        line["batched"] = batched_summary(args.batch, local)
+        line["served"] = served_summary(args.served_lambda, args.served_horizon, local)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_dyck(n)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def batched_summary(count, device):
+    """The batched workload (512 queries, n ~ U[256, 8192], 3-24 RSM states):
+    one batch in AUTO and with bit-packed rows only, against the same
+    queries one at a time; every batched answer compared with its solo run."""
+    import torch
+    from paper_2103_14688_gb300 import cfpq
+    qs = W.batched_queries(count=count)
+
+    def batch(mode):
+        ctx = cfpq.Context(device=device, closure_mode=mode)
+        ctx.batch_run(qs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.batch_run(qs)
+        torch.cuda.synchronize()
+        return ctx, time.perf_counter() - t0
+
+    actx, at = batch(cfpq.CFPQ_CLOSURE_AUTO)
+    bctx, bt = batch(cfpq.CFPQ_CLOSURE_BITPACKED)
+    solo = cfpq.Context(device=device)
+    st, mism = 0.0, 0
+    for i, (g, r) in enumerate(qs):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        solo.load_graph(g)
+        solo.load_rsm(r)
+        solo.run()
+        torch.cuda.synchronize()
+        st += time.perf_counter() - t0
+        for b in range(r.n_boxes):
+            want = solo.reachable_words(b)
+            mism += int(not ((actx.batch_reachable_words(i, b) == want).all() and
+                             (bctx.batch_reachable_words(i, b) == want).all()))
+    for c in (actx, bctx, solo):
+        c.close()
+    return {"queries": len(qs), "batched_qps": len(qs) / at, "batched_bitpacked_qps": len(qs) / bt,
+            "one_at_a_time_qps": len(qs) / st, "speedup_vs_one_at_a_time": st / at,
+            "mismatches_vs_solo": mism, "timing": "host clock around one batch_run after a warm-up batch"}
+
+
+def served_summary(lam, horizon, device):
+    """The served workload (resident Zipf graph n = 32768, random RSMs with
+    3-32 states, Poisson arrivals at `lam` per second for `horizon` s):
+    queries/s and p50/p99 latency, and the same queries one at a time."""
+    import torch
+    from paper_2103_14688_gb300 import cfpq
+    wl = W.serving_workload(lam=lam, n_queries=100000, horizon_s=horizon)
+    srv = cfpq.Server(wl.graph, device=device)
+    t_start = time.perf_counter()
+    pending = list(zip(wl.arrivals.tolist(), wl.choice.tolist()))
+    live, lat, i = {}, [], 0
+    while i < len(pending) or live:
+        now = time.perf_counter() - t_start
+        while i < len(pending) and pending[i][0] <= now:
+            live[srv.submit(wl.pool[pending[i][1]])] = pending[i][0]
+            i += 1
+        srv.step()
+        now = time.perf_counter() - t_start
+        for t in list(live):
+            if srv.poll(t):
+                lat.append(now - live.pop(t))
+                srv.release(t)
+        if not live and i < len(pending):
+            time.sleep(max(0.0, min(0.001, pending[i][0] - now)))
+    el = time.perf_counter() - t_start
+    srv.close()
+    solo = cfpq.Context(device=device)
+    solo.load_graph(wl.graph)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in wl.choice.tolist():
+        solo.load_rsm(wl.pool[j])
+        solo.run()
+    torch.cuda.synchronize()
+    solo_s = time.perf_counter() - t0
+    solo.close()
+    lat = np.array(lat)
+    return {"lambda": lam, "horizon_s": horizon, "queries": int(len(lat)), "qps": len(lat) / el,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "one_at_a_time_qps": len(wl.choice) / solo_s}
 
 
 def _traffic_from_profiles(name):
@@ -896,6 +981,8 @@ def main():
     ap.add_argument("--dyck-n", type=int, default=65536)
     ap.add_argument("--e2e-steps", type=int, default=5, help="end-to-end steps (at most --steps)")
     ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--served-lambda", type=float, default=100.0, help="default line: served probe arrival rate")
+    ap.add_argument("--served-horizon", type=float, default=3.0, help="default line: served probe seconds")
     ap.add_argument("--lambdas", default="10,30,100,300,1000")
     ap.add_argument("--horizon", type=float, default=5.0)
     ap.add_argument("--no-extras", action="store_true")

@@ -348,6 +348,55 @@ int cfpq_result_reachable_bits(cfpq_server *srv, uint64_t ticket, uint32_t box, 
  * other queries continue unchanged). */
 int cfpq_release(cfpq_server *srv, uint64_t ticket);
 
+/* ---- one query over several GPUs (column sharding) ---------------------------------- */
+
+/* The multi-GPU version of index creation that Sec. 6 names as future work.
+ * Row x of a closure block C[s,t] is the OR, over the product edges
+ * (s,x) -> (u,y) of M3 (Sec. 2.4), of row y of C[u,t] (and bit y when u = t),
+ * so any range of columns (target vertices) of C3 needs only the same range
+ * of the rows it reads.  Each rank (one context per GPU) loads the whole
+ * graph and RSM and computes C3 on its own columns [col0, col1); Listing 1's
+ * extraction then yields the new nonterminal edges in those columns.  After
+ * every iteration the caller exchanges them (an all-gather of the ranks'
+ * slices, e.g. NCCL) and installs the full rows on every rank, which start
+ * the next iteration with the same M2 and A2.  The loop ends after the
+ * first iteration in which no rank found an edge -- the unsharded loop's
+ * last iteration too, so the answer and the iteration count are the same.
+ *
+ *   cfpq_shard_begin(ctx, col0, col1);
+ *   do { cfpq_shard_step(ctx, slice, &k);  all-gather slices -> full;
+ *        cfpq_shard_apply(ctx, full, &done); } while (!done);
+ *
+ * Columns are in the padded width n_pad = n rounded up to 128: col0 a
+ * multiple of 256 (a tensor-core tile), col1 a multiple of 256 or n_pad,
+ * col0 <= col1 (an empty range is allowed); the ranks' ranges must partition
+ * [0, n_pad).  Slices and full rows are device buffers of 64-bit words,
+ * box-major: slice = n_boxes x n rows of (col1 - col0) / 64 words (the rank's
+ * columns of the iteration's new edges), full = n_boxes x n rows of
+ * n_pad / 64 words (the ranks' slices side by side in column order).  The
+ * loop runs with one launch per kernel and pass (the exchange needs the host
+ * between iterations).  After the loop every rank holds the whole answer
+ * (cfpq_get_reachable*); its closure blocks hold only its columns, so
+ * cfpq_get_closure_rows and cfpq_count_index describe those columns only.
+ *
+ * Errors: CFPQ_ERR_STATE (no graph/RSM, a start answer set, step/apply
+ * without begin), CFPQ_ERR_INVALID_ARG (columns, NULL buffers),
+ * CFPQ_ERR_TIMEOUT (a cap of cfpq_options stopped the loop), CFPQ_ERR_CUDA. */
+int cfpq_shard_begin(cfpq_ctx *ctx, uint32_t col0, uint32_t col1);
+
+/* Run one iteration (closure passes and extraction) on the rank's columns and
+ * write its new edges into d_slice; *new_edges (may be NULL) = their count. */
+int cfpq_shard_step(cfpq_ctx *ctx, uint64_t *d_slice, uint64_t *new_edges);
+
+/* Install the gathered new edges d_full of every rank (M2 |= them, A2 :=
+ * them) and decide whether the loop goes on: *done = 1 when no rank found an
+ * edge in the iteration just stepped (the result is then readable). */
+int cfpq_shard_apply(cfpq_ctx *ctx, const uint64_t *d_full, int *done);
+
+/* Loop statistics of the sharded run so far (iterations, passes, edges found
+ * by every rank, this rank's row ORs and tile products). */
+int cfpq_shard_stats(cfpq_ctx *ctx, cfpq_run_stats *stats);
+
 /* ---- building block: dense Boolean product on the tensor cores ---------------------- */
 
 /* c = a * b over the Boolean semiring for n x n bit matrices (host buffers,

@@ -117,6 +117,10 @@ def _declare(lib):
         "cfpq_load_graph_device": (c_int, [P, c_uint32, c_uint32, c_size_t, P, P, P]),
         "cfpq_load_graph_device_noalloc": (c_int, [P, c_uint32, c_uint32, c_size_t, P, P, P]),
         "cfpq_load_rsm": (c_int, [P, POINTER(cfpq_rsm)]),
+        "cfpq_shard_begin": (c_int, [P, c_uint32, c_uint32]),
+        "cfpq_shard_step": (c_int, [P, P, POINTER(c_uint64)]),
+        "cfpq_shard_apply": (c_int, [P, P, POINTER(c_int)]),
+        "cfpq_shard_stats": (c_int, [P, POINTER(cfpq_run_stats)]),
         "cfpq_run": (c_int, [P, POINTER(cfpq_run_stats)]),
         "cfpq_run_sources": (c_int, [P, POINTER(c_uint32), c_uint32, POINTER(cfpq_run_stats)]),
         "cfpq_count_index": (c_int, [P, u64p, u64p]),
@@ -395,13 +399,19 @@ class Context:
         self._batch_n = [g.n for g, _ in queries]
         return list(per), tot
 
-    def batch_reachable_bits(self, q: int, box: int = 0) -> np.ndarray:
+    def batch_reachable_words(self, q: int, box: int = 0) -> np.ndarray:
+        """M2^box of query q of the last batch as bit rows, uint64 [n, ceil(n/64)]."""
         n = self._batch_n[q]
         wn = (n + 63) // 64
         out = np.zeros(n * wn, dtype=np.uint64)
         self._check(self.lib.cfpq_batch_get_reachable_bits(self.h, q, box, c_void_p(out.ctypes.data)),
                     "cfpq_batch_get_reachable_bits")
-        return np.unpackbits(out.reshape(n, wn).view(np.uint8), axis=1, bitorder="little")[:, :n].astype(bool)
+        return out.reshape(n, wn)
+
+    def batch_reachable_bits(self, q: int, box: int = 0) -> np.ndarray:
+        n = self._batch_n[q]
+        w = self.batch_reachable_words(q, box)
+        return np.unpackbits(w.view(np.uint8), axis=1, bitorder="little")[:, :n].astype(bool)
 
 
 class Server:
@@ -482,6 +492,49 @@ class Server:
         if rc != CFPQ_OK:
             raise CfpqError(rc, "cfpq_release: " + status_string(rc))
         self._keep.pop(ticket, None)
+
+
+class ColumnShardEngine:
+    """This rank's part of one query split by closure columns (the engine of
+    ``shard.run_column_sharded``): a Context holding the whole graph and RSM,
+    computing the closure on the columns it is given.  Slices and full rows
+    are int64 torch tensors on the context's device ([B, n, words])."""
+
+    def __init__(self, ctx: "Context", g, r):
+        import torch
+        self.ctx, self.lib = ctx, ctx.lib
+        ctx.load_graph(g)
+        ctx.load_rsm(r)
+        self.n, self.B = g.n, r.n_boxes
+        self.W = (g.n + 127) // 128 * 2
+        self.device = torch.device("cuda", ctx._opt.device)
+        self.slice = None
+
+    def begin(self, col0: int, col1: int):
+        import torch
+        self.ctx._check(self.lib.cfpq_shard_begin(self.ctx.h, col0, col1), "cfpq_shard_begin")
+        self.slice = torch.zeros((self.B, self.n, (col1 - col0) // 64), dtype=torch.int64, device=self.device)
+
+    def step(self):
+        k = c_uint64()
+        self.ctx._check(self.lib.cfpq_shard_step(self.ctx.h, c_void_p(self.slice.data_ptr()), ctypes.byref(k)),
+                        "cfpq_shard_step")
+        self.last_new = k.value
+        return self.slice
+
+    def apply(self, full) -> bool:
+        import torch
+        full = full.to(self.device).contiguous()
+        assert full.dtype == torch.int64 and tuple(full.shape) == (self.B, self.n, self.W)
+        d = c_int()
+        self.ctx._check(self.lib.cfpq_shard_apply(self.ctx.h, c_void_p(full.data_ptr()), ctypes.byref(d)),
+                        "cfpq_shard_apply")
+        return bool(d.value)
+
+    def stats(self) -> cfpq_run_stats:
+        st = cfpq_run_stats()
+        self.ctx._check(self.lib.cfpq_shard_stats(self.ctx.h, ctypes.byref(st)), "cfpq_shard_stats")
+        return st
 
 
 def tc_bool_product(a: np.ndarray, b: np.ndarray, use_int8: bool = False, stream=None) -> np.ndarray:

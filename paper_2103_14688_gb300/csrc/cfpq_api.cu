@@ -765,6 +765,126 @@ extern "C" int cfpq_extract_paths(cfpq_ctx *ctx, uint32_t box, uint32_t vs, uint
 }
 
 // ---------------------------------------------------------------------------
+// Column-sharded index creation (one query over several ranks).
+// ---------------------------------------------------------------------------
+namespace {
+
+// Passes of the executor driven from the host until no query runs (done or
+// paused for the exchange of a sharded iteration).
+int host_passes(cfpq_ctx *ctx, Executor &ex) {
+    int running = 1;
+    while (running) {
+        if (ex.enqueue_pass(ctx->stream, 0, 0, ex.running.as<int>(), nullptr))
+            return fail(ctx, CFPQ_ERR_CUDA, "pass launch failed");
+        CK(ctx, cudaMemcpyAsync(&running, ex.running.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return CFPQ_OK;
+}
+
+}  // namespace
+
+extern "C" int cfpq_shard_begin(cfpq_ctx *ctx, uint32_t col0, uint32_t col1) {
+    if (!ctx) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (!ctx->has_graph || !ctx->has_rsm) return fail(ctx, CFPQ_ERR_STATE, "load a graph and an RSM first");
+    if (ctx->has_start) return fail(ctx, CFPQ_ERR_STATE, "a start answer is set (cfpq_set_start); clear it first");
+    const uint32_t n_pad = ctx->graph.n_pad;
+    if (col0 > col1 || col1 > n_pad || col0 % 256u != 0u || (col1 % 256u != 0u && col1 != n_pad))
+        return fail(ctx, CFPQ_ERR_INVALID_ARG,
+                    "columns must satisfy col0 <= col1 <= n_pad (n rounded up to 128), col0 a multiple of 256 and "
+                    "col1 a multiple of 256 or n_pad");
+    if (int rc = set_device(ctx)) return rc;
+    if (int rc = ensure_query(ctx)) return rc;
+    QueryDev &q = ctx->query;
+    std::string e;
+    if (!ctx->shard_cnt.ensure(&ctx->A, (size_t)q.B * 16, &e)) return fail(ctx, CFPQ_ERR_OUT_OF_MEMORY, e);
+    ctx->has_result = false;
+    ++ctx->result_gen;
+    ctx->result_sources.clear();
+    if (ctx->exec.enqueue_prologue(ctx->stream, ctx->opt.max_iterations, ctx->opt.max_rounds, kDefaultPassCap))
+        return fail(ctx, CFPQ_ERR_CUDA, "prologue launch failed");
+    CK(ctx, launch_shard_setup(q.ctl(), col0 / 128u, col1 / 128u, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->shard_on = true;
+    ctx->shard_c0 = col0;
+    ctx->shard_c1 = col1;
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+extern "C" int cfpq_shard_step(cfpq_ctx *ctx, uint64_t *d_slice, uint64_t *new_edges) {
+    if (!ctx) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (!ctx->shard_on) return fail(ctx, CFPQ_ERR_STATE, "no sharded run (cfpq_shard_begin)");
+    const uint32_t wl = (ctx->shard_c1 - ctx->shard_c0) / 64u;
+    if (wl && !d_slice) return fail(ctx, CFPQ_ERR_INVALID_ARG, "d_slice is NULL");
+    if (int rc = set_device(ctx)) return rc;
+    QueryDev &q = ctx->query;
+    if (int rc = host_passes(ctx, ctx->exec)) return rc;
+    std::vector<QCtl> ctls;
+    int tc_error = 0;
+    if (ctx->exec.read_ctls(ctx->stream, &ctls, &tc_error)) return fail(ctx, CFPQ_ERR_CUDA, "reading loop state failed");
+    if (tc_error)
+        return fail(ctx, CFPQ_ERR_TIMEOUT, "a tile-product kernel gave up (bounded wait on its MMAs or on a counter)");
+    const QCtl &c = ctls[0];
+    if (c.phase == kPhasePause) {
+        CK(ctx, launch_shard_export(q.a2_mem.as<uint64_t>(), q.a2it_mem.as<uint32_t>(), q.n, q.W, q.B,
+                                    ctx->shard_c0 / 64u, ctx->shard_c1 / 64u, c.iter, d_slice, ctx->stream));
+        if (new_edges) *new_edges = c.shard_new;
+    } else {
+        if (wl) CK(ctx, cudaMemsetAsync(d_slice, 0, (size_t)q.B * q.n * wl * 8, ctx->stream));
+        if (new_edges) *new_edges = 0;
+    }
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (c.phase == kPhaseDone && c.status != kStatusOk)
+        return fail(ctx, CFPQ_ERR_TIMEOUT, "iteration, round or pass cap reached before the fixpoint");
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+extern "C" int cfpq_shard_apply(cfpq_ctx *ctx, const uint64_t *d_full, int *done) {
+    if (!ctx || !d_full || !done) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (!ctx->shard_on) return fail(ctx, CFPQ_ERR_STATE, "no sharded run (cfpq_shard_begin)");
+    if (int rc = set_device(ctx)) return rc;
+    QueryDev &q = ctx->query;
+    std::vector<QCtl> ctls;
+    if (ctx->exec.read_ctls(ctx->stream, &ctls, nullptr)) return fail(ctx, CFPQ_ERR_CUDA, "reading loop state failed");
+    if (ctls[0].phase == kPhasePause) {
+        CK(ctx, launch_shard_apply(d_full, q.m2_mem.as<uint64_t>(), q.a2_mem.as<uint64_t>(),
+                                   q.a2it_mem.as<uint32_t>(), q.n, q.W, q.B, ctls[0].iter,
+                                   ctx->shard_cnt.as<unsigned long long>(), q.ctl(), q.boxit_mem.as<uint32_t>(),
+                                   ctx->stream));
+        if (ctx->exec.enqueue_lists(ctx->stream)) return fail(ctx, CFPQ_ERR_CUDA, "list launch failed");
+        if (ctx->exec.read_ctls(ctx->stream, &ctls, nullptr))
+            return fail(ctx, CFPQ_ERR_CUDA, "reading loop state failed");
+    }
+    *done = ctls[0].phase != kPhaseRun ? 1 : 0;
+    if (*done) {
+        ctx->shard_on = false;
+        ctx->has_result = true;
+        ++ctx->result_gen;
+        if (ctls[0].status != kStatusOk)
+            return fail(ctx, CFPQ_ERR_TIMEOUT, "iteration, round or pass cap reached before the fixpoint");
+    }
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+extern "C" int cfpq_shard_stats(cfpq_ctx *ctx, cfpq_run_stats *stats) {
+    if (!ctx || !stats) return CFPQ_ERR_INVALID_ARG;
+    API_TRY
+    if (int rc = set_device(ctx)) return rc;
+    std::vector<QCtl> ctls;
+    if (!ctx->query.prepared) return fail(ctx, CFPQ_ERR_NOT_READY, "no run");
+    if (ctx->exec.read_ctls(ctx->stream, &ctls, nullptr)) return fail(ctx, CFPQ_ERR_CUDA, "reading loop state failed");
+    fill_stats(stats, ctls[0], ctx->query, 0.0);
+    return CFPQ_OK;
+    API_CATCH(ctx)
+}
+
+// ---------------------------------------------------------------------------
 // Batched index creation.
 // ---------------------------------------------------------------------------
 extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_query *queries,

@@ -34,6 +34,10 @@ struct cfpq_ctx {
     std::vector<uint64_t> start_bits;
     bool has_start = false;
     uint32_t start_B = 0, start_n = 0;
+    // column sharding (cfpq_shard_*): this rank's output columns [c0, c1)
+    bool shard_on = false;
+    uint32_t shard_c0 = 0, shard_c1 = 0;
+    DBuf shard_cnt;  // per box: new edges, new to this rank (k_shard_apply)
     // batch
     std::vector<std::unique_ptr<GraphDev>> bgraphs;
     std::vector<std::unique_ptr<QueryDev>> bqueries;

@@ -30,6 +30,7 @@ constexpr uint32_t kModeNew = 0;   // FIRST pass of a level
 constexpr uint32_t kModeProp = 1;  // REPEAT pass of a cyclic level
 constexpr uint32_t kPhaseRun = 0;
 constexpr uint32_t kPhaseDone = 1;
+constexpr uint32_t kPhasePause = 2;  // column sharding: iteration done, new edges not yet exchanged
 constexpr uint32_t kStatusOk = 0;
 constexpr uint32_t kStatusIterCap = 1;
 constexpr uint32_t kStatusRoundCap = 2;
@@ -76,6 +77,15 @@ struct QCtl {
     unsigned long long tile_kstages;  // K stages of those tiles run on the tensor cores (128 x 256 x 128 MACs each)
     unsigned long long rounds_total;
     unsigned long long rows_changed_total;  // summed over passes
+    // Column sharding (one query over several ranks): the closure is
+    // computed on the 128-bit column vectors [col_v0, col_v1) of every block
+    // only (all columns: 0, ~0), and with `shard` set the loop pauses after
+    // every iteration (kPhasePause) until the new edges of all ranks are
+    // installed; shard_new = this rank's new edges of that iteration.
+    uint32_t shard;
+    uint32_t col_v0, col_v1;
+    uint32_t pad4;
+    unsigned long long shard_new;
 };
 
 // One source of an output block C[s,t]: a transition s -l-> u with t = u or

@@ -78,6 +78,14 @@ cudaError_t launch_nonempty_bits(const uint32_t *off, uint32_t n, uint32_t n_ter
 cudaError_t launch_copy_rows(const uint64_t *const *ptrs, const uint32_t *rows, uint32_t njobs, uint32_t W,
                              uint64_t *out, cudaStream_t st);
 
+// ---- column sharding (cfpq_shard.cu) ----
+cudaError_t launch_shard_setup(QCtl *ctl, uint32_t v0, uint32_t v1, cudaStream_t st);
+cudaError_t launch_shard_export(const uint64_t *a2, const uint32_t *a2_it, uint32_t n, uint32_t W, uint32_t B,
+                                uint32_t w0, uint32_t w1, uint32_t iter, uint64_t *out, cudaStream_t st);
+cudaError_t launch_shard_apply(const uint64_t *full, uint64_t *m2, uint64_t *a2, uint32_t *a2_it, uint32_t n,
+                               uint32_t W, uint32_t B, uint32_t iter, unsigned long long *cnt, QCtl *ctl,
+                               uint32_t *box_new_it, cudaStream_t st);
+
 // ---- single-CTA fixpoint (cfpq_small.cu) ----
 struct SmallSrc;
 size_t small_smem_bytes(uint32_t n, uint32_t W, uint32_t B, uint32_t nblk);

@@ -291,6 +291,18 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
     const int lpr = (int)it.lpr, grp = lane / lpr, gl = lane % lpr, rpw = 32 / lpr;
     const unsigned gmask = (lpr == 32 ? FULLMASK : ((1u << lpr) - 1u)) << (grp * lpr);
     const uint32_t W = it.W, nvec = W / 2;
+    // the columns of the output this rank computes (column sharding; else
+    // all): closure rows are read and written only there
+    // (bit j of winmask: the lane's vector j lies in [col_v0, col_v1) and in the row)
+    uint32_t winmask = 0u;
+    {
+        const uint32_t cv0 = c->col_v0, cv1 = min(c->col_v1, nvec);
+#pragma unroll
+        for (int j = 0; j < VPL; ++j) {
+            const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
+            if (v >= cv0 && v < cv1) winmask |= 1u << j;
+        }
+    }
     // column slice of the nonterminal adjacency (general variant, rows of 2+
     // vectors per lane: the engine slices only rows of 8192+ bits)
     constexpr bool kSlices = NT && VPL >= 2;
@@ -380,7 +392,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
 #pragma unroll
                                     for (int j = 0; j < VPL; ++j) {
                                         const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
-                                        cp_async16(&sl[j * 32 + lane], r + (v < nvec ? v : 0u), v < nvec);
+                                        cp_async16(&sl[j * 32 + lane], r + (((winmask >> j) & 1u) ? v : 0u), ((winmask >> j) & 1u));
                                     }
                                     if (gl == 0) ++my_ors;
                                     vmask |= 1u << sidx;
@@ -437,7 +449,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
 #pragma unroll
                                 for (int j = 0; j < VPL; ++j) {
                                     const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
-                                    rv[u][j] = (hs[u] && v < nvec) ? r[v] : make_uint4(0, 0, 0, 0);
+                                    rv[u][j] = (hs[u] && ((winmask >> j) & 1u)) ? r[v] : make_uint4(0, 0, 0, 0);
                                 }
                             }
 #pragma unroll
@@ -484,8 +496,8 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
 #pragma unroll
                                 for (int j = 0; j < VPL; ++j) {
                                     const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
-                                    a0[j] = (k0 && v < nvec) ? r0[v] : make_uint4(0, 0, 0, 0);
-                                    a1[j] = (k1 && v < nvec) ? r1[v] : make_uint4(0, 0, 0, 0);
+                                    a0[j] = (k0 && ((winmask >> j) & 1u)) ? r0[v] : make_uint4(0, 0, 0, 0);
+                                    a1[j] = (k1 && ((winmask >> j) & 1u)) ? r1[v] : make_uint4(0, 0, 0, 0);
                                 }
 #pragma unroll
                                 for (int j = 0; j < VPL; ++j) {
@@ -564,7 +576,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
 #pragma unroll
             for (int j = 0; j < VPL; ++j) {
                 const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
-                if (v < nvec && nz4(acc[j])) {
+                if (((winmask >> j) & 1u) && nz4(acc[j])) {
                     const unsigned long long lo = ((unsigned long long)acc[j].y << 32) | acc[j].x;
                     const unsigned long long hi = ((unsigned long long)acc[j].w << 32) | acc[j].z;
                     if (lo && (lo & ~atomicOr(o + 2u * v, lo))) ch = true;
@@ -576,7 +588,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
 #pragma unroll
             for (int j = 0; j < VPL; ++j) {
                 const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
-                if (v < nvec && nz4(acc[j])) {
+                if (((winmask >> j) & 1u) && nz4(acc[j])) {
                     const uint4 old = o[v];
                     const uint4 nw = andnot4(acc[j], old);
                     if (nz4(nw)) {
@@ -662,6 +674,7 @@ __global__ void __launch_bounds__(256) k_extract(const XItem *__restrict__ items
     const int lpr = (int)it.lpr, grp = lane / lpr, gl = lane % lpr, rpw = 32 / lpr;
     const unsigned gmask = (lpr == 32 ? FULLMASK : ((1u << lpr) - 1u)) << (grp * lpr);
     const uint32_t W = it.W, nvec = W / 2;
+    const uint32_t cv0 = c->col_v0, cv1 = min(c->col_v1, nvec);  // this rank's columns (all unless sharded)
     uint32_t my_new = 0;
     for (uint32_t rbase = it.row0 + (uint32_t)(warp * rpw); rbase < it.row1; rbase += 8u * rpw) {
         const uint32_t row = rbase + grp;
@@ -678,7 +691,7 @@ __global__ void __launch_bounds__(256) k_extract(const XItem *__restrict__ items
 #pragma unroll
             for (int j = 0; j < VPL; ++j) {
                 const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
-                if (v < nvec) or4(acc[j], r[v]);
+                if (v >= cv0 && v < cv1) or4(acc[j], r[v]);
             }
         }
         bool has = false;
@@ -687,7 +700,7 @@ __global__ void __launch_bounds__(256) k_extract(const XItem *__restrict__ items
 #pragma unroll
             for (int j = 0; j < VPL; ++j) {
                 const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
-                if (v < nvec) {
+                if (v >= cv0 && v < cv1) {
                     acc[j] = andnot4(acc[j], m[v]);
                     if (nz4(acc[j])) has = true;
                 }
@@ -700,7 +713,7 @@ __global__ void __launch_bounds__(256) k_extract(const XItem *__restrict__ items
 #pragma unroll
             for (int j = 0; j < VPL; ++j) {
                 const uint32_t v = (uint32_t)gl + (uint32_t)j * lpr;
-                if (v < nvec) {
+                if (v >= cv0 && v < cv1) {
                     a[v] = acc[j];
                     if (nz4(acc[j])) {
                         uint4 mm = m[v];
@@ -788,7 +801,19 @@ __device__ void control_body(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaG
                 for (uint32_t b = 0; b < c.n_boxes; ++b)
                     if (((c.nt_read_mask >> b) & 1ull) && c.box_new_it[b] == c.iter + 1u) read_new = true;
             }
-            if (c.new_edges == 0ull) {
+            if (c.shard) {
+                // column sharding: whether the loop goes on depends on every
+                // rank's new edges; pause at the next iteration's start until
+                // they are installed (k_shard_apply, k_shard_finish)
+                c.shard_new = c.new_edges;
+                c.iter += 1;
+                c.g += 1;
+                c.level = 0;
+                c.mode = kModeNew;
+                c.g_iter_start = c.g;
+                c.rounds_in_iter = 0;
+                c.phase = kPhasePause;
+            } else if (c.new_edges == 0ull) {
                 c.phase = kPhaseDone;
             } else if (c.max_iter && c.iter >= c.max_iter) {
                 c.status = kStatusIterCap;
@@ -921,6 +946,8 @@ __global__ void k_ctl_reset(QCtl *const *ctls, uint32_t nq, uint32_t max_iter, u
         c.mode = kModeNew;
         c.phase = kPhaseRun;
         c.g_iter_start = 2;
+        c.col_v0 = 0u;
+        c.col_v1 = 0xFFFFFFFFu;
         c.max_iter = max_iter;
         c.max_rounds = max_rounds;
         c.max_passes = max_passes;

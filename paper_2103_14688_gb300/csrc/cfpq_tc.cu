@@ -225,6 +225,16 @@ struct KDim {
     bool compact;
 };
 
+// Output columns [*c0, *c1) the job may write (column sharding; else all).
+__device__ __forceinline__ void job_window(const TcJob &J, uint32_t *c0, uint32_t *c1) {
+    *c0 = 0u;
+    *c1 = 0xFFFFFFFFu;
+    if (J.ctl) {
+        *c0 = J.ctl->col_v0 * 128u;
+        *c1 = J.ctl->col_v1 >= 0x01000000u ? 0xFFFFFFFFu : J.ctl->col_v1 * 128u;
+    }
+}
+
 // A channel-1 job (covers_new) is always compacted, and runs (kdim > 0)
 // only when new_tiles_pay: otherwise the row gather ORs the new edges' rows.
 __device__ __forceinline__ KDim job_kdim(const TcJob &J, uint32_t g) {
@@ -304,6 +314,9 @@ __global__ void __launch_bounds__(tc::kThreads, 2)
             continue;
         }
         const uint32_t m0 = (t / J.tiles_n) * kBM, n0 = (t % J.tiles_n) * kBN;
+        uint32_t wc0, wc1;
+        job_window(J, &wc0, &wc1);
+        if (n0 < wc0 || n0 >= wc1) continue;  // another rank's columns (uniform over the CTA)
         const uint32_t n = J.n, W = J.W;
         const uint32_t kwords = (K.kdim + 63u) >> 6;
         if (tid < kBM) s_row_changed[tid] = 0;
@@ -662,8 +675,11 @@ __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, E
             const uint32_t units = kchunks * zchunks;
             const uint32_t first = (blockIdx.x + gridDim.x - (u0 % gridDim.x)) % gridDim.x;
             u0 += units;
+            uint32_t wc0, wc1;
+            job_window(J, &wc0, &wc1);
             for (uint32_t u = first; u < units; u += gridDim.x) {
                 const uint32_t k0 = (u / zchunks) * 128u, w0 = (u % zchunks) * 4u;
+                if (w0 * 64u < wc0 || w0 * 64u >= wc1) continue;  // another rank's columns (uniform over the CTA)
                 __syncthreads();  // the previous unit's reads of s_bits are done
                 {
                     const uint32_t i = (uint32_t)tid >> 1, h = ((uint32_t)tid & 1u) * 2u;
@@ -752,6 +768,7 @@ struct JobCache {
     const TcJob *J = nullptr;
     uint32_t li0 = 1u, li1 = 0u;  // live-tile indices of the job: [li0, li1)
     uint32_t ks = 0, g = 0, mlim = 0;
+    uint32_t c0 = 0, c1 = 0;      // output columns of this rank (column sharding)
     bool ok = false;
 };
 
@@ -763,14 +780,20 @@ __device__ __forceinline__ bool next_tile(const TcJob *jobs, const ExecTables &T
                 li += ((jc.li1 - 1u - li) / gridDim.x) * gridDim.x;
                 continue;
             }
-            const uint32_t t = li - jc.li0;
-            tl.m0 = (t / jc.J->tiles_n) * 128u;
-            if (tl.m0 >= jc.mlim) {  // past a channel-1 job's rows: the rest of the job too
+            // Column-major tile order: CTAs running side by side share the
+            // B tile (256 columns x K) and each reads its own A tile (128
+            // rows x K), half the operand bytes of the row-major order when
+            // the operands do not fit L2.  A channel-1 job walks only the
+            // tile rows its row list fills.
+            const uint32_t t = li - jc.li0, mt = (jc.mlim + 127u) / 128u;
+            if (t >= mt * jc.J->tiles_n) {  // past a channel-1 job's rows: the rest of the job too
                 li += ((jc.li1 - 1u - li) / gridDim.x) * gridDim.x;
                 continue;
             }
+            tl.m0 = (t % mt) * 128u;
+            tl.n0 = (t / mt) * 256u;
+            if (tl.n0 < jc.c0 || tl.n0 >= jc.c1) continue;  // another rank's columns
             tl.J = jc.J;
-            tl.n0 = (t % jc.J->tiles_n) * 256u;
             tl.ks = jc.ks;
             tl.g = jc.g;
             tl.mlim = jc.mlim;
@@ -801,6 +824,7 @@ __device__ __forceinline__ bool next_tile(const TcJob *jobs, const ExecTables &T
         jc.ks = (K.kdim + 127u) / 128u;
         jc.g = g;
         jc.mlim = ok && J.covers_new ? (uint32_t)*J.mcount : J.n;
+        job_window(J, &jc.c0, &jc.c1);
         li -= gridDim.x;  // re-enter through the cache
     }
     return false;

@@ -136,7 +136,9 @@ def all_gather_columns(local, ranges: Sequence[Tuple[int, int]], dist):
 
 def run_column_sharded(engine, rank: int, world: int, dist=None, exchange=None) -> int:
     """Index creation of one query on this rank's columns, exchanging every
-    iteration's new edges with the other ranks; returns the iterations run.
+    iteration's new edges with the other ranks; returns the exchange steps
+    (the iterations run; an engine may count one more that it can tell
+    would add nothing).
 
     ``engine`` is this rank's closure: ``n``, ``begin(col0, col1)``,
     ``step()`` (one iteration of Listing 1 on the columns: the new edges of
@@ -164,7 +166,7 @@ def run_column_sharded(engine, rank: int, world: int, dist=None, exchange=None) 
 def run_column_sharded_lockstep(engines: Sequence) -> int:
     """The same protocol with every rank's engine in this process (ranks run
     one after another within an iteration; nothing waits on another rank's
-    kernels): the all-gather is a concatenation."""
+    kernels): the all-gather is a concatenation.  Returns the steps."""
     world = len(engines)
     ranges = column_ranges(engines[0].n, world)
     for e, (c0, c1) in zip(engines, ranges):
