@@ -876,7 +876,7 @@ def run_other(args):
     elif args.workload == "served":
         out = []
         for lam in [float(x) for x in args.lambdas.split(",")]:
-            wl = W.serving_workload(lam=lam, n_queries=100000, horizon_s=args.horizon)
+            wl = W.serving_workload(lam=lam, n_queries=args.served_queries, horizon_s=args.horizon)
             srv = cfpq.Server(wl.graph)
             t_start = time.perf_counter()
             pending = list(zip(wl.arrivals.tolist(), wl.choice.tolist()))
@@ -902,7 +902,7 @@ def run_other(args):
                         "admission_waits": waits})
             srv.close()
         # the same pool of queries one at a time on the same resident graph
-        wl = W.serving_workload(lam=100.0, n_queries=100000, horizon_s=args.horizon)
+        wl = W.serving_workload(lam=100.0, n_queries=args.served_queries, horizon_s=args.horizon)
         solo = cfpq.Context()
         solo.load_graph(wl.graph)
         k = min(200, len(wl.choice))
@@ -984,7 +984,8 @@ def main():
     ap.add_argument("--served-lambda", type=float, default=100.0, help="default line: served probe arrival rate")
     ap.add_argument("--served-horizon", type=float, default=3.0, help="default line: served probe seconds")
     ap.add_argument("--lambdas", default="10,30,100,300,1000")
-    ap.add_argument("--horizon", type=float, default=5.0)
+    ap.add_argument("--horizon", type=float, default=60.0, help="served workload: seconds of arrivals per lambda")
+    ap.add_argument("--served-queries", type=int, default=2000, help="served workload: arrivals per lambda (cap)")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--loop", default="device", choices=["device", "host"],
                     help="dyck_modes workload: fixpoint loop in a CUDA graph (device) or one launch per pass (host)")

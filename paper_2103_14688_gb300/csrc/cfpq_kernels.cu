@@ -231,7 +231,12 @@ template <int VPL, bool NT>
 struct GatherDyn {
     static constexpr bool on = NT && VPL >= 4;
 };
-constexpr uint32_t kGatherParts = 4;
+// Units per item: measured on Dyck-4 (AUTO / bit-packed, ms) at n = 65536:
+// 4: 1545 / 2707, 8: 1543 / 2589, 16: 1560 / 2564, 32: 1585 / 2531; at
+// n = 16384: 4: 58 / 84, 8: 50 / 71, 32: 50 / 62.  (Leaving rows with more
+// than 256-4096 bits to enumerate to a second launch split over 16 warps
+// gained 1-2% in AUTO and cost 10-20% bit-packed: not kept.)
+constexpr uint32_t kGatherParts = 8;
 
 template <int VPL, bool NT>
 __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
