@@ -717,12 +717,11 @@ __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, E
 
 // ---------------------------------------------------------------------------
 // TMA-fed product of the compacted jobs.  Warp 0 (one lane) streams the FP8
-// operand tiles of every K stage into a ring of kRing shared-memory stages
-// with cp.async.bulk.tensor (128-byte swizzle); warp 1 (one lane) issues the
-// tcgen05 MMAs into one of two TMEM accumulators and commits each stage back
-// to the producer; warps 2-5 read a finished accumulator (each its TMEM lane
-// quarter), threshold it and OR the bits into the output block while the
-// next tile accumulates in the other half of TMEM.
+// operand tiles of every K stage into a ring of shared-memory stages with
+// cp.async.bulk.tensor (128-byte swizzle); warp 1 (one lane) issues the
+// tcgen05 MMAs into TMEM and commits each stage back to the producer; warps
+// 2-9 read a finished accumulator (each its TMEM lane quarter and column
+// half), threshold it and OR the bits into the output block.
 // ---------------------------------------------------------------------------
 namespace tc2 {
 constexpr int kRing = 4;
@@ -772,6 +771,7 @@ struct JobCache {
     bool ok = false;
 };
 
+template <uint32_t ROWS>  // output rows per tile: 128, or 256 (two accumulators, PAIR)
 __device__ __forceinline__ bool next_tile(const TcJob *jobs, const ExecTables &T, uint32_t total, uint32_t &li,
                                           Tile &tl, JobCache &jc) {
     for (; li < total; li += gridDim.x) {
@@ -785,12 +785,12 @@ __device__ __forceinline__ bool next_tile(const TcJob *jobs, const ExecTables &T
             // rows x K), half the operand bytes of the row-major order when
             // the operands do not fit L2.  A channel-1 job walks only the
             // tile rows its row list fills.
-            const uint32_t t = li - jc.li0, mt = (jc.mlim + 127u) / 128u;
-            if (t >= mt * jc.J->tiles_n) {  // past a channel-1 job's rows: the rest of the job too
+            const uint32_t t = li - jc.li0, mt = (jc.mlim + ROWS - 1u) / ROWS;
+            if (t >= mt * jc.J->tiles_n) {  // past the job's row tiles: the rest of the job too
                 li += ((jc.li1 - 1u - li) / gridDim.x) * gridDim.x;
                 continue;
             }
-            tl.m0 = (t % mt) * 128u;
+            tl.m0 = (t % mt) * ROWS;
             tl.n0 = (t / mt) * 256u;
             if (tl.n0 < jc.c0 || tl.n0 >= jc.c1) continue;  // another rank's columns
             tl.J = jc.J;
@@ -831,11 +831,22 @@ __device__ __forceinline__ bool next_tile(const TcJob *jobs, const ExecTables &T
 }
 }  // namespace tc2
 
+// PAIR: each CTA computes 256 output rows (two 128-row A tiles against one
+// B tile per K stage, two TMEM accumulators of 256 columns, so no second
+// buffer): 64 KiB of operands per stage feed twice the multiply-adds of the
+// 48 KiB stage of the single tile, and three stages in flight hold as much
+// work as six of those.
+template <bool PAIR>
 __global__ void __launch_bounds__(tc2::kThreads, 1)
     k_tc_product_tma(const TcJob *__restrict__ jobs, const unsigned char *__restrict__ maps, ExecTables T,
                      int *err_flag) {
     using namespace tc;
     using namespace tc2;
+    constexpr uint32_t kRows = PAIR ? 256u : 128u;
+    constexpr int kRingN = PAIR ? 3 : kRing;
+    constexpr uint32_t kStageN = (PAIR ? 2u : 1u) * kABytes + kBBytes;
+    constexpr uint32_t kBufs = PAIR ? 1u : 2u;  // accumulator buffers (each 256 columns per 128 rows)
+    static_assert(kRingN * kStageN <= kRing * kStage, "stages exceed the shared memory of the launch");
     extern __shared__ __align__(1024) unsigned char smem_raw2[];
     __shared__ uint64_t full[kRing], empty[kRing], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base;
@@ -847,7 +858,7 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
         (reinterpret_cast<uintptr_t>(smem_raw2) + 1023u) & ~static_cast<uintptr_t>(1023u));
     if (warp == 0) tmem_alloc(&tmem_base, tc2::kTmemCols);
     if (tid == 0) {
-        for (int i = 0; i < kRing; ++i) {
+        for (int i = 0; i < kRingN; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
@@ -869,15 +880,16 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
             uint32_t stage = 0, ph = 0, li = blockIdx.x;
             Tile tl;
             JobCache jc;
-            while (!to && next_tile(jobs, T, total, li, tl, jc)) {
+            while (!to && next_tile<kRows>(jobs, T, total, li, tl, jc)) {
                 const unsigned char *ma = maps + (size_t)tl.J->map * 2u * 128u, *mb = ma + 128;
                 for (uint32_t k = 0; k < tl.ks; ++k) {
                     if (!mbar_wait(&empty[stage], ph ^ 1u)) { to = true; break; }
-                    unsigned char *sa = base + (size_t)stage * kStage, *sb = sa + kABytes;
-                    arrive_expect_tx(&full[stage], kStage);
+                    unsigned char *sa = base + (size_t)stage * kStageN, *sb = sa + (PAIR ? 2u : 1u) * kABytes;
+                    arrive_expect_tx(&full[stage], kStageN);
                     tma_load(sa, ma, (int32_t)(k * 128u), (int32_t)tl.m0, &full[stage]);
+                    if (PAIR) tma_load(sa + kABytes, ma, (int32_t)(k * 128u), (int32_t)(tl.m0 + 128u), &full[stage]);
                     tma_load(sb, mb, (int32_t)(k * 128u), (int32_t)tl.n0, &full[stage]);
-                    if (++stage == (uint32_t)kRing) { stage = 0; ph ^= 1u; }
+                    if (++stage == (uint32_t)kRingN) { stage = 0; ph ^= 1u; }
                 }
                 li += gridDim.x;
             }
@@ -887,80 +899,94 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
             uint32_t stage = 0, ph = 0, acc = 0, aph = 0, li = blockIdx.x;
             Tile tl;
             JobCache jc;
-            while (!to && next_tile(jobs, T, total, li, tl, jc)) {
+            while (!to && next_tile<kRows>(jobs, T, total, li, tl, jc)) {
                 if (!mbar_wait(&tempty[acc], aph ^ 1u)) { to = true; break; }
                 tc_after();
                 const uint32_t d = tmem + acc * 256u;
                 for (uint32_t k = 0; k < tl.ks; ++k) {
                     if (!mbar_wait(&full[stage], ph)) { to = true; break; }
                     tc_after();
-                    const uint32_t sa = smem_u32(base + (size_t)stage * kStage), sb = sa + kABytes;
+                    const uint32_t sa = smem_u32(base + (size_t)stage * kStageN);
+                    const uint32_t sb = sa + (PAIR ? 2u : 1u) * kABytes;
 #pragma unroll
-                    for (uint32_t kk = 0; kk < 4; ++kk)
-                        tc::mma(false, d, desc_sw128(sa + kk * 32u), desc_sw128(sb + kk * 32u), idesc,
-                                (k > 0 || kk > 0) ? 1u : 0u);
+                    for (uint32_t kk = 0; kk < 4; ++kk) {
+                        const uint32_t accum = (k > 0 || kk > 0) ? 1u : 0u;
+                        tc::mma(false, d, desc_sw128(sa + kk * 32u), desc_sw128(sb + kk * 32u), idesc, accum);
+                        if (PAIR)  // rows m0 + 128 .. into the second accumulator
+                            tc::mma(false, d + 256u, desc_sw128(sa + kABytes + kk * 32u), desc_sw128(sb + kk * 32u),
+                                    idesc, accum);
+                    }
                     mma_commit(&empty[stage]);  // the stage is free once these MMAs have read it
-                    if (++stage == (uint32_t)kRing) { stage = 0; ph ^= 1u; }
+                    if (++stage == (uint32_t)kRingN) { stage = 0; ph ^= 1u; }
                 }
                 if (to) break;
                 mma_commit(&tfull[acc]);
                 QCtl *cw = tl.J->ctl;
-                if (cw) {
-                    atomicAdd(&cw->tile_mmas, 1ull);
-                    atomicAdd(&cw->tile_kstages, (unsigned long long)tl.ks);
+                if (cw) {  // counted in 128 x 256 tiles
+                    atomicAdd(&cw->tile_mmas, PAIR ? 2ull : 1ull);
+                    atomicAdd(&cw->tile_kstages, (unsigned long long)tl.ks * (PAIR ? 2ull : 1ull));
                 }
-                if (++acc == 2u) { acc = 0; aph ^= 1u; }
+                if (++acc == kBufs) { acc = 0; aph ^= 1u; }
                 li += gridDim.x;
             }
         }
     } else {  // epilogue: warps 2-9; TMEM lanes 32 * (warp % 4) ..., columns half * 128 ...
         const uint32_t quarter = (uint32_t)warp & 3u, half = (uint32_t)(warp - 2) >> 2;
+        constexpr int kHalves = PAIR ? 2 : 1;  // 128-row halves of the tile
         uint32_t acc = 0, aph = 0, li = blockIdx.x;
         Tile tl;
         JobCache jc;
-        while (!to && next_tile(jobs, T, total, li, tl, jc)) {
+        while (!to && next_tile<kRows>(jobs, T, total, li, tl, jc)) {
             if (!mbar_wait(&tfull[acc], aph)) { to = true; }
             if (__any_sync(0xffffffffu, to)) { to = true; break; }
             tc_after();
             const TcJob &J = *tl.J;
-            // output row: tile row m0 + r, through xs for a channel-1 job
-            const uint32_t r = quarter * 32u + (uint32_t)lane, mr = tl.m0 + r;
-            const uint32_t x = mr >= tl.mlim ? J.n : (J.covers_new ? J.xs[mr] : mr);
-            uint32_t mask[4];
+            uint32_t mask[kHalves][4];
+#pragma unroll
+            for (int hh = 0; hh < kHalves; ++hh) {
 #pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
-                uint32_t v[32];
-                tmem_ld32(tmem + acc * 256u + half * 128u + 32u * (uint32_t)c + ((quarter * 32u) << 16), v);
-                uint32_t mb = 0u;
+                for (int c = 0; c < 4; ++c) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + acc * 256u + (uint32_t)hh * 256u + half * 128u + 32u * (uint32_t)c +
+                                  ((quarter * 32u) << 16),
+                              v);
+                    uint32_t mb = 0u;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) mb |= (v[i] != 0u ? 1u : 0u) << i;
+                    for (int i = 0; i < 32; ++i) mb |= (v[i] != 0u ? 1u : 0u) << i;
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc)
-                    if (cc == c) mask[cc] = mb;
+                    for (int cc = 0; cc < 4; ++cc)
+                        if (cc == c) mask[hh][cc] = mb;
+                }
             }
             tc_before();
             __syncwarp();
-            if (lane == 0) arrive(&tempty[acc]);  // the accumulator may be overwritten
-            bool ch = false;
-            if (x < J.n) {
-                const uint32_t w0 = (tl.n0 >> 6) + half * 2u;
+            if (lane == 0) arrive(&tempty[acc]);  // the accumulators may be overwritten
 #pragma unroll
-                for (int w = 0; w < 2; ++w) {
-                    const uint32_t ww = w0 + (uint32_t)w;
-                    const uint64_t add = (uint64_t)mask[2 * w] | ((uint64_t)mask[2 * w + 1] << 32);
-                    if (ww >= J.W || !add) continue;
-                    const uint64_t old = atomicOr(reinterpret_cast<unsigned long long *>(J.out + (size_t)x * J.W + ww),
-                                                  (unsigned long long)add);
-                    if (add & ~old) ch = true;
+            for (int hh = 0; hh < kHalves; ++hh) {
+                // output row: tile row m0 + 128 hh + r, through xs for a channel-1 job
+                const uint32_t r = quarter * 32u + (uint32_t)lane, mr = tl.m0 + 128u * (uint32_t)hh + r;
+                const uint32_t x = mr >= tl.mlim ? J.n : (J.covers_new ? J.xs[mr] : mr);
+                bool ch = false;
+                if (x < J.n) {
+                    const uint32_t w0 = (tl.n0 >> 6) + half * 2u;
+#pragma unroll
+                    for (int w = 0; w < 2; ++w) {
+                        const uint32_t ww = w0 + (uint32_t)w;
+                        const uint64_t add = (uint64_t)mask[hh][2 * w] | ((uint64_t)mask[hh][2 * w + 1] << 32);
+                        if (ww >= J.W || !add) continue;
+                        const uint64_t old = atomicOr(
+                            reinterpret_cast<unsigned long long *>(J.out + (size_t)x * J.W + ww), (unsigned long long)add);
+                        if (add & ~old) ch = true;
+                    }
+                }
+                if (ch && J.out_stamp) J.out_stamp[x] = tl.g;  // both column halves may stamp: same value
+                const unsigned chb = __ballot_sync(0xffffffffu, ch);
+                if (lane == 0 && chb) {
+                    if (J.out_last) *J.out_last = tl.g;
+                    if (J.ctl) atomicAdd(&J.ctl->changed_rows, (unsigned long long)__popc(chb));
                 }
             }
-            if (ch && J.out_stamp) J.out_stamp[x] = tl.g;  // both halves may stamp: same value
-            const unsigned chb = __ballot_sync(0xffffffffu, ch);
-            if (lane == 0 && chb) {
-                if (J.out_last) *J.out_last = tl.g;
-                if (J.ctl) atomicAdd(&J.ctl->changed_rows, (unsigned long long)__popc(chb));
-            }
-            if (++acc == 2u) { acc = 0; aph ^= 1u; }
+            if (++acc == kBufs) { acc = 0; aph ^= 1u; }
             li += gridDim.x;
         }
     }
@@ -970,6 +996,11 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
     tc_after();
     if (warp == 0) tmem_dealloc(tmem, tc2::kTmemCols);
 }
+
+// 256-row tiles (two accumulators) in the TMA-fed products: Dyck-4 n = 65536
+// tile products 852 -> 762 ms, the query 1.49 -> 1.41 s (128-row tiles with
+// double-buffered accumulators: the kernel with PAIR = false).
+constexpr bool kTilePair = true;
 
 static int g_tc_sms[64];
 
@@ -992,7 +1023,7 @@ cudaError_t prepare_tc_launch() {
     e = cudaFuncSetAttribute(k_tc_a8, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kColMaxW * 8u * (256u / 32u)));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_product_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_tc_product_tma<kTilePair>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(tc2::kRing * tc2::kStage + 1024u));
     if (e != cudaSuccess) return e;
     int sms = 0;
@@ -1046,7 +1077,7 @@ cudaError_t launch_tc_product_tma(const TcJob *jobs, const void *maps, uint32_t 
     if (!sms) return cudaErrorNotReady;  // prepare_tc_launch was not called
     uint32_t grid = (uint32_t)sms;  // one CTA per SM: the ring and both accumulators fill it
     if (max_tiles < grid) grid = max_tiles;
-    k_tc_product_tma<<<grid, tc2::kThreads, tc2::kRing * tc2::kStage + 1024u, st>>>(
+    k_tc_product_tma<kTilePair><<<grid, tc2::kThreads, tc2::kRing * tc2::kStage + 1024u, st>>>(
         jobs, static_cast<const unsigned char *>(maps), T, err_flag);
     return cudaGetLastError();
 }
