@@ -319,6 +319,12 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
     }
     const bool sliced = slices_on && (sv0 != 0u || sv1 < nvec);
     uint32_t my_changed = 0, my_ors = 0;
+    // channels of the item's first 16 sources in this pass (4 bits each): the
+    // same for every row of the unit
+    unsigned long long chpack = 0ull;
+    if constexpr (NT)
+        for (uint32_t k = 0; k < it.nsrc && k < 16u; ++k)
+            chpack |= (unsigned long long)src_channels<NT>(srcs[it.src0 + k], mode, iter, g, g0, dmask) << (4u * k);
 
     // rows of this warp: the unit's range of rpw-row steps (dynamic), or
     // every eighth step of the item (one CTA per item)
@@ -340,8 +346,14 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
         for (int j = 0; j < VPL; ++j) acc[j] = make_uint4(0, 0, 0, 0);
 
         for (uint32_t k = 0; k < it.nsrc; ++k) {
+            uint32_t chans;
+            if constexpr (NT)
+                chans = k < 16u ? (uint32_t)(chpack >> (4u * k)) & 15u
+                                : src_channels<NT>(srcs[it.src0 + k], mode, iter, g, g0, dmask);
+            else
+                chans = src_channels<NT>(srcs[it.src0 + k], mode, iter, g, g0, dmask);
+            if (!chans) continue;  // the source takes no part in this pass
             const SrcDesc d = srcs[it.src0 + k];
-            const uint32_t chans = src_channels<NT>(d, mode, iter, g, g0, dmask);
             // closure rows read by this source (none when the tiles OR them:
             // only the product edges themselves are left here)
             const uint64_t *const rblk = (NT && (chans & 8u)) ? nullptr : d.rblk;
@@ -525,6 +537,8 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                     bool rowok;
                     if (new_edges) { adj = d.nt_new; rowok = valid && d.nt_new_it[row] == iter; }
                     else { adj = d.nt_all; rowok = valid; }
+                    // no row of the warp has edges of this channel: nothing to enumerate
+                    if (!__any_sync(FULLMASK, rowok)) continue;
                     uint4 a[VPL];
 #pragma unroll
                     for (int j = 0; j < VPL; ++j) {
