@@ -143,9 +143,11 @@ struct GItem {
     // in 128-bit vectors: [slice & 0xFFFF, slice >> 16).  Items of one row
     // range with different slices share the output rows and merge them with
     // atomicOr; the CSR sources are taken by the slice that starts at 0.
-    // Slices take part only while a box in nt_boxes (the boxes read by the
-    // block's nonterminal sources) is dense (QCtl::dense_mask); otherwise the
-    // first slice covers every column and the others do nothing.
+    // Slices take part only while a box in nt_boxes (the boxes whose dense
+    // adjacency the block's gather enumerates into closure-row ORs: sources
+    // reading a closure block that is not pure-terminal, without a tile job)
+    // is dense (QCtl::dense_mask); otherwise the first slice covers every
+    // column and the others do nothing.
     uint32_t slice;
     uint32_t nt_boxes;
     uint32_t pad;

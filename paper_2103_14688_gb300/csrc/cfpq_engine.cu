@@ -588,10 +588,19 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                 // split over several items, so that rows with thousands of new
                 // edges (hubs) spread over several CTAs
                 const uint32_t nvec = q.W / 2u;
-                uint32_t nt_boxes = 0;  // boxes read by the block's nonterminal sources (first 32)
+                // Boxes (first 32) whose dense adjacency this block's row gather
+                // enumerates into OR-ed closure rows: nonterminal sources reading a
+                // closure block (not a pure-terminal one) with no tile job.  A hub
+                // row of such a box costs thousands of row ORs, which the column
+                // slices spread over several units.  (Measured on Dyck-4 n = 65536:
+                // slicing every block with a nonterminal source cost AUTO
+                // 1.22 -> 1.28 s with 4 slices and 1.46 s with 8, as the warp units
+                // already balance the lighter blocks.)
+                uint32_t nt_boxes = 0;
                 for (uint32_t k = 0; k < q.blk_nsrc[b]; ++k) {
                     const auto &sd = q.srcs[q.blk_src0[b] + k];
-                    if (sd.label_kind != 0 && sd.label < 32u) nt_boxes |= 1u << sd.label;
+                    if (sd.label_kind != 0 && sd.label < 32u && sd.rblk >= 0 && !sd.pure_rb && sd.tc_slot < 0)
+                        nt_boxes |= 1u << sd.label;
                 }
                 const bool sliceable = has_nt && q.W >= 128u && nt_boxes != 0u;
                 // 4 slices: measured on Dyck-4 n = 65536 (1: 2.93 s, 2: 2.56, 3: 2.53,

@@ -655,12 +655,14 @@ __global__ void __launch_bounds__(256) k_tc_a8(const TcJob *__restrict__ jobs, E
 }
 
 // b8[z][k] = B[ys[k]][z] as a 0/1 FP8 byte (B's listed rows transposed), for
-// z < n_pad and k below the next multiple of 128 of D.  Unit: 128 listed rows
-// x 256 columns; the rows' 256-bit slices are staged in shared memory and each
-// thread writes the 128 bytes of one column z.
+// the columns z of the rank's window below n_pad and k below the next
+// multiple of 128 of D.  Unit of a warp: 32 listed rows x 32 columns.  Lane l
+// loads the 32 bits of row ys[k0 + l] at those columns; 32 ballots transpose
+// them (ballot c = column z0 + c over the 32 rows, kept by lane c), and every
+// lane writes its column's 32 bytes.
 __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, ExecTables T) {
-    __shared__ uint64_t s_bits[128][4];
-    const int tid = threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     uint32_t u0 = 0;
     for (uint32_t q = 0; q < T.nq; ++q) {
         const uint32_t jb = T.t_job_beg[q], je = T.t_job_end[q];
@@ -671,45 +673,27 @@ __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, E
             if (!tc_job_active(J, &thr, &iter, &g)) continue;
             const KDim K = job_kdim(J, g);
             if (!K.compact || K.kdim == 0u) continue;
-            const uint32_t D = K.kdim, kchunks = (D + 127u) / 128u, W = J.W, zchunks = (W * 64u + 255u) / 256u;
-            const uint32_t units = kchunks * zchunks;
-            const uint32_t first = (blockIdx.x + gridDim.x - (u0 % gridDim.x)) % gridDim.x;
-            u0 += units;
             uint32_t wc0, wc1;
             job_window(J, &wc0, &wc1);
-            for (uint32_t u = first; u < units; u += gridDim.x) {
-                const uint32_t k0 = (u / zchunks) * 128u, w0 = (u % zchunks) * 4u;
-                if (w0 * 64u < wc0 || w0 * 64u >= wc1) continue;  // another rank's columns (uniform over the CTA)
-                __syncthreads();  // the previous unit's reads of s_bits are done
-                {
-                    const uint32_t i = (uint32_t)tid >> 1, h = ((uint32_t)tid & 1u) * 2u;
-                    const bool ok = k0 + i < D;
-                    const uint32_t y = ok ? J.ys[k0 + i] : 0u;
+            const uint32_t D = K.kdim, W = J.W, zend = min(W * 64u, wc1), zbeg = min(wc0, zend);
+            const uint32_t kchunks = ((D + 127u) & ~127u) / 32u, zchunks = (zend - zbeg) / 32u;
+            const uint32_t units = kchunks * zchunks;
+            const uint32_t first = (gw + nw - (u0 % nw)) % nw;
+            u0 += units;
+            for (uint32_t u = first; u < units; u += nw) {
+                const uint32_t k0 = (u / zchunks) * 32u, z0 = zbeg + (u % zchunks) * 32u;
+                const uint32_t k = k0 + (uint32_t)lane;
+                uint32_t bits = 0u;
+                if (k < D) bits = (uint32_t)(J.B[(size_t)J.ys[k] * W + (z0 >> 6)] >> (z0 & 63u));
+                uint32_t mine = 0u;
 #pragma unroll
-                    for (int t = 0; t < 2; ++t) {
-                        const uint32_t w = w0 + h + (uint32_t)t;
-                        s_bits[i][h + t] = (ok && w < W) ? J.B[(size_t)y * W + w] : 0ull;
-                    }
+                for (int c = 0; c < 32; ++c) {
+                    const uint32_t m = __ballot_sync(0xffffffffu, (bits >> c) & 1u);
+                    if (lane == c) mine = m;  // bit i: row ys[k0 + i] has column z0 + c
                 }
-                __syncthreads();
-                const uint32_t z = w0 * 64u + (uint32_t)tid;
-                if (z < W * 64u) {
-                    const int wi = tid >> 6, bi = tid & 63;
-                    uint4 *dst = reinterpret_cast<uint4 *>(J.b8 + (size_t)z * J.kcap + k0);
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        uint32_t v[4];
-#pragma unroll
-                        for (int qd = 0; qd < 4; ++qd) {
-                            uint32_t wv = 0u;
-#pragma unroll
-                            for (int b = 0; b < 4; ++b)
-                                if ((s_bits[c * 16 + qd * 4 + b][wi] >> bi) & 1ull) wv |= 0x38u << (8 * b);
-                            v[qd] = wv;
-                        }
-                        dst[c] = make_uint4(v[0], v[1], v[2], v[3]);
-                    }
-                }
+                uint4 *dst = reinterpret_cast<uint4 *>(J.b8 + (size_t)(z0 + (uint32_t)lane) * J.kcap + k0);
+                dst[0] = tc::expand16(mine & 0xFFFFu, 0x38u);
+                dst[1] = tc::expand16(mine >> 16, 0x38u);
             }
         }
     }
