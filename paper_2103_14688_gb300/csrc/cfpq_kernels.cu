@@ -123,35 +123,42 @@ struct GatherRing {
     static constexpr bool on = VPL >= 4;
     static constexpr int depth = VPL <= 8 ? 4 : 3;
     // narrower rows keep one row-sized slot per warp: the bitmap of
-    // pure-terminal reads (or_pure_rows_smem)
+    // pure-terminal reads (pure_bitmap_*)
     static constexpr int slots = on ? depth : 1;
     static constexpr size_t bytes = (size_t)8 * slots * 32 * VPL * 16;  // 8 warps
 };
 
 // The same for a warp that owns one row (lpr = 32, rows of 4+ vectors per
 // lane), with a row-sized shared-memory bitmap `bm` (uint4-aligned, the
-// vectors in row order): every lane sets the columns it finds with a shared
-// atomic -- no broadcast -- and the bitmap is ORed into the accumulators once.
+// vectors in row order): the bitmap is cleared once per row and source, every
+// lane sets the columns it finds with a shared atomic -- no broadcast -- for
+// every candidate of the enumeration, and the bitmap is ORed into the
+// accumulators once at the end.
 template <int VPL>
-__device__ __forceinline__ void or_pure_rows_smem(uint4 (&acc)[VPL], const SrcDesc &d, uint32_t y_l, bool keep_l,
-                                                  uint32_t nvec, int lane, uint4 *bm) {
+__device__ __forceinline__ void pure_bitmap_clear(uint32_t nvec, int lane, uint4 *bm) {
 #pragma unroll
     for (int j = 0; j < VPL; ++j) {
         const uint32_t v = (uint32_t)lane + 32u * (uint32_t)j;
         if (v < nvec) bm[v] = make_uint4(0, 0, 0, 0);
     }
     __syncwarp();
-    if (keep_l) {
-        unsigned int *w = reinterpret_cast<unsigned int *>(bm);
-        for (uint32_t p = 0; p < d.pure_n; ++p) {
-            const uint32_t *off = d.pure_off[p];
-            const uint32_t e1 = off[y_l + 1];
-            for (uint32_t e = off[y_l]; e < e1; ++e) {
-                const uint32_t z = d.pure_col[e];
-                atomicOr(w + (z >> 5), 1u << (z & 31u));
-            }
+}
+
+__device__ __forceinline__ void pure_bitmap_set(const SrcDesc &d, uint32_t y_l, bool keep_l, uint4 *bm) {
+    if (!keep_l) return;
+    unsigned int *w = reinterpret_cast<unsigned int *>(bm);
+    for (uint32_t p = 0; p < d.pure_n; ++p) {
+        const uint32_t *off = d.pure_off[p];
+        const uint32_t e1 = off[y_l + 1];
+        for (uint32_t e = off[y_l]; e < e1; ++e) {
+            const uint32_t z = d.pure_col[e];
+            atomicOr(w + (z >> 5), 1u << (z & 31u));
         }
     }
+}
+
+template <int VPL>
+__device__ __forceinline__ void pure_bitmap_or(uint4 (&acc)[VPL], uint32_t nvec, int lane, const uint4 *bm) {
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < VPL; ++j) {
@@ -376,7 +383,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                     if constexpr (NT) {
                         if (d.pure_n && !use_ident) {
                             if (lpr == 32) {  // one row per warp: the bitmap in the warp's first slot
-                                or_pure_rows_smem<VPL>(acc, d, y_l, keep, nvec, lane, ring);
+                                pure_bitmap_set(d, y_l, keep, ring);
                                 return;
                             }
                             or_pure_rows<VPL>(acc, d, y_l, keep, lpr, gl, grp, gmask);
@@ -568,6 +575,10 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                         for (int j = 0; j < VPL; ++j) or4(acc[j], a[j]);
                         if (rblk == nullptr) continue;
                     }
+                    // a pure-terminal block read by a warp-owned row: the
+                    // columns found go to the row's shared-memory bitmap
+                    const bool pure_bm = d.pure_n && !use_ident && lpr == 32;
+                    if (pure_bm) pure_bitmap_clear<VPL>(nvec, lane, ring);
                     // Each lane proposes the lowest set bit of its part of the
                     // adjacency row per step (ballot/ffs enumeration).
                     while (true) {
@@ -584,6 +595,7 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
                         if (!__any_sync(FULLMASK, has)) break;
                         take_batch(y, has);
                     }
+                    if (pure_bm) pure_bitmap_or<VPL>(acc, nvec, lane, ring);
                 }
             }
         }
