@@ -323,9 +323,10 @@ int QueryDev::plan(std::string *err) {
         // (channel 1, run when the tiles beat the gather: new_tiles_pay)
         sd.tc_slot_new = (sd.tc_slot >= 0 && sd.label_kind == 1 && !sd.same_level) ? (int32_t)n_tc_src++ : -1;
     }
-    // a context's query holds full-size slots (2 n^2 bytes each) only while
-    // there are few of them: 4 slots at n = 65536 are 34 GB
-    if (full_kcap && n_tc_src > 4u && W * 64u > 8192u) kcap = std::max<uint32_t>(128u, ((W * 32u) + 127u) & ~127u);
+    // a context's query holds full-size slots (2 n^2 bytes each) only up to
+    // 96 GiB of them (at n = 65536: 11 slots; Dyck-4 in TC_FP8 mode has 10)
+    if (full_kcap && W * 64u > 8192u && (uint64_t)n_tc_src * tc_slot_bytes() > (96ull << 30))
+        kcap = std::max<uint32_t>(128u, ((W * 32u) + 127u) & ~127u);
     // Extraction blocks: (q0_b, f) for f final in box b.
     fblocks.clear();
     box_f0.assign(B, 0);

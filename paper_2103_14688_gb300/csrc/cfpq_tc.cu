@@ -592,22 +592,51 @@ __global__ void __launch_bounds__(256) k_tc_newcols(const TcJob *__restrict__ jo
 // List the rows y of B with stamp >= thr; for a channel-1 job the columns
 // of its newcols (order irrelevant: the product sums over them).
 __global__ void __launch_bounds__(256) k_tc_rows(const TcJob *__restrict__ jobs, ExecTables T, int *err_flag) {
-    const int lane = threadIdx.x & 31;
+    // a unit's listed rows are counted over the CTA first, so that the unit
+    // reserves its part of the list with one atomic (one per warp step kept
+    // thousands of atomics queued on the count word of a pass)
+    constexpr uint32_t kPer = kRowChunk / 256u;  // rows per thread
+    static_assert(kRowChunk % 256u == 0u && kPer <= 32u, "k_tc_rows: 256 threads, a bit per row");
+    __shared__ uint32_t s_warp[8], s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for_job_chunks(jobs, T, kRowChunk, [&](const TcJob &J, uint32_t c) {
         uint32_t thr, iter, g;
         if (!tc_job_active(J, &thr, &iter, &g) || (!J.b_stamp && !J.covers_new)) return;
-        const uint32_t y_end = min(J.n, (c + 1u) * kRowChunk);
-        for (uint32_t y0 = c * kRowChunk; y0 < y_end; y0 += blockDim.x) {
-            const uint32_t y = y0 + threadIdx.x;
+        const uint32_t y_beg = c * kRowChunk, y_end = min(J.n, y_beg + kRowChunk);
+        uint32_t mask = 0u;
+#pragma unroll
+        for (uint32_t i = 0; i < kPer; ++i) {
+            const uint32_t y = y_beg + threadIdx.x + 256u * i;
             const bool dirty = y < y_end && (J.covers_new ? ((J.newcols[y >> 6] >> (y & 63u)) & 1ull) != 0ull
                                                           : J.b_stamp[y] >= thr);
-            const unsigned bal = __ballot_sync(0xffffffffu, dirty);
-            if (!bal) continue;
-            uint32_t base = 0;
-            if (lane == 0) base = reserve_rows(J.kcount, g, (uint32_t)__popc(bal), err_flag);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (dirty && base != 0xFFFFFFFFu) J.ys[base + (uint32_t)__popc(bal & ((1u << lane) - 1u))] = y;
+            if (dirty) mask |= 1u << i;
         }
+        // exclusive prefix of the threads' counts over the CTA
+        const uint32_t cnt = (uint32_t)__popc(mask);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t run = 0u;
+            for (int w = 0; w < 8; ++w) {
+                const uint32_t t = s_warp[w];
+                s_warp[w] = run;
+                run += t;
+            }
+            s_base = run ? reserve_rows(J.kcount, g, run, err_flag) : 0u;
+        }
+        __syncthreads();
+        const uint32_t base = s_base;
+        if (base != 0xFFFFFFFFu) {
+            uint32_t pos = base + s_warp[warp] + incl - cnt;
+            for (uint32_t m = mask; m; m &= m - 1u) J.ys[pos++] = y_beg + threadIdx.x + 256u * (uint32_t)(__ffs(m) - 1);
+        }
+        __syncthreads();  // s_warp and s_base are reused by the next unit
     });
 }
 
@@ -656,10 +685,11 @@ __global__ void __launch_bounds__(256) k_tc_a8(const TcJob *__restrict__ jobs, E
 
 // b8[z][k] = B[ys[k]][z] as a 0/1 FP8 byte (B's listed rows transposed), for
 // the columns z of the rank's window below n_pad and k below the next
-// multiple of 128 of D.  Unit of a warp: 32 listed rows x 32 columns.  Lane l
-// loads the 32 bits of row ys[k0 + l] at those columns; 32 ballots transpose
-// them (ballot c = column z0 + c over the 32 rows, kept by lane c), and every
-// lane writes its column's 32 bytes.
+// multiple of 128 of D.  Unit of a warp: 32 listed rows x 128 columns.  Lane
+// l loads the 128 bits of row ys[k0 + l] at those columns (one 16-byte load);
+// for every 32 of those columns, 32 ballots transpose them (ballot c = column
+// z0 + c over the 32 rows, kept by lane c), and every lane writes its
+// column's 32 bytes.
 __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, ExecTables T) {
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -676,24 +706,44 @@ __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, E
             uint32_t wc0, wc1;
             job_window(J, &wc0, &wc1);
             const uint32_t D = K.kdim, W = J.W, zend = min(W * 64u, wc1), zbeg = min(wc0, zend);
-            const uint32_t kchunks = ((D + 127u) & ~127u) / 32u, zchunks = (zend - zbeg) / 32u;
+            // (the window and n_pad are multiples of 128 columns)
+            const uint32_t kchunks = ((D + 127u) & ~127u) / 32u, zchunks = (zend - zbeg) / 128u;
             const uint32_t units = kchunks * zchunks;
             const uint32_t first = (gw + nw - (u0 % nw)) % nw;
             u0 += units;
-            for (uint32_t u = first; u < units; u += nw) {
-                const uint32_t k0 = (u / zchunks) * 32u, z0 = zbeg + (u % zchunks) * 32u;
-                const uint32_t k = k0 + (uint32_t)lane;
-                uint32_t bits = 0u;
-                if (k < D) bits = (uint32_t)(J.B[(size_t)J.ys[k] * W + (z0 >> 6)] >> (z0 & 63u));
-                uint32_t mine = 0u;
+            // two units per step, both rows loaded before either is transposed
+            // (the list and row loads are a dependent pair)
+            for (uint32_t u = first; u < units; u += 2u * nw) {
+                uint4 row[2];
+                uint32_t k0s[2], zbs[2];
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const uint32_t m = __ballot_sync(0xffffffffu, (bits >> c) & 1u);
-                    if (lane == c) mine = m;  // bit i: row ys[k0 + i] has column z0 + c
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t uu = u + (uint32_t)h * nw;
+                    k0s[h] = uu < units ? (uu / zchunks) * 32u : D;
+                    zbs[h] = zbeg + (uu % zchunks) * 128u;
+                    const uint32_t k = k0s[h] + (uint32_t)lane;
+                    row[h] = make_uint4(0u, 0u, 0u, 0u);
+                    if (uu < units && k < D)
+                        row[h] = *reinterpret_cast<const uint4 *>(J.B + (size_t)J.ys[k] * W + (zbs[h] >> 6));
                 }
-                uint4 *dst = reinterpret_cast<uint4 *>(J.b8 + (size_t)(z0 + (uint32_t)lane) * J.kcap + k0);
-                dst[0] = tc::expand16(mine & 0xFFFFu, 0x38u);
-                dst[1] = tc::expand16(mine >> 16, 0x38u);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (u + (uint32_t)h * nw >= units) continue;  // (uniform over the warp)
+                    const uint32_t parts[4] = {row[h].x, row[h].y, row[h].z, row[h].w};
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const uint32_t bits = parts[p], z0 = zbs[h] + 32u * (uint32_t)p;
+                        uint32_t mine = 0u;
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            const uint32_t m = __ballot_sync(0xffffffffu, (bits >> c) & 1u);
+                            if (lane == c) mine = m;  // bit i: row ys[k0 + i] has column z0 + c
+                        }
+                        uint4 *dst = reinterpret_cast<uint4 *>(J.b8 + (size_t)(z0 + (uint32_t)lane) * J.kcap + k0s[h]);
+                        dst[0] = tc::expand16(mine & 0xFFFFu, 0x38u);
+                        dst[1] = tc::expand16(mine >> 16, 0x38u);
+                    }
+                }
             }
         }
     }
@@ -1048,7 +1098,7 @@ cudaError_t launch_tc_compact(const TcJob *jobs, const ExecTables &T, uint32_t m
     k_tc_a8<<<(unsigned)sms * 4u, 256, (size_t)max_w * 8u * 8u, st>>>(jobs, T, max_w);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_tc_b8<<<(unsigned)sms * 4u, 256, 0, st>>>(jobs, T);
+    k_tc_b8<<<(unsigned)sms * 8u, 256, 0, st>>>(jobs, T);
     return cudaGetLastError();
 }
 
