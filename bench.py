@@ -58,7 +58,10 @@ METRIC = "CFPQ queries/s & closure Bool-GOPS, tensor-core/batched vs bit-packed,
 UNIT = "queries/s"
 WORKLOAD = "rpq_abc_n8192_deg8"
 FP8_PER_BF16 = 2.0  # nominal dense tensor rates: FP8 4.5 PFLOP/s vs bf16 2.25 PFLOP/s
-TILE_FLOP_PER_KSTAGE = 2.0 * 128 * 256 * 128  # one K stage of a 128 x 256 tile, 128 deep
+FP4_PER_BF16 = 6.0  # nominal dense FP4 13.5 PFLOP/s vs bf16 2.25 PFLOP/s
+# one K stage of a 128 x 256 tile, 128 deep (an FP4 stage of a 256 x 192 tile,
+# 256 deep, is counted as three of these)
+TILE_FLOP_PER_KSTAGE = 2.0 * 128 * 256 * 128
 
 
 def _config(n, deg, flush):
@@ -358,20 +361,23 @@ def _roofline_gather(st, peaks, n):
             "accounting": "(source rows ORed + 2 x output rows changed) x row bytes"}
 
 
-def _roofline_tiles(st, peaks, n):
-    """Tile products: dense 0/1 FP8 multiply-adds over the compacted inner
+def _roofline_tiles(st, peaks, n, fp4=False):
+    """Tile products: dense 0/1 multiply-adds over the compacted inner
     dimension (2 x 128 x 256 x 128 per K stage) over the product launches'
-    event time, against the FP8 peak (measured sustained bf16 x the nominal
-    FP8/bf16 ratio: the kernel runs inside a long step)."""
+    event time, against the peak of the tiles' format (measured sustained
+    bf16 x the nominal FP8/bf16 or FP4/bf16 ratio: the kernel runs inside a
+    long step)."""
     flop = st.tile_kstages * TILE_FLOP_PER_KSTAGE
     launches = max(1, st.tile_launches)
     sec = max(st.ms_tile_products, 1e-9) / 1e3
     achieved = flop / sec / 1e12
-    peak = peaks["bf16_tflops_sustained"] * FP8_PER_BF16
+    ratio, fmt = (FP4_PER_BF16, "FP4") if fp4 else (FP8_PER_BF16, "FP8")
+    peak = peaks["bf16_tflops_sustained"] * ratio
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": _traffic_from_profiles(f"k_tc_product_tma_dyck4_n{n}"),
-            "kernel": "cfpq::k_tc_product_tma (tcgen05 kind::f8f6f4)",
-            "peak_source": f"{peaks['kind']} bf16_tflops_sustained x {FP8_PER_BF16} (nominal FP8/bf16)",
+            "frac": achieved / peak,
+            "traffic": _traffic_from_profiles(f"k_tc_product_tma_{'fp4_' if fp4 else ''}dyck4_n{n}"),
+            "kernel": "cfpq::k_tc_product_tma (tcgen05 " + ("kind::mxf4, 0/1 E2M1" if fp4 else "kind::f8f6f4") + ")",
+            "peak_source": f"{peaks['kind']} bf16_tflops_sustained x {ratio} (nominal {fmt}/bf16)",
             "launches_timed": launches, "flop_per_launch": flop / launches,
             "ms_per_launch": st.ms_tile_products / launches,
             "accounting": "tile K stages x 2 x 128 x 256 x 128 (inner dimension compacted to the dirty rows)"}
@@ -475,8 +481,10 @@ def run_dyck(args):
     modes = None
     if not args.no_extras:
         modes = {"auto_ms_per_query": step_ms, "auto_tile_products": stats.tile_mmas}
-        for name, mode in (("bitpacked", cfpq.CFPQ_CLOSURE_BITPACKED), ("tc_fp8", cfpq.CFPQ_CLOSURE_TC_FP8)):
-            mctx = cfpq.Context(device=local, closure_mode=mode)
+        for name, mode, fmt in (("bitpacked", cfpq.CFPQ_CLOSURE_BITPACKED, 0),
+                                ("tc_fp8", cfpq.CFPQ_CLOSURE_TC_FP8, 0), ("tc_fp4", cfpq.CFPQ_CLOSURE_TC_FP4, 0),
+                                ("auto_fp8_tiles", cfpq.CFPQ_CLOSURE_AUTO, cfpq.CFPQ_TILES_FP8)):
+            mctx = cfpq.Context(device=local, closure_mode=mode, tile_format=fmt)
             mctx.load_rsm(r)
             mctx.load_graph_device(n, nt, d_src, d_lbl, d_dst)
             mctx.run()  # warm-up: buffers, plan, CUDA graph
@@ -497,7 +505,7 @@ def run_dyck(args):
     pctx.close()
     peaks = _peaks()
     roof_g = _roofline_gather(ps, peaks, n)
-    roof_t = _roofline_tiles(ps, peaks, n) if ps.tile_launches else None
+    roof_t = _roofline_tiles(ps, peaks, n, fp4=True) if ps.tile_launches else None  # AUTO's default tiles: FP4
     dominant, other = (roof_g, roof_t)
     if roof_t is not None and ps.ms_tile_products > ps.ms_gather:
         dominant, other = roof_t, roof_g
@@ -725,14 +733,15 @@ def run_other(args):
     elif args.workload == "dyck_modes":
         g, r = W.dyck_zipf(args.dyck_n)
         res = {}
-        all_modes = {"auto": cfpq.CFPQ_CLOSURE_AUTO, "bitpacked": cfpq.CFPQ_CLOSURE_BITPACKED,
-                     "tc_fp8": cfpq.CFPQ_CLOSURE_TC_FP8}
+        all_modes = {"auto": (cfpq.CFPQ_CLOSURE_AUTO, 0), "bitpacked": (cfpq.CFPQ_CLOSURE_BITPACKED, 0),
+                     "tc_fp8": (cfpq.CFPQ_CLOSURE_TC_FP8, 0), "tc_fp4": (cfpq.CFPQ_CLOSURE_TC_FP4, 0),
+                     "auto_fp8": (cfpq.CFPQ_CLOSURE_AUTO, cfpq.CFPQ_TILES_FP8)}
         names = [m for m in args.modes.split(",") if m in all_modes]
         if args.no_extras:
             names = names[:1]
         for name in names:
-            mode = all_modes[name]
-            ctx = cfpq.Context(closure_mode=mode, loop_mode=loop_mode)
+            mode, fmt = all_modes[name]
+            ctx = cfpq.Context(closure_mode=mode, tile_format=fmt, loop_mode=loop_mode)
             ctx.load_graph(g)
             ctx.load_rsm(r)
             st, ms = _ctx_time(ctx, stream, ctx.run)
@@ -989,7 +998,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--loop", default="device", choices=["device", "host"],
                     help="dyck_modes workload: fixpoint loop in a CUDA graph (device) or one launch per pass (host)")
-    ap.add_argument("--modes", default="auto,bitpacked,tc_fp8",
+    ap.add_argument("--modes", default="auto,bitpacked,tc_fp8,tc_fp4,auto_fp8",
                     help="dyck_modes workload: closure modes to run (the first is the line's value)")
     args = ap.parse_args()
     if args.impl == "reference":

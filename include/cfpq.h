@@ -61,7 +61,8 @@ typedef void (*cfpq_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
 /* Closure kernels (Listing 1, incremental transitive closure). */
 /* AUTO: bit-packed rows; from n = 2048 on, a nonterminal whose matrix M2
  * holds >= n^2/32 edges (checked after every iteration) moves its products
- * with the dirty closure rows to tensor-core tiles as in TC_FP8. */
+ * with the dirty closure rows to tensor-core tiles as in TC_FP8 / TC_FP4,
+ * in the format cfpq_options::tile_format selects. */
 #define CFPQ_CLOSURE_AUTO 0
 #define CFPQ_CLOSURE_BITPACKED 1 /* bit-packed uint64 rows only */
 /* TC_FP8: products of whole label matrices with the closure rows changed in
@@ -70,6 +71,16 @@ typedef void (*cfpq_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
  * the new edges of an iteration stay on bit-packed rows. */
 #define CFPQ_CLOSURE_TC_FP8 2
 #define CFPQ_CLOSURE_TC_I8 3     /* 0/1 INT8 tcgen05 products: CFPQ_ERR_UNSUPPORTED on sm_103a (no kind::i8) */
+/* TC_FP4: as TC_FP8, with 0/1 E2M1 operands (two per byte) multiplied by the
+ * block-scaled FP4 MMA (tcgen05 kind::mxf4, every scale factor 1.0, FP32
+ * accumulate, count > 0); tiles of 256 x 192 output bits.  Exact for the
+ * same reason: counts never exceed the inner dimension (< 2^24). */
+#define CFPQ_CLOSURE_TC_FP4 4
+
+/* Operand format of AUTO's tensor-core tiles (cfpq_options::tile_format). */
+#define CFPQ_TILES_DEFAULT 0 /* the library's choice (FP4) */
+#define CFPQ_TILES_FP8 1
+#define CFPQ_TILES_FP4 2
 
 /* Fixpoint loop control (Listing 1, "while M2 is changing"). */
 #define CFPQ_LOOP_DEVICE 0 /* one CUDA-graph launch; device-side convergence flags */
@@ -95,6 +106,8 @@ typedef struct {
     cfpq_alloc_fn alloc;     /* NULL = cudaMallocAsync */
     cfpq_free_fn free;
     void *alloc_user;
+    uint32_t tile_format;    /* CFPQ_TILES_*: operand format of AUTO's tiles; the result does
+                                not depend on it */
 } cfpq_options;
 
 /* Recursive state machine (Sec. 2.3, Def. of an RSM).  States are numbered

@@ -33,6 +33,10 @@ CFPQ_CLOSURE_AUTO = 0
 CFPQ_CLOSURE_BITPACKED = 1
 CFPQ_CLOSURE_TC_FP8 = 2
 CFPQ_CLOSURE_TC_I8 = 3
+CFPQ_CLOSURE_TC_FP4 = 4
+CFPQ_TILES_DEFAULT = 0
+CFPQ_TILES_FP8 = 1
+CFPQ_TILES_FP4 = 2
 CFPQ_LOOP_DEVICE = 0
 CFPQ_LOOP_HOST = 1
 
@@ -45,7 +49,7 @@ class cfpq_options(Structure):
                 ("max_rounds", c_uint32), ("closure_mode", c_uint32), ("loop_mode", c_uint32),
                 ("profile", c_uint32), ("no_single_cta", c_uint32), ("gather_slices", c_uint32),
                 ("memory_budget", c_size_t), ("alloc", cfpq_alloc_fn), ("free", cfpq_free_fn),
-                ("alloc_user", c_void_p)]
+                ("alloc_user", c_void_p), ("tile_format", c_uint32)]
 
 
 class cfpq_rsm(Structure):

@@ -165,6 +165,8 @@ int ensure_query(cfpq_ctx *ctx, bool restricted = false) {
     QueryDev &q = ctx->query;
     q.g = &ctx->graph;
     q.closure_mode = ctx->opt.closure_mode;
+    if (q.tile_fp4 != tiles_fp4(ctx->opt.closure_mode, ctx->opt.tile_format)) ctx->exec_dirty = true;
+    q.tile_fp4 = tiles_fp4(ctx->opt.closure_mode, ctx->opt.tile_format);
     q.gather_slices = ctx->opt.gather_slices;
     q.full_kcap = true;
     if (q.restricted != restricted) ctx->exec_dirty = true;  // the work items carry the row masks
@@ -250,7 +252,9 @@ int cfpq_create(cfpq_ctx **out, const cfpq_options *opt, void *stream) {
     } else {
         cfpq_default_options(&c->opt);
     }
-    if (c->opt.loop_mode > CFPQ_LOOP_HOST || c->opt.closure_mode > CFPQ_CLOSURE_TC_I8) return CFPQ_ERR_INVALID_ARG;
+    if (c->opt.loop_mode > CFPQ_LOOP_HOST || c->opt.closure_mode > CFPQ_CLOSURE_TC_FP4 ||
+        c->opt.tile_format > CFPQ_TILES_FP4)
+        return CFPQ_ERR_INVALID_ARG;
     if (c->opt.closure_mode == CFPQ_CLOSURE_TC_I8) return CFPQ_ERR_UNSUPPORTED;  // no kind::i8 MMA on sm_103a
     if (c->opt.profile && c->opt.loop_mode != CFPQ_LOOP_HOST) return CFPQ_ERR_INVALID_ARG;
     if ((c->opt.alloc == nullptr) != (c->opt.free == nullptr)) return CFPQ_ERR_INVALID_ARG;
@@ -907,6 +911,7 @@ extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_quer
         if (rc) return fail(ctx, rc, "query " + std::to_string(i) + ": " + e);
         std::unique_ptr<QueryDev> q(new QueryDev());
         q->closure_mode = ctx->opt.closure_mode;
+        q->tile_fp4 = tiles_fp4(ctx->opt.closure_mode, ctx->opt.tile_format);
         q->gather_slices = ctx->opt.gather_slices;
         rc = copy_rsm(qq.rsm, &q->rsm, &e);
         if (rc) return fail(ctx, rc, "query " + std::to_string(i) + ": " + e);

@@ -122,6 +122,7 @@ struct SrcDesc {
     // themselves (ident).
     uint32_t tile_new;
     uint32_t tc_kcap;
+    uint32_t tc_ratio;         // new_tiles_pay's ratio for the job's tile format
     const unsigned long long *tc_kcount;
     const unsigned long long *tc_mcount;
     const unsigned long long *tc_ecount;
@@ -203,11 +204,17 @@ struct TcJob {
     // of kcap bytes), and the product runs its inner dimension over the
     // listed rows only, operands brought in by TMA.  kcount = (pass stamp <<
     // 32) | count.  A job whose list is longer than kcap runs uncompacted.
+    // With fp4 set the operands are 0/1 E2M1 nibbles instead, two per byte
+    // (element k in byte k/2, even k in the low nibble), for the block-scaled
+    // FP4 products; kstride = bytes per operand row (kcap, or kcap/2 for fp4).
     uint32_t *ys;
     unsigned long long *kcount;
     uint8_t *a8;
     uint8_t *b8;
     uint32_t map;               // index of the job's pair of tensor maps (a8, b8)
+    uint32_t kstride;
+    uint32_t fp4;
+    uint32_t tile_ratio;        // new_tiles_pay's ratio (channel-1 jobs)
     // Channel-1 job (covers_new): the iteration's new edges A2 (A = A2 rows,
     // a_it = their iteration marks) times whole rows of B, compacted on both
     // sides: M to the rows x with a new edge (xs, count *mcount), K to the
@@ -226,16 +233,18 @@ struct TcJob {
 // Does the channel-1 tile job beat the row gather?  The gather reads one
 // closure row (n/8 bytes) per new edge (e of them); the compacted product
 // issues 2 * M * K * n multiply-adds (M and K rounded up to whole 128-row
-// tiles).  With the gather's measured ~3.5 TB/s and the tiles' ~2.5 PFLOP/s
-// (0/1 FP8), the tiles win when M * K < e * 2.5e15 / (16 * 3.5e12), i.e.
-// about 44 * e; n cancels.  listed_k = K for this pass (0 if the list was not
-// built), kcap = the job's room for it.
+// tiles).  With the gather's measured ~3.5 TB/s and the FP8 tiles' ~2.5
+// PFLOP/s, the tiles win when M * K < e * 2.5e15 / (16 * 3.5e12), i.e.
+// about 44 * e; n cancels.  The ratio scales with the tile format's rate
+// (kTileEdgeRatio for FP8, kTileEdgeRatioFp4 for FP4).  listed_k = K for
+// this pass (0 if the list was not built), kcap = the job's room for it.
 constexpr unsigned long long kTileEdgeRatio = 44;
+constexpr unsigned long long kTileEdgeRatioFp4 = 88;
 __host__ __device__ inline bool new_tiles_pay(uint32_t listed_k, uint32_t kcap, unsigned long long m,
-                                              unsigned long long e) {
+                                              unsigned long long e, unsigned long long ratio) {
     if (listed_k == 0 || listed_k > kcap || m == 0) return false;
     const unsigned long long pm = (m + 127ull) & ~127ull, pk = ((unsigned long long)listed_k + 127ull) & ~127ull;
-    return pm * pk < kTileEdgeRatio * e;
+    return pm * pk < ratio * e;
 }
 
 constexpr uint32_t kDenseDiv = 32;  // a box is dense from n^2 / 32 edges on (one bit in two words)

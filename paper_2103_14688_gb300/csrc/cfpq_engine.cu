@@ -272,6 +272,7 @@ int QueryDev::plan(std::string *err) {
     // (full_kcap: every row, so that a product covering the new edges, whose
     // list can grow to n, stays compacted)
     kcap = (W * 64u <= 8192u || full_kcap) ? W * 64u : std::max<uint32_t>(128u, ((W * 32u) + 127u) & ~127u);
+    if (tile_fp4) kcap = std::max<uint32_t>(kcap, 256u);  // E2M1 operand rows of at least one 128-byte TMA box
     blk_src0.assign(blocks.size(), 0);
     blk_nsrc.assign(blocks.size(), 0);
     for (size_t b = 0; b < blocks.size(); ++b) {
@@ -313,7 +314,7 @@ int QueryDev::plan(std::string *err) {
         // tensor-core mode: the dirty-row channels of every source that reads
         // a (non-pure) closure block are tile products; new edges stay on the
         // row gather
-        sd.dense = (closure_mode == CFPQ_CLOSURE_TC_FP8 && tiles_ok) ? 1u : 0u;
+        sd.dense = (closure_all_tiles(closure_mode) && tiles_ok) ? 1u : 0u;
         // AUTO: the same for a nonterminal source while its box's matrix is
         // dense (large queries only: a tile is 128 x 256)
         sd.box_switch =
@@ -345,7 +346,7 @@ int QueryDev::plan(std::string *err) {
 }
 
 uint64_t QueryDev::tc_slot_bytes() const {
-    return (uint64_t)W * 64 * 8 + 256 + ((uint64_t)n + (uint64_t)W * 64) * kcap;
+    return (uint64_t)W * 64 * 8 + 256 + ((uint64_t)n + (uint64_t)W * 64) * tc_kstride();
 }
 
 uint64_t QueryDev::footprint() const {
@@ -408,7 +409,7 @@ int QueryDev::prepare_small(Allocator *A, cudaStream_t st, uint32_t max_iter, ui
                             std::string *err) {
     small_ok = false;
     const uint32_t nblk = (uint32_t)blocks.size();
-    if (W > 8 || closure_mode == CFPQ_CLOSURE_TC_FP8) return CFPQ_OK;
+    if (W > 8 || closure_all_tiles(closure_mode)) return CFPQ_OK;
     const size_t smem = small_smem_bytes(n, W, B, nblk);
     const size_t limit = small_smem_limit();
     if (smem == 0 || smem > limit) return CFPQ_OK;
@@ -513,6 +514,18 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     std::vector<uint32_t> t_lvl((size_t)nq * maxL1, 0), t_lvl_tiles((size_t)nq * maxL1, 0);
     max_tc_tiles = 0;
     max_tc_w = 0;
+    // one tile format per executor: the product kernel is launched for it
+    tile_fp4 = false;
+    bool fmt_set = false;
+    for (QueryDev *q : qs) {
+        if (!q->n_tc_src) continue;
+        if (fmt_set && q->tile_fp4 != tile_fp4) {
+            *err = "queries of one executor use different tile formats";
+            return CFPQ_ERR_INVALID_ARG;
+        }
+        tile_fp4 = q->tile_fp4;
+        fmt_set = true;
+    }
     uint32_t n_maps = 0;
     size_t n_newcols = 0;  // words of the channel-1 jobs' column bitmaps and counts
     std::vector<size_t> newcols_of;
@@ -561,6 +574,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                 // the executor's newcols buffer (offsets, made pointers below)
                 d.tile_new = 1u;
                 d.tc_kcap = q.kcap;
+                d.tc_ratio = (uint32_t)(q.tile_fp4 ? kTileEdgeRatioFp4 : kTileEdgeRatio);
                 d.tc_kcount = q.tc_kcount((uint32_t)sd.tc_slot_new);
                 d.tc_mcount = reinterpret_cast<const unsigned long long *>((size_t)(n_newcols + q.W));
                 d.tc_ecount = reinterpret_cast<const unsigned long long *>((size_t)(n_newcols + q.W + 1));
@@ -676,6 +690,9 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                     j.box = sd.label_kind == 1 ? sd.label : 0u;
                     j.switchable = sd.box_switch;
                     j.kcap = q.kcap;
+                    j.kstride = q.tc_kstride();
+                    j.fp4 = q.tile_fp4 ? 1u : 0u;
+                    j.tile_ratio = (uint32_t)(q.tile_fp4 ? kTileEdgeRatioFp4 : kTileEdgeRatio);
                     j.ys = q.tc_ys((uint32_t)sd.tc_slot);
                     j.kcount = q.tc_kcount((uint32_t)sd.tc_slot);
                     j.a8 = q.tc_a8((uint32_t)sd.tc_slot);
@@ -875,7 +892,7 @@ int Executor::enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int us
     if (ev) ENG_CK(cudaEventRecord(ev[2], st));
     if (n_tcjobs) {
         ENG_CK(launch_tc_product(false, tcjobs.as<TcJob>(), max_tc_tiles, T, tc_err.as<int>(), st));
-        ENG_CK(launch_tc_product_tma(tcjobs.as<TcJob>(), tcmaps.p, max_tc_tiles, T, tc_err.as<int>(), st));
+        ENG_CK(launch_tc_product_tma(tcjobs.as<TcJob>(), tcmaps.p, max_tc_tiles, T, tc_err.as<int>(), st, tile_fp4));
     }
     if (ev) ENG_CK(cudaEventRecord(ev[3], st));
     // the last extraction launch of the pass also runs the loop control

@@ -38,7 +38,7 @@ cudaError_t launch_tc_compact(const TcJob *jobs, const ExecTables &T, uint32_t m
 // Products of the compacted jobs: TMA-fed tcgen05 pipeline (maps = the
 // jobs' tensor maps, two per job, from tc_encode_maps).
 cudaError_t launch_tc_product_tma(const TcJob *jobs, const void *maps, uint32_t max_tiles, const ExecTables &T,
-                                  int *err_flag, cudaStream_t st);
+                                  int *err_flag, cudaStream_t st, bool fp4);
 // Bytes of one tensor map; encode the a8/b8 maps of every job with buffers
 // (job.map indexes pairs) into host memory.
 size_t tc_map_bytes();
@@ -191,6 +191,7 @@ struct QueryDev {
     uint64_t device_bytes = 0;
     // host descriptors (pointers filled once buffers exist; ctl set by the executor)
     uint32_t closure_mode = CFPQ_CLOSURE_AUTO;
+    bool tile_fp4 = false;       // tile operands are E2M1 nibbles (tiles_fp4)
     uint32_t gather_slices = 0;  // cfpq_options::gather_slices
     // Multiple-source runs: per state the rows reachable from the sources
     // (compute_reach); the work items of block (s, t) then skip the rows of
@@ -215,12 +216,14 @@ struct QueryDev {
     // Product jobs' compaction buffers, one slot per tile job: the dirty
     // row list (n_pad entries), its pass-stamped count, the row list of a
     // channel-1 job (n_pad entries), A's columns at the listed rows as FP8
-    // bytes (n rows of kcap) and the listed B rows transposed (n_pad rows of
-    // kcap).  Every part starts 128-byte aligned.
+    // bytes (n rows of kcap; E2M1 nibbles: kcap/2) and the listed B rows
+    // transposed (n_pad rows of the same).  Every part starts 128-byte
+    // aligned.
     DBuf tc_mem;
     uint32_t n_tc_src = 0, kcap = 0;
     bool full_kcap = false;  // tile jobs' inner dimension may hold every row (else half above n = 8192)
     uint64_t tc_slot_bytes() const;
+    uint32_t tc_kstride() const { return tile_fp4 ? kcap / 2u : kcap; }  // bytes per operand row
     unsigned char *tc_slot(uint32_t k) const { return tc_mem.as<unsigned char>() + (size_t)k * tc_slot_bytes(); }
     uint32_t *tc_ys(uint32_t k) const { return reinterpret_cast<uint32_t *>(tc_slot(k)); }
     unsigned long long *tc_kcount(uint32_t k) const {
@@ -228,7 +231,7 @@ struct QueryDev {
     }
     uint32_t *tc_xs(uint32_t k) const { return reinterpret_cast<uint32_t *>(tc_slot(k) + (size_t)W * 64 * 4 + 256); }
     uint8_t *tc_a8(uint32_t k) const { return tc_slot(k) + (size_t)W * 64 * 8 + 256; }
-    uint8_t *tc_b8(uint32_t k) const { return tc_a8(k) + (size_t)n * kcap; }
+    uint8_t *tc_b8(uint32_t k) const { return tc_a8(k) + (size_t)n * tc_kstride(); }
     std::vector<uint32_t> blk_src0, blk_nsrc;  // per block
     std::vector<uint32_t> blk_level;           // per block, 0..n_levels-1
     uint32_t n_levels = 1;
@@ -260,6 +263,15 @@ struct QueryDev {
     uint64_t *a2_ptr(uint32_t b) const { return a2_mem.as<uint64_t>() + (size_t)b * n * W; }
 };
 
+// Closure modes that put every dirty-row product of a closure block on tiles.
+inline bool closure_all_tiles(uint32_t mode) {
+    return mode == CFPQ_CLOSURE_TC_FP8 || mode == CFPQ_CLOSURE_TC_FP4;
+}
+// Tile operands of a query: E2M1 for TC_FP4, and for AUTO unless FP8 is asked.
+inline bool tiles_fp4(uint32_t mode, uint32_t tile_format) {
+    return mode == CFPQ_CLOSURE_TC_FP4 || (mode == CFPQ_CLOSURE_AUTO && tile_format != CFPQ_TILES_FP8);
+}
+
 // Closure passes per iteration of the CUDA graph's while node.
 constexpr uint32_t kLoopUnroll = 2;
 
@@ -274,6 +286,7 @@ struct Executor {
     uint32_t n_items[kClasses] = {0}, n_xitems[kClasses] = {0};
     uint32_t max_live[kClasses] = {0};  // bound on live items of a pass: sum over queries of the largest level
     uint32_t n_tcjobs = 0, max_tc_tiles = 0, max_tc_w = 0;
+    bool tile_fp4 = false;  // the tile jobs' format (every query of an executor shares it)
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream: capture is not allowed on the legacy default stream

@@ -208,7 +208,7 @@ __device__ __forceinline__ uint32_t src_channels(const SrcDesc &d, uint32_t mode
     if (NT && ch && d.tile_new && d.tc_kcount) {
         const unsigned long long kc = *reinterpret_cast<const volatile unsigned long long *>(d.tc_kcount);
         const uint32_t listed = ((uint32_t)(kc >> 32) == g) ? (uint32_t)kc : 0u;
-        if (new_tiles_pay(listed, d.tc_kcap, *d.tc_mcount, *d.tc_ecount)) ch = d.ident ? 9u : 0u;
+        if (new_tiles_pay(listed, d.tc_kcap, *d.tc_mcount, *d.tc_ecount, d.tc_ratio)) ch = d.ident ? 9u : 0u;
     }
     return ch;
 }

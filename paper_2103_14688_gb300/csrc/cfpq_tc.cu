@@ -71,6 +71,36 @@ __device__ __forceinline__ void mma(bool int8, uint32_t dtmem, uint64_t ad, uint
         "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
 }
 
+// Instruction descriptor of the block-scaled FP4 MMA (kind::mxf4): A and B
+// E2M1 (format 1), both K-major, N >> 3, scale factors UE8M0 (bit 23), M >> 4,
+// scale-factor data ids 0.  D is always FP32.
+__host__ __device__ constexpr uint32_t make_idesc_mxf4(uint32_t M, uint32_t N) {
+    return (1u << 7) | (1u << 10) | ((N >> 3) << 17) | (1u << 23) | ((M >> 4) << 24);
+}
+
+// 128 x N x 64 MMA of packed 0/1 E2M1 operands (two per byte, 1.0 = 0x2) with
+// per-32-element UE8M0 scale factors read from TMEM at sfa / sfb; every scale
+// there is 2^0, so D accumulates the plain count.
+__device__ __forceinline__ void mma_fp4(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t sfa,
+                                        uint32_t sfb, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}\n" ::"r"(
+            dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accum));
+}
+
+// Store v into 32 consecutive TMEM columns of the warp's 32 lanes.
+__device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+        "r"(v)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void mma_commit(uint64_t *mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
                  : "memory");
@@ -159,6 +189,21 @@ __device__ __forceinline__ uint4 expand16(uint32_t b, uint32_t one) {
     return make_uint4(spread4(b) * one, spread4(b >> 4) * one, spread4(b >> 8) * one, spread4(b >> 12) * one);
 }
 
+// 8 bits -> 8 nibbles of a word (bit i -> nibble i, the low nibble of byte
+// i/2 for even i), each 0 or 0x2 (E2M1 1.0).
+__device__ __forceinline__ uint32_t nib8(uint32_t b) {
+    uint32_t x = b & 0xFFu;
+    x = (x | (x << 12)) & 0x000F000Fu;
+    x = (x | (x << 6)) & 0x03030303u;
+    x = (x | (x << 3)) & 0x11111111u;
+    return x << 1;
+}
+
+// 32 bits -> 32 E2M1 nibbles (16 bytes).
+__device__ __forceinline__ uint4 expand32_e2m1(uint32_t b) {
+    return make_uint4(nib8(b), nib8(b >> 8), nib8(b >> 16), nib8(b >> 24));
+}
+
 // Byte offset of element (row r, k byte) in a K-major no-swizzle tile whose
 // rows are grouped by 8 and whose K is split into kKG 16-byte columns.
 __device__ __forceinline__ uint32_t core_off(uint32_t r, uint32_t kg) {
@@ -242,7 +287,7 @@ __device__ __forceinline__ KDim job_kdim(const TcJob &J, uint32_t g) {
     if (J.ys && J.kcount) {
         const unsigned long long kc = *reinterpret_cast<volatile unsigned long long *>(J.kcount);
         const uint32_t d = ((uint32_t)(kc >> 32) == g) ? (uint32_t)kc : 0u;
-        if (J.covers_new) return KDim{new_tiles_pay(d, J.kcap, *J.mcount, *J.ecount) ? d : 0u, true};
+        if (J.covers_new) return KDim{new_tiles_pay(d, J.kcap, *J.mcount, *J.ecount, J.tile_ratio) ? d : 0u, true};
         if (d <= J.kcap) k = KDim{d, true};
     }
     return k;
@@ -642,7 +687,8 @@ __global__ void __launch_bounds__(256) k_tc_rows(const TcJob *__restrict__ jobs,
 
 // a8[x][k] = A[x][ys[k]] as a 0/1 FP8 byte for k < D, 0 up to the next
 // multiple of 128; one warp per row x, the row staged in shared memory, each
-// lane writing 4 consecutive bytes of a coalesced 128-byte step.
+// lane writing 4 consecutive bytes of a coalesced 128-byte step.  FP4 jobs
+// get E2M1 nibbles instead (see below).
 __global__ void __launch_bounds__(256) k_tc_a8(const TcJob *__restrict__ jobs, ExecTables T, uint32_t max_w) {
     extern __shared__ uint64_t s_rowbuf[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -666,7 +712,29 @@ __global__ void __launch_bounds__(256) k_tc_a8(const TcJob *__restrict__ jobs, E
         }
         nz = __any_sync(0xffffffffu, nz);
         __syncwarp();
-        uint32_t *dst = reinterpret_cast<uint32_t *>(J.a8 + (size_t)m * J.kcap);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(J.a8 + (size_t)m * J.kstride);
+        if (J.fp4) {
+            // E2M1 nibbles: 8 elements (4 bytes) per lane and 256-element step,
+            // zero up to the next multiple of 256 (a whole K stage) within kcap
+            const uint32_t kend = min((D + 255u) & ~255u, J.kcap);
+            for (uint32_t k0 = 0; k0 < kend; k0 += 256u) {
+                const uint32_t kb = k0 + 8u * (uint32_t)lane;
+                if (kb >= kend) continue;
+                uint32_t word = 0u;
+                if (nz && kb < D) {
+                    const uint4 y0 = *reinterpret_cast<const uint4 *>(J.ys + kb);
+                    const uint4 y1 = *reinterpret_cast<const uint4 *>(J.ys + kb + 4u);
+                    const uint32_t yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (kb + (uint32_t)i < D && ((row[yv[i] >> 6] >> (yv[i] & 63u)) & 1ull))
+                            word |= 0x2u << (4 * i);
+                }
+                dst[kb >> 3] = word;
+            }
+            __syncwarp();
+            return;
+        }
         for (uint32_t k0 = 0; k0 < dpad; k0 += 128u) {
             const uint32_t kb = k0 + 4u * (uint32_t)lane;
             uint32_t word = 0u;
@@ -685,7 +753,8 @@ __global__ void __launch_bounds__(256) k_tc_a8(const TcJob *__restrict__ jobs, E
 
 // b8[z][k] = B[ys[k]][z] as a 0/1 FP8 byte (B's listed rows transposed), for
 // the columns z of the rank's window below n_pad and k below the next
-// multiple of 128 of D.  Unit of a warp: 32 listed rows x 128 columns.  Lane
+// multiple of 128 of D (FP4 jobs: E2M1 nibbles, k below the next multiple of
+// 256 within kcap).  Unit of a warp: 32 listed rows x 128 columns.  Lane
 // l loads the 128 bits of row ys[k0 + l] at those columns (one 16-byte load);
 // for every 32 of those columns, 32 ballots transpose them (ballot c = column
 // z0 + c over the 32 rows, kept by lane c), and every lane writes its
@@ -706,8 +775,10 @@ __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, E
             uint32_t wc0, wc1;
             job_window(J, &wc0, &wc1);
             const uint32_t D = K.kdim, W = J.W, zend = min(W * 64u, wc1), zbeg = min(wc0, zend);
-            // (the window and n_pad are multiples of 128 columns)
-            const uint32_t kchunks = ((D + 127u) & ~127u) / 32u, zchunks = (zend - zbeg) / 128u;
+            // (the window and n_pad are multiples of 128 columns; an FP4 job's
+            // K stage is 256 elements, zero-padded within kcap)
+            const uint32_t kpad = J.fp4 ? min((D + 255u) & ~255u, J.kcap) : (D + 127u) & ~127u;
+            const uint32_t kchunks = kpad / 32u, zchunks = (zend - zbeg) / 128u;
             const uint32_t units = kchunks * zchunks;
             const uint32_t first = (gw + nw - (u0 % nw)) % nw;
             u0 += units;
@@ -739,9 +810,14 @@ __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, E
                             const uint32_t m = __ballot_sync(0xffffffffu, (bits >> c) & 1u);
                             if (lane == c) mine = m;  // bit i: row ys[k0 + i] has column z0 + c
                         }
-                        uint4 *dst = reinterpret_cast<uint4 *>(J.b8 + (size_t)(z0 + (uint32_t)lane) * J.kcap + k0s[h]);
-                        dst[0] = tc::expand16(mine & 0xFFFFu, 0x38u);
-                        dst[1] = tc::expand16(mine >> 16, 0x38u);
+                        unsigned char *rowp = J.b8 + (size_t)(z0 + (uint32_t)lane) * J.kstride;
+                        if (J.fp4) {
+                            *reinterpret_cast<uint4 *>(rowp + k0s[h] / 2u) = tc::expand32_e2m1(mine);
+                        } else {
+                            uint4 *dst = reinterpret_cast<uint4 *>(rowp + k0s[h]);
+                            dst[0] = tc::expand16(mine & 0xFFFFu, 0x38u);
+                            dst[1] = tc::expand16(mine >> 16, 0x38u);
+                        }
                     }
                 }
             }
@@ -802,10 +878,17 @@ struct JobCache {
     uint32_t li0 = 1u, li1 = 0u;  // live-tile indices of the job: [li0, li1)
     uint32_t ks = 0, g = 0, mlim = 0;
     uint32_t c0 = 0, c1 = 0;      // output columns of this rank (column sharding)
+    uint32_t ntn = 0;             // column tiles of the job
     bool ok = false;
 };
 
-template <uint32_t ROWS>  // output rows per tile: 128, or 256 (two accumulators, PAIR)
+// ROWS: output rows per tile, 128, or 256 (two accumulators, PAIR).  COLS:
+// output columns per tile, 256 (FP8), or 192 (FP4: the two accumulators
+// leave TMEM columns for the scale factors).  KSTAGE: elements of K per
+// 128-byte stage row (128 FP8 bytes or 256 E2M1 nibbles).  The live-tile
+// indices of a job cover tiles_m x tiles_n tiles of 128 x 256, at least as
+// many as ceil(n / ROWS) x ceil(n / COLS) for both shapes.
+template <uint32_t ROWS, uint32_t COLS = 256u, uint32_t KSTAGE = 128u>
 __device__ __forceinline__ bool next_tile(const TcJob *jobs, const ExecTables &T, uint32_t total, uint32_t &li,
                                           Tile &tl, JobCache &jc) {
     for (; li < total; li += gridDim.x) {
@@ -820,13 +903,15 @@ __device__ __forceinline__ bool next_tile(const TcJob *jobs, const ExecTables &T
             // the operands do not fit L2.  A channel-1 job walks only the
             // tile rows its row list fills.
             const uint32_t t = li - jc.li0, mt = (jc.mlim + ROWS - 1u) / ROWS;
-            if (t >= mt * jc.J->tiles_n) {  // past the job's row tiles: the rest of the job too
+            if (t >= mt * jc.ntn) {  // past the job's row tiles: the rest of the job too
                 li += ((jc.li1 - 1u - li) / gridDim.x) * gridDim.x;
                 continue;
             }
             tl.m0 = (t % mt) * ROWS;
-            tl.n0 = (t / mt) * 256u;
-            if (tl.n0 < jc.c0 || tl.n0 >= jc.c1) continue;  // another rank's columns
+            tl.n0 = (t / mt) * COLS;
+            // another rank's columns (rank windows are multiples of 256
+            // columns; a 192-column tile may straddle one and is masked)
+            if (tl.n0 + COLS <= jc.c0 || tl.n0 >= jc.c1) continue;
             tl.J = jc.J;
             tl.ks = jc.ks;
             tl.g = jc.g;
@@ -855,9 +940,10 @@ __device__ __forceinline__ bool next_tile(const TcJob *jobs, const ExecTables &T
         jc.li0 = li - t;
         jc.li1 = li - t + tiles;
         jc.ok = ok;
-        jc.ks = (K.kdim + 127u) / 128u;
+        jc.ks = (K.kdim + KSTAGE - 1u) / KSTAGE;
         jc.g = g;
         jc.mlim = ok && J.covers_new ? (uint32_t)*J.mcount : J.n;
+        jc.ntn = COLS == 256u ? J.tiles_n : (J.n + COLS - 1u) / COLS;
         job_window(J, &jc.c0, &jc.c1);
         li -= gridDim.x;  // re-enter through the cache
     }
@@ -866,23 +952,34 @@ __device__ __forceinline__ bool next_tile(const TcJob *jobs, const ExecTables &T
 }  // namespace tc2
 
 // PAIR: each CTA computes 256 output rows (two 128-row A tiles against one
-// B tile per K stage, two TMEM accumulators of 256 columns, so no second
-// buffer): 64 KiB of operands per stage feed twice the multiply-adds of the
-// 48 KiB stage of the single tile, and three stages in flight hold as much
-// work as six of those.
-template <bool PAIR>
+// B tile per K stage, two TMEM accumulators, so no second buffer): 64 KiB of
+// operands per stage feed twice the multiply-adds of the 48 KiB stage of the
+// single tile, and three stages in flight hold as much work as six of those.
+//
+// FP4 (with PAIR): the operands are packed 0/1 E2M1 nibbles, 256 elements of
+// K per 128-byte stage row, multiplied by the block-scaled kind::mxf4 MMA
+// (M = 128, N = 192, K = 64) whose scale factors are all 2^0.  The two
+// 192-column accumulators sit at TMEM columns 0 and 256; the columns between
+// (192-255 and 448-511) hold the UE8M0 scale factors, every byte 0x7F, so any
+// scale the MMA reads there is 1.0 and the accumulator holds the plain count.
+// A stage is 2 x 16 KiB of A and 24 KiB of B; four stages are in flight.
+template <bool PAIR, bool FP4>
 __global__ void __launch_bounds__(tc2::kThreads, 1)
     k_tc_product_tma(const TcJob *__restrict__ jobs, const unsigned char *__restrict__ maps, ExecTables T,
                      int *err_flag) {
     using namespace tc;
     using namespace tc2;
+    static_assert(PAIR || !FP4, "FP4 tiles run paired");
     constexpr uint32_t kRows = PAIR ? 256u : 128u;
-    constexpr int kRingN = PAIR ? 3 : kRing;
-    constexpr uint32_t kStageN = (PAIR ? 2u : 1u) * kABytes + kBBytes;
+    constexpr uint32_t kCols = FP4 ? 192u : 256u;        // output columns per tile (MMA N)
+    constexpr uint32_t kKStage = FP4 ? 256u : 128u;      // K elements per 128-byte stage row
+    constexpr uint32_t kBBytesN = kCols * 128u;
+    constexpr int kRingN = FP4 ? 4 : (PAIR ? 3 : kRing);
+    constexpr uint32_t kStageN = (PAIR ? 2u : 1u) * kABytes + kBBytesN;
     constexpr uint32_t kBufs = PAIR ? 1u : 2u;  // accumulator buffers (each 256 columns per 128 rows)
-    static_assert(kRingN * kStageN <= kRing * kStage, "stages exceed the shared memory of the launch");
+    static_assert(kRingN * kStageN + 1024u <= 227u * 1024u, "stages exceed the shared memory of an SM");
     extern __shared__ __align__(1024) unsigned char smem_raw2[];
-    __shared__ uint64_t full[kRing], empty[kRing], tfull[2], tempty[2];
+    __shared__ uint64_t full[kRingN], empty[kRingN], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base;
     const uint32_t total = *T.t_total;
     if (blockIdx.x >= total) return;
@@ -906,7 +1003,22 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
     __syncthreads();
     tc_after();
     const uint32_t tmem = tmem_base;
-    constexpr uint32_t idesc = make_idesc(1, 128, 256);
+    constexpr uint32_t kSfa = 192u, kSfb = 224u;  // FP4: scale-factor columns of A and B
+    if constexpr (FP4) {
+        // every TMEM column outside the two accumulators holds UE8M0 1.0
+        // (warps 2-5 cover the four lane quarters of columns 192-255, warps
+        // 6-9 those of columns 448-511)
+        if (warp >= 2) {
+            const uint32_t quarter = (uint32_t)warp & 3u, col = warp < 6 ? 192u : 448u;
+            tmem_fill32(tmem + ((quarter * 32u) << 16) + col, 0x7F7F7F7Fu);
+            tmem_fill32(tmem + ((quarter * 32u) << 16) + col + 32u, 0x7F7F7F7Fu);
+            tmem_wait_st();
+        }
+        tc_before();
+        __syncthreads();
+        tc_after();
+    }
+    constexpr uint32_t idesc = FP4 ? make_idesc_mxf4(128, kCols) : make_idesc(1, 128, 256);
     bool to = false;
 
     if (warp == 0) {
@@ -914,7 +1026,7 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
             uint32_t stage = 0, ph = 0, li = blockIdx.x;
             Tile tl;
             JobCache jc;
-            while (!to && next_tile<kRows>(jobs, T, total, li, tl, jc)) {
+            while (!to && next_tile<kRows, kCols, kKStage>(jobs, T, total, li, tl, jc)) {
                 const unsigned char *ma = maps + (size_t)tl.J->map * 2u * 128u, *mb = ma + 128;
                 for (uint32_t k = 0; k < tl.ks; ++k) {
                     if (!mbar_wait(&empty[stage], ph ^ 1u)) { to = true; break; }
@@ -933,7 +1045,7 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
             uint32_t stage = 0, ph = 0, acc = 0, aph = 0, li = blockIdx.x;
             Tile tl;
             JobCache jc;
-            while (!to && next_tile<kRows>(jobs, T, total, li, tl, jc)) {
+            while (!to && next_tile<kRows, kCols, kKStage>(jobs, T, total, li, tl, jc)) {
                 if (!mbar_wait(&tempty[acc], aph ^ 1u)) { to = true; break; }
                 tc_after();
                 const uint32_t d = tmem + acc * 256u;
@@ -944,11 +1056,19 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
                     const uint32_t sb = sa + (PAIR ? 2u : 1u) * kABytes;
 #pragma unroll
                     for (uint32_t kk = 0; kk < 4; ++kk) {
+                        // 32 bytes of each operand row per MMA: K = 32 FP8 or 64 E2M1
                         const uint32_t accum = (k > 0 || kk > 0) ? 1u : 0u;
-                        tc::mma(false, d, desc_sw128(sa + kk * 32u), desc_sw128(sb + kk * 32u), idesc, accum);
-                        if (PAIR)  // rows m0 + 128 .. into the second accumulator
-                            tc::mma(false, d + 256u, desc_sw128(sa + kABytes + kk * 32u), desc_sw128(sb + kk * 32u),
-                                    idesc, accum);
+                        if constexpr (FP4) {
+                            tc::mma_fp4(d, desc_sw128(sa + kk * 32u), desc_sw128(sb + kk * 32u), idesc, tmem + kSfa,
+                                        tmem + kSfb, accum);
+                            tc::mma_fp4(d + 256u, desc_sw128(sa + kABytes + kk * 32u), desc_sw128(sb + kk * 32u),
+                                        idesc, tmem + kSfa, tmem + kSfb, accum);
+                        } else {
+                            tc::mma(false, d, desc_sw128(sa + kk * 32u), desc_sw128(sb + kk * 32u), idesc, accum);
+                            if (PAIR)  // rows m0 + 128 .. into the second accumulator
+                                tc::mma(false, d + 256u, desc_sw128(sa + kABytes + kk * 32u),
+                                        desc_sw128(sb + kk * 32u), idesc, accum);
+                        }
                     }
                     mma_commit(&empty[stage]);  // the stage is free once these MMAs have read it
                     if (++stage == (uint32_t)kRingN) { stage = 0; ph ^= 1u; }
@@ -956,13 +1076,67 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
                 if (to) break;
                 mma_commit(&tfull[acc]);
                 QCtl *cw = tl.J->ctl;
-                if (cw) {  // counted in 128 x 256 tiles
+                if (cw) {
+                    // counted in 128 x 256 tiles and 128 x 256 x 128 stages (an
+                    // FP4 pair stage, 2 x 128 x 192 x 256, is three of those)
                     atomicAdd(&cw->tile_mmas, PAIR ? 2ull : 1ull);
-                    atomicAdd(&cw->tile_kstages, (unsigned long long)tl.ks * (PAIR ? 2ull : 1ull));
+                    atomicAdd(&cw->tile_kstages, (unsigned long long)tl.ks * (FP4 ? 3ull : PAIR ? 2ull : 1ull));
                 }
                 if (++acc == kBufs) { acc = 0; aph ^= 1u; }
                 li += gridDim.x;
             }
+        }
+    } else if constexpr (FP4) {
+        // epilogue: warps 2-5 read accumulator 0 (tile rows 0-127), warps 6-9
+        // accumulator 1 (rows 128-255), each its TMEM lane quarter and all 192
+        // columns (three output words per row)
+        const uint32_t quarter = (uint32_t)warp & 3u, hh = (uint32_t)(warp - 2) >> 2;
+        uint32_t aph = 0, li = blockIdx.x;
+        Tile tl;
+        JobCache jc;
+        while (!to && next_tile<kRows, kCols, kKStage>(jobs, T, total, li, tl, jc)) {
+            if (!mbar_wait(&tfull[0], aph)) { to = true; }
+            if (__any_sync(0xffffffffu, to)) { to = true; break; }
+            tc_after();
+            const TcJob &J = *tl.J;
+            uint32_t mask[6];
+#pragma unroll 1
+            for (int c = 0; c < 6; ++c) {
+                uint32_t v[32];
+                tmem_ld32(tmem + hh * 256u + 32u * (uint32_t)c + ((quarter * 32u) << 16), v);
+                uint32_t mb = 0u;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) mb |= (v[i] != 0u ? 1u : 0u) << i;
+#pragma unroll
+                for (int cc = 0; cc < 6; ++cc)
+                    if (cc == c) mask[cc] = mb;
+            }
+            tc_before();
+            __syncwarp();
+            if (lane == 0) arrive(&tempty[0]);  // the accumulators may be overwritten
+            const uint32_t r = quarter * 32u + (uint32_t)lane, mr = tl.m0 + 128u * hh + r;
+            const uint32_t x = mr >= tl.mlim ? J.n : (J.covers_new ? J.xs[mr] : mr);
+            bool ch = false;
+            if (x < J.n) {
+#pragma unroll
+                for (int w = 0; w < 3; ++w) {
+                    const uint32_t ww = (tl.n0 >> 6) + (uint32_t)w, z = ww * 64u;
+                    uint64_t add = (uint64_t)mask[2 * w] | ((uint64_t)mask[2 * w + 1] << 32);
+                    if (z < jc.c0 || z >= jc.c1) add = 0ull;  // another rank's columns
+                    if (ww >= J.W || !add) continue;
+                    const uint64_t old = atomicOr(
+                        reinterpret_cast<unsigned long long *>(J.out + (size_t)x * J.W + ww), (unsigned long long)add);
+                    if (add & ~old) ch = true;
+                }
+            }
+            if (ch && J.out_stamp) J.out_stamp[x] = tl.g;
+            const unsigned chb = __ballot_sync(0xffffffffu, ch);
+            if (lane == 0 && chb) {
+                if (J.out_last) *J.out_last = tl.g;
+                if (J.ctl) atomicAdd(&J.ctl->changed_rows, (unsigned long long)__popc(chb));
+            }
+            aph ^= 1u;
+            li += gridDim.x;
         }
     } else {  // epilogue: warps 2-9; TMEM lanes 32 * (warp % 4) ..., columns half * 128 ...
         const uint32_t quarter = (uint32_t)warp & 3u, half = (uint32_t)(warp - 2) >> 2;
@@ -1036,6 +1210,14 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
 // double-buffered accumulators: the kernel with PAIR = false).
 constexpr bool kTilePair = true;
 
+// Dynamic shared memory of k_tc_product_tma<PAIR, FP4>: its stage ring and
+// 1024 bytes of alignment.
+constexpr uint32_t tma_smem_bytes(bool pair, bool fp4) {
+    return (fp4 ? 4u * (2u * tc2::kABytes + 192u * 128u)
+                : pair ? 3u * (2u * tc2::kABytes + tc2::kBBytes) : (uint32_t)tc2::kRing * tc2::kStage) +
+           1024u;
+}
+
 static int g_tc_sms[64];
 
 int tc_smem_bytes() { return 2 * tc::kStageBytes; }
@@ -1057,8 +1239,11 @@ cudaError_t prepare_tc_launch() {
     e = cudaFuncSetAttribute(k_tc_a8, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kColMaxW * 8u * (256u / 32u)));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_product_tma<kTilePair>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(tc2::kRing * tc2::kStage + 1024u));
+    e = cudaFuncSetAttribute(k_tc_product_tma<kTilePair, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tma_smem_bytes(kTilePair, false));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_product_tma<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tma_smem_bytes(true, true));
     if (e != cudaSuccess) return e;
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1103,7 +1288,7 @@ cudaError_t launch_tc_compact(const TcJob *jobs, const ExecTables &T, uint32_t m
 }
 
 cudaError_t launch_tc_product_tma(const TcJob *jobs, const void *maps, uint32_t max_tiles, const ExecTables &T,
-                                  int *err_flag, cudaStream_t st) {
+                                  int *err_flag, cudaStream_t st, bool fp4) {
     if (max_tiles == 0 || maps == nullptr) return cudaSuccess;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1111,8 +1296,12 @@ cudaError_t launch_tc_product_tma(const TcJob *jobs, const void *maps, uint32_t 
     if (!sms) return cudaErrorNotReady;  // prepare_tc_launch was not called
     uint32_t grid = (uint32_t)sms;  // one CTA per SM: the ring and both accumulators fill it
     if (max_tiles < grid) grid = max_tiles;
-    k_tc_product_tma<kTilePair><<<grid, tc2::kThreads, tc2::kRing * tc2::kStage + 1024u, st>>>(
-        jobs, static_cast<const unsigned char *>(maps), T, err_flag);
+    if (fp4)
+        k_tc_product_tma<true, true><<<grid, tc2::kThreads, tma_smem_bytes(true, true), st>>>(
+            jobs, static_cast<const unsigned char *>(maps), T, err_flag);
+    else
+        k_tc_product_tma<kTilePair, false><<<grid, tc2::kThreads, tma_smem_bytes(kTilePair, false), st>>>(
+            jobs, static_cast<const unsigned char *>(maps), T, err_flag);
     return cudaGetLastError();
 }
 
@@ -1124,8 +1313,10 @@ cudaError_t launch_wait_selftest(uint64_t limit_ns, int *timed_out, cudaStream_t
 static_assert(sizeof(CUtensorMap) == 128, "the product kernel indexes tensor maps in 128-byte steps");
 size_t tc_map_bytes() { return sizeof(CUtensorMap); }
 
-// a8: kcap x n bytes, box 128 x 128; b8: kcap x n_pad bytes, box 128 x 256;
-// both UINT8 with the 128-byte swizzle (the K-major layout the MMA reads).
+// a8: kstride x n bytes, box 128 x 128; b8: kstride x n_pad bytes, box 128 x
+// 256 (FP4 jobs: 128 x 192, the tile's columns); both UINT8 with the
+// 128-byte swizzle (the K-major layout the MMA reads; an E2M1 byte holds two
+// elements).
 cudaError_t tc_encode_maps(const TcJob *jobs, uint32_t n_jobs, void *out) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -1139,9 +1330,9 @@ cudaError_t tc_encode_maps(const TcJob *jobs, uint32_t n_jobs, void *out) {
     for (uint32_t j = 0; j < n_jobs; ++j) {
         const TcJob &J = jobs[j];
         if (!J.ys) continue;
-        const cuuint64_t dims_a[2] = {J.kcap, J.n}, dims_b[2] = {J.kcap, (cuuint64_t)J.W * 64u};
-        const cuuint64_t stride[1] = {J.kcap};
-        const cuuint32_t box_a[2] = {128u, 128u}, box_b[2] = {128u, 256u}, es[2] = {1u, 1u};
+        const cuuint64_t dims_a[2] = {J.kstride, J.n}, dims_b[2] = {J.kstride, (cuuint64_t)J.W * 64u};
+        const cuuint64_t stride[1] = {J.kstride};
+        const cuuint32_t box_a[2] = {128u, 128u}, box_b[2] = {128u, J.fp4 ? 192u : 256u}, es[2] = {1u, 1u};
         CUresult r = encode(&m[2 * J.map], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, J.a8, dims_a, stride, box_a, es,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

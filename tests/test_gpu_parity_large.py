@@ -60,6 +60,7 @@ def _check_against_golden(words, case, block_rows):
 
 SIZES = [8192, 16384, 32768]
 MODES = [("auto", {}), ("bitpacked", {"closure_mode": 1}), ("tc_fp8", {"closure_mode": 2}),
+         ("tc_fp4", {"closure_mode": 4}), ("auto_fp8_tiles", {"tile_format": 1}),
          ("auto_slices1", {"gather_slices": 1}), ("auto_slices3", {"gather_slices": 3})]
 
 
