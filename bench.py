@@ -440,6 +440,7 @@ def run_dyck(args):
     total_ms = shard.max_over_ranks(float(np.sum(times)), dist, dev)
     value = ws * args.steps / (total_ms / 1000.0)
     stats = last
+    tuning = ctx.tune().as_dict()  # the autotuner's probe ran in the first warm-up step
     words = ctx.reachable_words(0)
     pairs = int(ctx.count_reachable(0))
     cbits, m3bits = ctx.count_index()
@@ -523,6 +524,7 @@ def run_dyck(args):
         "roofline": dominant,
         "roofline_other": other,
         "closure_modes": modes,
+        "autotune": tuning,
         "closure_time_split_ms": {"gather": ps.ms_gather, "tile_operands": ps.ms_tile_operands,
                                   "tile_products": ps.ms_tile_products, "host_loop_result_equal": prof_equal},
         "closure_bool_gops": stats.row_ors * stats.row_bytes * 8 / (step_ms / 1000.0) / 1e9,
@@ -741,6 +743,8 @@ def run_other(args):
             names = names[:1]
         for name in names:
             mode, fmt = all_modes[name]
+            if name == "auto" and args.tile_format:
+                fmt = args.tile_format
             ctx = cfpq.Context(closure_mode=mode, tile_format=fmt, loop_mode=loop_mode)
             ctx.load_graph(g)
             ctx.load_rsm(r)
@@ -998,6 +1002,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--loop", default="device", choices=["device", "host"],
                     help="dyck_modes workload: fixpoint loop in a CUDA graph (device) or one launch per pass (host)")
+    ap.add_argument("--tile-format", type=int, default=0,
+                    help="dyck_modes workload: tile_format of the auto mode (0 = the autotuner's choice; "
+                         "1 FP8, 2 FP4, 3 FP8 128-row tiles: no autotuner probe in the process)")
     ap.add_argument("--modes", default="auto,bitpacked,tc_fp8,tc_fp4,auto_fp8",
                     help="dyck_modes workload: closure modes to run (the first is the line's value)")
     args = ap.parse_args()

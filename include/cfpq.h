@@ -77,10 +77,14 @@ typedef void (*cfpq_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
  * same reason: counts never exceed the inner dimension (< 2^24). */
 #define CFPQ_CLOSURE_TC_FP4 4
 
-/* Operand format of AUTO's tensor-core tiles (cfpq_options::tile_format). */
-#define CFPQ_TILES_DEFAULT 0 /* the library's choice (FP4) */
-#define CFPQ_TILES_FP8 1
-#define CFPQ_TILES_FP4 2
+/* Tile kernel of the tensor-core products (cfpq_options::tile_format): the
+ * operand format and the output tile of one CTA.  DEFAULT is the
+ * autotuner's choice for AUTO (see cfpq_tune), FP8 pairs for TC_FP8. */
+#define CFPQ_TILES_DEFAULT 0
+#define CFPQ_TILES_FP8 1     /* 0/1 FP8, 256 x 256 output bits per CTA (two 128-row accumulators) */
+#define CFPQ_TILES_FP4 2     /* 0/1 E2M1, 256 x 192 output bits per CTA */
+#define CFPQ_TILES_FP8_128 3 /* 0/1 FP8, 128 x 256 output bits per CTA (double-buffered accumulator) */
+#define CFPQ_TILES_NVFP4 4   /* as FP4, multiplied by kind::mxf4nvf4 (16-element UE4M3 scales, all 1.0) */
 
 /* Fixpoint loop control (Listing 1, "while M2 is changing"). */
 #define CFPQ_LOOP_DEVICE 0 /* one CUDA-graph launch; device-side convergence flags */
@@ -106,8 +110,11 @@ typedef struct {
     cfpq_alloc_fn alloc;     /* NULL = cudaMallocAsync */
     cfpq_free_fn free;
     void *alloc_user;
-    uint32_t tile_format;    /* CFPQ_TILES_*: operand format of AUTO's tiles; the result does
-                                not depend on it */
+    uint32_t tile_format;    /* CFPQ_TILES_*: tile kernel of AUTO's (and TC_FP8's) products; the
+                                result does not depend on it */
+    uint32_t no_autotune;    /* 0 = the first AUTO query that may use tiles (n >= 2048) on a
+                                device runs the autotuner's probe once (cfpq_tune); 1 = use the
+                                built-in choices, never probe */
 } cfpq_options;
 
 /* Recursive state machine (Sec. 2.3, Def. of an RSM).  States are numbered
@@ -164,6 +171,29 @@ typedef struct {
     uint32_t gather_launches;  /* row-gather launches timed */
     uint32_t tile_launches;    /* passes whose tile-product launches were timed */
 } cfpq_run_stats;
+
+/* Result of the autotuner (cfpq_tune). */
+typedef struct {
+    uint32_t struct_size;   /* sizeof(cfpq_tuning), set by the caller */
+    uint32_t tuned;         /* 1: measured on this device; 0: built-in choices (probe off or failed) */
+    uint32_t tile_format;   /* CFPQ_TILES_FP8 / _FP4 / _FP8_128 / _NVFP4: the tile kernel AUTO uses */
+    uint32_t edge_ratio;    /* cost model: an iteration's new edges (e of them, M rows x K columns
+                               after compaction) run as tiles while M * K < edge_ratio * e; for
+                               queries whose n x n closure blocks fit in half the L2 ... */
+    uint32_t edge_ratio_hbm;/* ... and for larger ones (their gather reads rows from HBM) */
+    int32_t probe_status;   /* CFPQ status of the probe (0 = ok) */
+    double gather_gbs;      /* measured: bytes of source rows ORed per second by the row gather
+                               (probe blocks of 8 MiB: L2-resident) */
+    double gather_gbs_hbm;  /* gather_gbs x read_hbm_gbs / read_l2_gbs (at most gather_gbs): the
+                               same rows from HBM */
+    double read_l2_gbs;     /* measured device read bandwidth over a 24 MiB buffer (L2-resident) */
+    double read_hbm_gbs;    /* ... over a 2 GiB buffer */
+    double fp8_tflops;      /* measured: 0/1 multiply-adds per second of each tile kernel (x 1e12) */
+    double fp4_tflops;
+    double fp8_128_tflops;
+    double nvfp4_tflops;
+    double probe_ms;        /* host time the probe took */
+} cfpq_tuning;
 
 /* ---- context ---------------------------------------------------------------- */
 
@@ -243,6 +273,26 @@ int cfpq_run_sources(cfpq_ctx *ctx, const uint32_t *sources, uint32_t n_sources,
  * n_vertices differ from the loaded RSM and graph.  cfpq_run_sources returns
  * CFPQ_ERR_STATE while a start is set.  Seeded pairs count in edges_added. */
 int cfpq_set_start(cfpq_ctx *ctx, const uint64_t *bits, uint32_t n_boxes, uint32_t n_vertices);
+
+/* Autotuner of the closure's tile products (no counterpart in the paper,
+ * whose closure runs on a CPU Boolean-matrix library).  On the context's
+ * device it runs a probe query -- Dyck-4 (S -> S S | o_i c_i | o_i S c_i)
+ * on a seeded graph of 8192 vertices with 3 out-edges each, 8 labels --
+ * with the bit-packed closure and with each tile kernel, times their kernel
+ * groups with CUDA events, times reads of an L2-sized and an HBM-sized
+ * buffer, and derives: the fastest tile kernel (AUTO's default) and the
+ * cost-model ratio between that kernel's multiply-add rate and the gather's
+ * row bytes (edge_ratio = tile rate / (16 x gather rate): one new edge costs
+ * the gather n/8 bytes, a tile product 2n multiply-adds per (row, column) of
+ * its M x K box), with the gather rate scaled by the measured HBM/L2 read
+ * bandwidths for queries whose closure blocks exceed half the L2.  The result is kept per
+ * device for the process; force = 1 measures again.  Every answer is the
+ * same whichever choices are made.  The probe uses the context's stream and
+ * allocator and about 3 GB of device memory for its duration.  Errors:
+ * CFPQ_ERR_INVALID_ARG (NULL ctx or out, wrong struct_size); a probe that
+ * fails leaves the built-in choices (tuned = 0, probe_status set) and
+ * returns CFPQ_OK. */
+int cfpq_tune(cfpq_ctx *ctx, int force, cfpq_tuning *out);
 
 /* Count nnz(C3) and nnz(M3) of the last run into *closure_bits / *m3_bits. */
 int cfpq_count_index(cfpq_ctx *ctx, uint64_t *closure_bits, uint64_t *m3_bits);

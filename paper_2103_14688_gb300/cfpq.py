@@ -37,6 +37,8 @@ CFPQ_CLOSURE_TC_FP4 = 4
 CFPQ_TILES_DEFAULT = 0
 CFPQ_TILES_FP8 = 1
 CFPQ_TILES_FP4 = 2
+CFPQ_TILES_FP8_128 = 3
+CFPQ_TILES_NVFP4 = 4
 CFPQ_LOOP_DEVICE = 0
 CFPQ_LOOP_HOST = 1
 
@@ -49,7 +51,7 @@ class cfpq_options(Structure):
                 ("max_rounds", c_uint32), ("closure_mode", c_uint32), ("loop_mode", c_uint32),
                 ("profile", c_uint32), ("no_single_cta", c_uint32), ("gather_slices", c_uint32),
                 ("memory_budget", c_size_t), ("alloc", cfpq_alloc_fn), ("free", cfpq_free_fn),
-                ("alloc_user", c_void_p), ("tile_format", c_uint32)]
+                ("alloc_user", c_void_p), ("tile_format", c_uint32), ("no_autotune", c_uint32)]
 
 
 class cfpq_rsm(Structure):
@@ -72,6 +74,17 @@ class cfpq_run_stats(Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class cfpq_tuning(Structure):
+    _fields_ = [("struct_size", c_uint32), ("tuned", c_uint32), ("tile_format", c_uint32), ("edge_ratio", c_uint32),
+                ("edge_ratio_hbm", c_uint32), ("probe_status", c_int32), ("gather_gbs", c_double),
+                ("gather_gbs_hbm", c_double), ("read_l2_gbs", c_double), ("read_hbm_gbs", c_double),
+                ("fp8_tflops", c_double), ("fp4_tflops", c_double), ("fp8_128_tflops", c_double),
+                ("nvfp4_tflops", c_double), ("probe_ms", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "struct_size"}
 
 
 class cfpq_query(Structure):
@@ -128,6 +141,7 @@ def _declare(lib):
         "cfpq_run": (c_int, [P, POINTER(cfpq_run_stats)]),
         "cfpq_run_sources": (c_int, [P, POINTER(c_uint32), c_uint32, POINTER(cfpq_run_stats)]),
         "cfpq_count_index": (c_int, [P, u64p, u64p]),
+        "cfpq_tune": (c_int, [P, c_int, POINTER(cfpq_tuning)]),
         "cfpq_check_bounded_wait": (c_int, [P, c_uint64, POINTER(c_int)]),
         "cfpq_set_start": (c_int, [P, P, c_uint32, c_uint32]),
         "cfpq_get_reachable": (c_int, [P, c_uint32, u32p, u32p, c_size_t, POINTER(c_size_t)]),
@@ -328,6 +342,15 @@ class Context:
         self._check(self.lib.cfpq_check_bounded_wait(self.h, c_uint64(limit_ns), ctypes.byref(t)),
                     "cfpq_check_bounded_wait")
         return bool(t.value)
+
+    def tune(self, force: bool = False) -> cfpq_tuning:
+        """The autotuner's measurements and choices for this context's device
+        (runs its probe query once per device and process, or again with
+        force)."""
+        t = cfpq_tuning()
+        t.struct_size = ctypes.sizeof(cfpq_tuning)
+        self._check(self.lib.cfpq_tune(self.h, 1 if force else 0, ctypes.byref(t)), "cfpq_tune")
+        return t
 
     def count_index(self) -> Tuple[int, int]:
         a, b = c_uint64(), c_uint64()

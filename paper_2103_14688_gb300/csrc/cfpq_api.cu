@@ -17,6 +17,21 @@
 
 using namespace cfpq;
 
+namespace cfpq {
+// The tile kernel and cost-model ratio of a query run with options o on a
+// graph of n vertices: the autotuner's choice for AUTO with the default tile
+// format (its probe runs first when such a query may use tiles, n >= 2048),
+// else the format asked for.
+void set_tiles(QueryDev &q, const cfpq_options &o, cudaStream_t st, uint32_t n) {
+    const bool want = o.closure_mode == CFPQ_CLOSURE_AUTO && o.tile_format == CFPQ_TILES_DEFAULT &&
+                      n >= kAutoTilesMinN;
+    const Tuning t = o.no_autotune ? Tuning{} : device_tuning(o, st, want, false);
+    q.tile_kind = tile_kind_of(o.closure_mode, o.tile_format, t);
+    q.tile_fp4 = tile_kind_fp4(q.tile_kind);
+    q.tile_ratio = tile_ratio_of(q.tile_kind, t, n);
+}
+}  // namespace cfpq
+
 namespace {
 
 constexpr uint32_t kDefaultPassCap = 1u << 20;
@@ -165,8 +180,12 @@ int ensure_query(cfpq_ctx *ctx, bool restricted = false) {
     QueryDev &q = ctx->query;
     q.g = &ctx->graph;
     q.closure_mode = ctx->opt.closure_mode;
-    if (q.tile_fp4 != tiles_fp4(ctx->opt.closure_mode, ctx->opt.tile_format)) ctx->exec_dirty = true;
-    q.tile_fp4 = tiles_fp4(ctx->opt.closure_mode, ctx->opt.tile_format);
+    {
+        const uint32_t kind0 = q.tile_kind, ratio0 = q.tile_ratio;
+        set_tiles(q, ctx->opt, ctx->stream, ctx->graph.n);
+        if (q.tile_kind != kind0 || q.tile_ratio != ratio0) ctx->exec_dirty = true;
+        if (int rc = set_device(ctx)) return rc;  // (a probe may have run)
+    }
     q.gather_slices = ctx->opt.gather_slices;
     q.full_kcap = true;
     if (q.restricted != restricted) ctx->exec_dirty = true;  // the work items carry the row masks
@@ -253,7 +272,7 @@ int cfpq_create(cfpq_ctx **out, const cfpq_options *opt, void *stream) {
         cfpq_default_options(&c->opt);
     }
     if (c->opt.loop_mode > CFPQ_LOOP_HOST || c->opt.closure_mode > CFPQ_CLOSURE_TC_FP4 ||
-        c->opt.tile_format > CFPQ_TILES_FP4)
+        c->opt.tile_format > CFPQ_TILES_NVFP4)
         return CFPQ_ERR_INVALID_ARG;
     if (c->opt.closure_mode == CFPQ_CLOSURE_TC_I8) return CFPQ_ERR_UNSUPPORTED;  // no kind::i8 MMA on sm_103a
     if (c->opt.profile && c->opt.loop_mode != CFPQ_LOOP_HOST) return CFPQ_ERR_INVALID_ARG;
@@ -903,6 +922,14 @@ extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_quer
     ctx->bqueries.clear();
     ctx->bgraphs.clear();
     std::string e;
+    // one tile kernel for the batch: tuned for its largest graph
+    uint32_t max_n = 0;
+    for (uint32_t i = 0; i < n_queries; ++i) max_n = std::max(max_n, queries[i].n_vertices);
+    if (max_n) {
+        QueryDev probe_q;
+        set_tiles(probe_q, ctx->opt, ctx->stream, max_n);  // (runs the probe first when it may pay)
+        if (int rc = set_device(ctx)) return rc;
+    }
     for (uint32_t i = 0; i < n_queries; ++i) {
         const cfpq_query &qq = queries[i];
         std::unique_ptr<GraphDev> g(new GraphDev());
@@ -911,7 +938,7 @@ extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_quer
         if (rc) return fail(ctx, rc, "query " + std::to_string(i) + ": " + e);
         std::unique_ptr<QueryDev> q(new QueryDev());
         q->closure_mode = ctx->opt.closure_mode;
-        q->tile_fp4 = tiles_fp4(ctx->opt.closure_mode, ctx->opt.tile_format);
+        set_tiles(*q, ctx->opt, ctx->stream, max_n);
         q->gather_slices = ctx->opt.gather_slices;
         rc = copy_rsm(qq.rsm, &q->rsm, &e);
         if (rc) return fail(ctx, rc, "query " + std::to_string(i) + ": " + e);

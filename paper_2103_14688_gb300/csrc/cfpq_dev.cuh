@@ -240,6 +240,14 @@ struct TcJob {
 // this pass (0 if the list was not built), kcap = the job's room for it.
 constexpr unsigned long long kTileEdgeRatio = 44;
 constexpr unsigned long long kTileEdgeRatioFp4 = 88;
+
+// Tile products (TMA-fed tcgen05 kernels): 0/1 FP8 operands in 256 x 256
+// output tiles (two 128-row accumulators per CTA) or in 128 x 256 tiles
+// (double-buffered accumulator), or 0/1 E2M1 operands in 256 x 192 tiles
+// (kind::mxf4 with 32-element UE8M0 scales, or kind::mxf4nvf4 with
+// 16-element UE4M3 scales; the operands are the same).
+constexpr uint32_t kTileFp8Pair = 0, kTileFp8Single = 1, kTileFp4Pair = 2, kTileFp4NvPair = 3, kTileKinds = 4;
+__host__ __device__ constexpr bool tile_kind_fp4(uint32_t k) { return k == kTileFp4Pair || k == kTileFp4NvPair; }
 __host__ __device__ inline bool new_tiles_pay(uint32_t listed_k, uint32_t kcap, unsigned long long m,
                                               unsigned long long e, unsigned long long ratio) {
     if (listed_k == 0 || listed_k > kcap || m == 0) return false;

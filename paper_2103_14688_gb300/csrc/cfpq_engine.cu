@@ -514,17 +514,17 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     std::vector<uint32_t> t_lvl((size_t)nq * maxL1, 0), t_lvl_tiles((size_t)nq * maxL1, 0);
     max_tc_tiles = 0;
     max_tc_w = 0;
-    // one tile format per executor: the product kernel is launched for it
-    tile_fp4 = false;
-    bool fmt_set = false;
+    // one tile kernel per executor: the product kernel is launched for it
+    tile_kind = kTileFp8Pair;
+    bool kind_set = false;
     for (QueryDev *q : qs) {
         if (!q->n_tc_src) continue;
-        if (fmt_set && q->tile_fp4 != tile_fp4) {
-            *err = "queries of one executor use different tile formats";
+        if (kind_set && q->tile_kind != tile_kind) {
+            *err = "queries of one executor use different tile kernels";
             return CFPQ_ERR_INVALID_ARG;
         }
-        tile_fp4 = q->tile_fp4;
-        fmt_set = true;
+        tile_kind = q->tile_kind;
+        kind_set = true;
     }
     uint32_t n_maps = 0;
     size_t n_newcols = 0;  // words of the channel-1 jobs' column bitmaps and counts
@@ -574,7 +574,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                 // the executor's newcols buffer (offsets, made pointers below)
                 d.tile_new = 1u;
                 d.tc_kcap = q.kcap;
-                d.tc_ratio = (uint32_t)(q.tile_fp4 ? kTileEdgeRatioFp4 : kTileEdgeRatio);
+                d.tc_ratio = q.tile_ratio;
                 d.tc_kcount = q.tc_kcount((uint32_t)sd.tc_slot_new);
                 d.tc_mcount = reinterpret_cast<const unsigned long long *>((size_t)(n_newcols + q.W));
                 d.tc_ecount = reinterpret_cast<const unsigned long long *>((size_t)(n_newcols + q.W + 1));
@@ -692,7 +692,7 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                     j.kcap = q.kcap;
                     j.kstride = q.tc_kstride();
                     j.fp4 = q.tile_fp4 ? 1u : 0u;
-                    j.tile_ratio = (uint32_t)(q.tile_fp4 ? kTileEdgeRatioFp4 : kTileEdgeRatio);
+                    j.tile_ratio = q.tile_ratio;
                     j.ys = q.tc_ys((uint32_t)sd.tc_slot);
                     j.kcount = q.tc_kcount((uint32_t)sd.tc_slot);
                     j.a8 = q.tc_a8((uint32_t)sd.tc_slot);
@@ -892,7 +892,7 @@ int Executor::enqueue_pass(cudaStream_t st, cudaGraphConditionalHandle h, int us
     if (ev) ENG_CK(cudaEventRecord(ev[2], st));
     if (n_tcjobs) {
         ENG_CK(launch_tc_product(false, tcjobs.as<TcJob>(), max_tc_tiles, T, tc_err.as<int>(), st));
-        ENG_CK(launch_tc_product_tma(tcjobs.as<TcJob>(), tcmaps.p, max_tc_tiles, T, tc_err.as<int>(), st, tile_fp4));
+        ENG_CK(launch_tc_product_tma(tcjobs.as<TcJob>(), tcmaps.p, max_tc_tiles, T, tc_err.as<int>(), st, tile_kind));
     }
     if (ev) ENG_CK(cudaEventRecord(ev[3], st));
     // the last extraction launch of the pass also runs the loop control

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -38,7 +39,7 @@ cudaError_t launch_tc_compact(const TcJob *jobs, const ExecTables &T, uint32_t m
 // Products of the compacted jobs: TMA-fed tcgen05 pipeline (maps = the
 // jobs' tensor maps, two per job, from tc_encode_maps).
 cudaError_t launch_tc_product_tma(const TcJob *jobs, const void *maps, uint32_t max_tiles, const ExecTables &T,
-                                  int *err_flag, cudaStream_t st, bool fp4);
+                                  int *err_flag, cudaStream_t st, uint32_t tile_kind);
 // Bytes of one tensor map; encode the a8/b8 maps of every job with buffers
 // (job.map indexes pairs) into host memory.
 size_t tc_map_bytes();
@@ -191,7 +192,9 @@ struct QueryDev {
     uint64_t device_bytes = 0;
     // host descriptors (pointers filled once buffers exist; ctl set by the executor)
     uint32_t closure_mode = CFPQ_CLOSURE_AUTO;
-    bool tile_fp4 = false;       // tile operands are E2M1 nibbles (tiles_fp4)
+    uint32_t tile_kind = kTileFp8Pair;  // product kernel of the tiles (TileKind)
+    bool tile_fp4 = false;              // tile operands are E2M1 nibbles (tile_kind_fp4(tile_kind))
+    uint32_t tile_ratio = (uint32_t)kTileEdgeRatio;  // new_tiles_pay's ratio for this tile kind
     uint32_t gather_slices = 0;  // cfpq_options::gather_slices
     // Multiple-source runs: per state the rows reachable from the sources
     // (compute_reach); the work items of block (s, t) then skip the rows of
@@ -267,10 +270,37 @@ struct QueryDev {
 inline bool closure_all_tiles(uint32_t mode) {
     return mode == CFPQ_CLOSURE_TC_FP8 || mode == CFPQ_CLOSURE_TC_FP4;
 }
-// Tile operands of a query: E2M1 for TC_FP4, and for AUTO unless FP8 is asked.
-inline bool tiles_fp4(uint32_t mode, uint32_t tile_format) {
-    return mode == CFPQ_CLOSURE_TC_FP4 || (mode == CFPQ_CLOSURE_AUTO && tile_format != CFPQ_TILES_FP8);
-}
+
+// ---- autotuner (cfpq_tune.cu) ----
+// Measured on a probe query per device: the rate of each tile kind and of
+// the row gather, the kind AUTO uses by default, and the cost-model ratio
+// for that kind (the channel-1 tiles run while M * K < ratio * new edges).
+struct Tuning {
+    bool tuned = false;
+    uint32_t kind = kTileFp4Pair;
+    double gather_gbs = 0, tflops[kTileKinds] = {0, 0, 0, 0}, probe_ms = 0;
+    double read_l2_gbs = 0, read_hbm_gbs = 0;  // device reads of an L2-sized / HBM-sized buffer
+    uint64_t l2_bytes = 0;
+    int status = 0;  // CFPQ status of the probe (0 = ok)
+    // the gather's rate for closure blocks of `block_bytes`: measured on
+    // L2-resident blocks, scaled by the read bandwidths beyond half the L2
+    double gather_rate(uint64_t block_bytes) const {
+        if (block_bytes * 2 <= l2_bytes || read_l2_gbs <= 0 || read_hbm_gbs <= 0) return gather_gbs;
+        return gather_gbs * std::min(1.0, read_hbm_gbs / read_l2_gbs);
+    }
+};
+// The device's tuning; runs the probe first when `run` and it has not run
+// (or when `force`).  `like` gives the allocator and stream of the probe.
+Tuning device_tuning(const cfpq_options &like, cudaStream_t st, bool run, bool force);
+// Set q's tile kernel, operand format and ratio for a run with options o on
+// a graph of n vertices (cfpq_api.cu).
+void set_tiles(QueryDev &q, const cfpq_options &o, cudaStream_t st, uint32_t n);
+// The tile kind of a query in closure mode `mode` with tile_format `fmt`
+// (CFPQ_TILES_DEFAULT: the tuned kind).
+uint32_t tile_kind_of(uint32_t mode, uint32_t fmt, const Tuning &t);
+// new_tiles_pay's ratio for a kind and a query of n vertices: from the
+// measured rates when tuned, else the built-in constant of its format.
+uint32_t tile_ratio_of(uint32_t kind, const Tuning &t, uint32_t n);
 
 // Closure passes per iteration of the CUDA graph's while node.
 constexpr uint32_t kLoopUnroll = 2;
@@ -286,7 +316,7 @@ struct Executor {
     uint32_t n_items[kClasses] = {0}, n_xitems[kClasses] = {0};
     uint32_t max_live[kClasses] = {0};  // bound on live items of a pass: sum over queries of the largest level
     uint32_t n_tcjobs = 0, max_tc_tiles = 0, max_tc_w = 0;
-    bool tile_fp4 = false;  // the tile jobs' format (every query of an executor shares it)
+    uint32_t tile_kind = kTileFp8Pair;  // the tile jobs' kernel (every query of an executor shares it)
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream: capture is not allowed on the legacy default stream

@@ -74,7 +74,7 @@ int cfpq_server_create(cfpq_server **out, const cfpq_options *opt, void *stream,
             cfpq_default_options(&s->opt);
         }
         if ((s->opt.alloc == nullptr) != (s->opt.free == nullptr)) return CFPQ_ERR_INVALID_ARG;
-        if (s->opt.closure_mode > CFPQ_CLOSURE_TC_FP4 || s->opt.tile_format > CFPQ_TILES_FP4)
+        if (s->opt.closure_mode > CFPQ_CLOSURE_TC_FP4 || s->opt.tile_format > CFPQ_TILES_NVFP4)
             return CFPQ_ERR_INVALID_ARG;
         if (s->opt.closure_mode == CFPQ_CLOSURE_TC_I8) return CFPQ_ERR_UNSUPPORTED;
         if (cudaSetDevice(s->opt.device) != cudaSuccess) {
@@ -122,7 +122,11 @@ int cfpq_submit(cfpq_server *s, const cfpq_rsm *rsm, uint64_t *ticket) {
         // footprint and cut the number of queries admitted together
         j.q->closure_mode = s->opt.closure_mode == CFPQ_CLOSURE_AUTO ? (uint32_t)CFPQ_CLOSURE_BITPACKED
                                                                      : s->opt.closure_mode;
-        j.q->tile_fp4 = tiles_fp4(j.q->closure_mode, s->opt.tile_format);
+        {
+            cfpq_options o = s->opt;
+            o.closure_mode = j.q->closure_mode;
+            set_tiles(*j.q, o, s->stream, s->graph.n);
+        }
         j.q->gather_slices = s->opt.gather_slices;
         std::string e;
         int rc = copy_rsm(rsm, &j.q->rsm, &e);

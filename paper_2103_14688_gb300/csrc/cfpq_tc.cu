@@ -71,23 +71,33 @@ __device__ __forceinline__ void mma(bool int8, uint32_t dtmem, uint64_t ad, uint
         "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
 }
 
-// Instruction descriptor of the block-scaled FP4 MMA (kind::mxf4): A and B
-// E2M1 (format 1), both K-major, N >> 3, scale factors UE8M0 (bit 23), M >> 4,
-// scale-factor data ids 0.  D is always FP32.
-__host__ __device__ constexpr uint32_t make_idesc_mxf4(uint32_t M, uint32_t N) {
-    return (1u << 7) | (1u << 10) | ((N >> 3) << 17) | (1u << 23) | ((M >> 4) << 24);
+// Instruction descriptor of the block-scaled FP4 MMAs (kind::mxf4 and
+// kind::mxf4nvf4): A and B E2M1 (format 1), both K-major, N >> 3, scale
+// factors UE8M0 (bit 23 set: mxf4) or UE4M3 (clear: mxf4nvf4 with 16-element
+// blocks), M >> 4, scale-factor data ids 0.  D is always FP32.
+__host__ __device__ constexpr uint32_t make_idesc_fp4(uint32_t M, uint32_t N, bool ue8m0) {
+    return (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((ue8m0 ? 1u : 0u) << 23) | ((M >> 4) << 24);
 }
 
 // 128 x N x 64 MMA of packed 0/1 E2M1 operands (two per byte, 1.0 = 0x2) with
-// per-32-element UE8M0 scale factors read from TMEM at sfa / sfb; every scale
-// there is 2^0, so D accumulates the plain count.
+// block scale factors read from TMEM at sfa / sfb: per 32 elements in UE8M0
+// (NV false, kind::mxf4) or per 16 elements in UE4M3 (NV true,
+// kind::mxf4nvf4).  Every scale there is 1.0, so D accumulates the plain count.
+template <bool NV>
 __device__ __forceinline__ void mma_fp4(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t sfa,
                                         uint32_t sfb, uint32_t accum) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}\n" ::"r"(
-            dtmem),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accum));
+    if constexpr (NV)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::mxf4nvf4.block_scale.scale_vec::4X [%0], %1, %2, %3, [%4], [%5], "
+            "p;\n\t}\n" ::"r"(dtmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accum));
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], "
+            "p;\n\t}\n" ::"r"(dtmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accum));
 }
 
 // Store v into 32 consecutive TMEM columns of the warp's 32 lanes.
@@ -958,12 +968,14 @@ __device__ __forceinline__ bool next_tile(const TcJob *jobs, const ExecTables &T
 //
 // FP4 (with PAIR): the operands are packed 0/1 E2M1 nibbles, 256 elements of
 // K per 128-byte stage row, multiplied by the block-scaled kind::mxf4 MMA
-// (M = 128, N = 192, K = 64) whose scale factors are all 2^0.  The two
+// (NV: kind::mxf4nvf4; M = 128, N = 192, K = 64) whose scale factors are all
+// 1.0.  The two
 // 192-column accumulators sit at TMEM columns 0 and 256; the columns between
-// (192-255 and 448-511) hold the UE8M0 scale factors, every byte 0x7F, so any
-// scale the MMA reads there is 1.0 and the accumulator holds the plain count.
+// (192-255 and 448-511) hold the scale factors, every byte 1.0 (UE8M0 0x7F,
+// UE4M3 0x38), so any scale the MMA reads there is 1.0 and the accumulator
+// holds the plain count.
 // A stage is 2 x 16 KiB of A and 24 KiB of B; four stages are in flight.
-template <bool PAIR, bool FP4>
+template <bool PAIR, bool FP4, bool NV = false>
 __global__ void __launch_bounds__(tc2::kThreads, 1)
     k_tc_product_tma(const TcJob *__restrict__ jobs, const unsigned char *__restrict__ maps, ExecTables T,
                      int *err_flag) {
@@ -1010,15 +1022,17 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
         // 6-9 those of columns 448-511)
         if (warp >= 2) {
             const uint32_t quarter = (uint32_t)warp & 3u, col = warp < 6 ? 192u : 448u;
-            tmem_fill32(tmem + ((quarter * 32u) << 16) + col, 0x7F7F7F7Fu);
-            tmem_fill32(tmem + ((quarter * 32u) << 16) + col + 32u, 0x7F7F7F7Fu);
+            // 1.0: UE8M0 0x7F (2^(127-127)); UE4M3 0x38 (2^(7-7) x 1.0)
+            constexpr uint32_t one4 = NV ? 0x38383838u : 0x7F7F7F7Fu;
+            tmem_fill32(tmem + ((quarter * 32u) << 16) + col, one4);
+            tmem_fill32(tmem + ((quarter * 32u) << 16) + col + 32u, one4);
             tmem_wait_st();
         }
         tc_before();
         __syncthreads();
         tc_after();
     }
-    constexpr uint32_t idesc = FP4 ? make_idesc_mxf4(128, kCols) : make_idesc(1, 128, 256);
+    constexpr uint32_t idesc = FP4 ? make_idesc_fp4(128, kCols, !NV) : make_idesc(1, 128, 256);
     bool to = false;
 
     if (warp == 0) {
@@ -1059,9 +1073,9 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
                         // 32 bytes of each operand row per MMA: K = 32 FP8 or 64 E2M1
                         const uint32_t accum = (k > 0 || kk > 0) ? 1u : 0u;
                         if constexpr (FP4) {
-                            tc::mma_fp4(d, desc_sw128(sa + kk * 32u), desc_sw128(sb + kk * 32u), idesc, tmem + kSfa,
+                            tc::mma_fp4<NV>(d, desc_sw128(sa + kk * 32u), desc_sw128(sb + kk * 32u), idesc, tmem + kSfa,
                                         tmem + kSfb, accum);
-                            tc::mma_fp4(d + 256u, desc_sw128(sa + kABytes + kk * 32u), desc_sw128(sb + kk * 32u),
+                            tc::mma_fp4<NV>(d + 256u, desc_sw128(sa + kABytes + kk * 32u), desc_sw128(sb + kk * 32u),
                                         idesc, tmem + kSfa, tmem + kSfb, accum);
                         } else {
                             tc::mma(false, d, desc_sw128(sa + kk * 32u), desc_sw128(sb + kk * 32u), idesc, accum);
@@ -1205,10 +1219,10 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
     if (warp == 0) tmem_dealloc(tmem, tc2::kTmemCols);
 }
 
-// 256-row tiles (two accumulators) in the TMA-fed products: Dyck-4 n = 65536
-// tile products 852 -> 762 ms, the query 1.49 -> 1.41 s (128-row tiles with
-// double-buffered accumulators: the kernel with PAIR = false).
-constexpr bool kTilePair = true;
+// 256-row tiles (two accumulators) in the TMA-fed FP8 products: Dyck-4
+// n = 65536 tile products 852 -> 762 ms, the query 1.49 -> 1.41 s (128-row
+// tiles with double-buffered accumulators: the kernel with PAIR = false,
+// tile kind kTileFp8Single).  The autotuner times all three kernels.
 
 // Dynamic shared memory of k_tc_product_tma<PAIR, FP4>: its stage ring and
 // 1024 bytes of alignment.
@@ -1239,10 +1253,16 @@ cudaError_t prepare_tc_launch() {
     e = cudaFuncSetAttribute(k_tc_a8, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kColMaxW * 8u * (256u / 32u)));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_product_tma<kTilePair, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tma_smem_bytes(kTilePair, false));
+    e = cudaFuncSetAttribute(k_tc_product_tma<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tma_smem_bytes(true, false));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_product_tma<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tma_smem_bytes(false, false));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_tc_product_tma<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tma_smem_bytes(true, true));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_product_tma<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tma_smem_bytes(true, true));
     if (e != cudaSuccess) return e;
     int sms = 0;
@@ -1288,7 +1308,7 @@ cudaError_t launch_tc_compact(const TcJob *jobs, const ExecTables &T, uint32_t m
 }
 
 cudaError_t launch_tc_product_tma(const TcJob *jobs, const void *maps, uint32_t max_tiles, const ExecTables &T,
-                                  int *err_flag, cudaStream_t st, bool fp4) {
+                                  int *err_flag, cudaStream_t st, uint32_t tile_kind) {
     if (max_tiles == 0 || maps == nullptr) return cudaSuccess;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1296,12 +1316,17 @@ cudaError_t launch_tc_product_tma(const TcJob *jobs, const void *maps, uint32_t 
     if (!sms) return cudaErrorNotReady;  // prepare_tc_launch was not called
     uint32_t grid = (uint32_t)sms;  // one CTA per SM: the ring and both accumulators fill it
     if (max_tiles < grid) grid = max_tiles;
-    if (fp4)
-        k_tc_product_tma<true, true><<<grid, tc2::kThreads, tma_smem_bytes(true, true), st>>>(
-            jobs, static_cast<const unsigned char *>(maps), T, err_flag);
+    const unsigned char *mp = static_cast<const unsigned char *>(maps);
+    if (tile_kind == kTileFp4Pair)
+        k_tc_product_tma<true, true><<<grid, tc2::kThreads, tma_smem_bytes(true, true), st>>>(jobs, mp, T, err_flag);
+    else if (tile_kind == kTileFp4NvPair)
+        k_tc_product_tma<true, true, true><<<grid, tc2::kThreads, tma_smem_bytes(true, true), st>>>(jobs, mp, T,
+                                                                                                    err_flag);
+    else if (tile_kind == kTileFp8Single)
+        k_tc_product_tma<false, false><<<grid, tc2::kThreads, tma_smem_bytes(false, false), st>>>(jobs, mp, T,
+                                                                                                  err_flag);
     else
-        k_tc_product_tma<kTilePair, false><<<grid, tc2::kThreads, tma_smem_bytes(kTilePair, false), st>>>(
-            jobs, static_cast<const unsigned char *>(maps), T, err_flag);
+        k_tc_product_tma<true, false><<<grid, tc2::kThreads, tma_smem_bytes(true, false), st>>>(jobs, mp, T, err_flag);
     return cudaGetLastError();
 }
 

@@ -63,12 +63,13 @@ def test_rpq_fp4_equals_bitpacked_and_oracle(C, n, deg, seed):
 
 
 @pytest.mark.parametrize("seed", range(8))
-def test_random_cfpq_fp4(C, seed):
+@pytest.mark.parametrize("fmt", [2, 4])  # kind::mxf4 (UE8M0 scales), kind::mxf4nvf4 (UE4M3 scales)
+def test_random_cfpq_fp4(C, seed, fmt):
     rng = np.random.Generator(np.random.PCG64(300 + seed))
     n = int(rng.integers(1, 500))
     g, r = W.small_random_instance(400 + seed, n=n, m=int(rng.integers(0, 4 * n + 1)),
                                    n_labels=int(rng.integers(1, 5)), max_states=16)
-    _, s1, a = _run(g, r, C.CFPQ_CLOSURE_TC_FP4)
+    _, s1, a = _run(g, r, C.CFPQ_CLOSURE_TC_FP4, tile_format=fmt)
     assert (a == oracle.worklist(g, r)).all()
     _, s2, b = _run(g, r, C.CFPQ_CLOSURE_TC_FP8)
     assert (a == b).all() and s1.iterations == s2.iterations
@@ -112,5 +113,5 @@ def test_batch_fp4(C):
 
 def test_tile_format_is_validated(C):
     with pytest.raises(C.CfpqError) as e:
-        C.Context(tile_format=3)
+        C.Context(tile_format=5)
     assert e.value.status == C.CFPQ_ERR_INVALID_ARG

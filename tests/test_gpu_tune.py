@@ -1,0 +1,73 @@
+"""The autotuner of the closure's tile products (cfpq_tune): it measures the
+row gather and every tile kernel on its probe query, picks the fastest tile
+kernel for AUTO and derives the cost-model ratio; whatever it picks, every
+answer stays the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_14688_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    from paper_2103_14688_gb300 import cfpq
+    cfpq.load()
+    return cfpq
+
+
+def _answer(C, g, r, **opts):
+    with C.Context(**opts) as ctx:
+        ctx.load_graph(g)
+        ctx.load_rsm(r)
+        st = ctx.run()
+        return st, np.stack([ctx.reachable_bits(b) for b in range(r.n_boxes)])
+
+
+def test_tune_measures_and_chooses(C):
+    with C.Context() as ctx:
+        t = ctx.tune()
+    assert t.tuned == 1 and t.probe_status == 0, t.as_dict()
+    assert t.gather_gbs > 0 and t.probe_ms > 0 and t.read_l2_gbs > 0 and t.read_hbm_gbs > 0
+    scaled = t.gather_gbs * min(1.0, t.read_hbm_gbs / t.read_l2_gbs)
+    assert abs(t.gather_gbs_hbm - scaled) <= 1e-6 * t.gather_gbs
+    rates = {C.CFPQ_TILES_FP8: t.fp8_tflops, C.CFPQ_TILES_FP4: t.fp4_tflops, C.CFPQ_TILES_FP8_128: t.fp8_128_tflops,
+             C.CFPQ_TILES_NVFP4: t.nvfp4_tflops}
+    assert all(v > 0 for v in rates.values())
+    assert t.tile_format == max(rates, key=rates.get)
+    for ratio, gbs in ((t.edge_ratio, t.gather_gbs), (t.edge_ratio_hbm, t.gather_gbs_hbm)):
+        want = rates[t.tile_format] * 1e3 / (16.0 * gbs)
+        assert 8 <= ratio <= 4096
+        assert abs(ratio - min(4096.0, max(8.0, want))) <= 1.0
+    # cached per device: a second call returns the same choice without a probe
+    with C.Context() as ctx:
+        t2 = ctx.tune()
+    assert (t2.tile_format, t2.edge_ratio, t2.fp4_tflops) == (t.tile_format, t.edge_ratio, t.fp4_tflops)
+
+
+@pytest.mark.parametrize("fmt", [0, 1, 2, 3, 4])
+def test_every_tile_kernel_gives_the_oracle_answer(C, fmt):
+    g, r = W.dyck_zipf(2048, seed=21)
+    st, a = _answer(C, g, r, tile_format=fmt, no_single_cta=1)
+    assert st.tile_mmas > 0
+    assert (a == oracle.worklist(g, r)).all()
+
+
+def test_fp8_single_tiles_in_tc_mode(C):
+    g, r = W.small_random_instance(77, n=600, m=2400, n_labels=3, max_states=14)
+    _, a = _answer(C, g, r, closure_mode=C.CFPQ_CLOSURE_TC_FP8, tile_format=C.CFPQ_TILES_FP8_128)
+    assert (a == oracle.worklist(g, r)).all()
+
+
+def test_no_autotune_and_bad_struct(C):
+    import ctypes
+    g, r = W.dyck_zipf(2048, seed=22)
+    _, a = _answer(C, g, r, no_autotune=1)
+    _, b = _answer(C, g, r)
+    assert (a == b).all()
+    with C.Context() as ctx:
+        t = C.cfpq_tuning()
+        t.struct_size = 3
+        assert ctx.lib.cfpq_tune(ctx.h, 0, ctypes.byref(t)) == C.CFPQ_ERR_INVALID_ARG
