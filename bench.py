@@ -557,17 +557,22 @@ def batched_summary(count, device):
     from paper_2103_14688_gb300 import cfpq
     qs = W.batched_queries(count=count)
 
-    def batch(mode):
+    split = {}
+
+    def batch(mode, name):
         ctx = cfpq.Context(device=device, closure_mode=mode)
         ctx.batch_run(qs)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.batch_run(qs)
+        _, tot = ctx.batch_run(qs)
         torch.cuda.synchronize()
-        return ctx, time.perf_counter() - t0
+        el = time.perf_counter() - t0
+        split[name] = {"setup_ms": tot.ms_setup, "loop_ms": tot.ms_loop, "passes": tot.rounds,
+                       "gpu_launches": tot.gpu_launches, "tile_products": tot.tile_mmas}
+        return ctx, el
 
-    actx, at = batch(cfpq.CFPQ_CLOSURE_AUTO)
-    bctx, bt = batch(cfpq.CFPQ_CLOSURE_BITPACKED)
+    actx, at = batch(cfpq.CFPQ_CLOSURE_AUTO, "auto")
+    bctx, bt = batch(cfpq.CFPQ_CLOSURE_BITPACKED, "bitpacked")
     solo = cfpq.Context(device=device)
     st, mism = 0.0, 0
     for i, (g, r) in enumerate(qs):
@@ -586,7 +591,8 @@ def batched_summary(count, device):
         c.close()
     return {"queries": len(qs), "batched_qps": len(qs) / at, "batched_bitpacked_qps": len(qs) / bt,
             "one_at_a_time_qps": len(qs) / st, "speedup_vs_one_at_a_time": st / at,
-            "mismatches_vs_solo": mism, "timing": "host clock around one batch_run after a warm-up batch"}
+            "mismatches_vs_solo": mism, "split": split,
+            "timing": "host clock around one batch_run after a warm-up batch"}
 
 
 def served_summary(lam, horizon, device):

@@ -954,7 +954,8 @@ extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_quer
     const auto t1 = std::chrono::steady_clock::now();
     std::vector<QCtl> ctls;
     uint32_t launches = 0;
-    if ((rc = run_executor(ctx, ctx->bexec, &ctls, &launches))) return rc;
+    ClosureProfile prof;
+    if ((rc = run_executor(ctx, ctx->bexec, &ctls, &launches, &prof))) return rc;
     ctx->has_batch = true;
     const auto t2 = std::chrono::steady_clock::now();
     const double ms = std::chrono::duration<double, std::milli>(t2 - t0).count();
@@ -976,6 +977,13 @@ extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_quer
         if (status_of(ctls[i])) worst = status_of(ctls[i]);
     }
     tot.ms_total = ms;
+    tot.ms_closure = prof.ms_closure;  // profile = 1: the batch's closure passes by kernel group
+    tot.ms_gather = prof.ms_gather;
+    tot.ms_tile_operands = prof.ms_operands;
+    tot.ms_tile_products = prof.ms_products;
+    tot.closure_launches = prof.closure_launches;
+    tot.gather_launches = prof.gather_launches;
+    tot.tile_launches = prof.tile_launches;
     tot.ms_setup = std::chrono::duration<double, std::milli>(t1 - t0).count();
     tot.ms_loop = std::chrono::duration<double, std::milli>(t2 - t1).count();
     tot.gpu_launches = launches;

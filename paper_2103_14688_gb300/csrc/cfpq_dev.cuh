@@ -288,7 +288,48 @@ struct ExecTables {
     uint32_t *t_pre;                         // [nq] prefix of live tiles
     uint32_t *t_job_beg;                     // [nq]
     uint32_t *t_job_end;                     // [nq]
+    // The tile jobs that take part in the next pass (tc_job_active), listed
+    // by the control kernel in any order: the operand kernels walk only these.
+    const TcJob *jobs;                       // the executor's jobs (null: none)
+    uint32_t *aj;                            // [number of jobs]
+    uint32_t *aj_n;                          // [1]
 };
+
+// Decide whether the job takes part in this pass and with which threshold.
+__device__ inline bool tc_job_active(const TcJob &j, uint32_t *thr, uint32_t *iter, uint32_t *g) {
+    if (!j.ctl) {
+        *thr = 0;
+        *iter = 0;
+        *g = 0;
+        return true;
+    }
+    const QCtl *c = j.ctl;
+    if (c->phase != kPhaseRun || c->level != j.level) return false;
+    if (j.switchable && (j.box >= 32u || !((c->dense_mask >> j.box) & 1u))) return false;
+    *iter = c->iter;
+    *g = c->g;
+    const uint32_t g0 = c->g_iter_start;
+    if (j.chan == 1u) {
+        if (c->mode != kModeNew) return false;
+        if (j.box_new_it && *j.box_new_it != c->iter) return false;
+        if (!j.box_new_it && c->iter != 1) return false;
+        *thr = 0;
+        return true;
+    }
+    if (j.chan == 2u) {
+        if (c->mode != kModeNew || j.same_level || !j.rlast || *j.rlast < g0) return false;
+        if (!j.box_new_it && c->iter == 1) return false;  // terminals: iteration 1 is covered by channel 1
+        *thr = g0;
+        return true;
+    }
+    if (j.chan == 4u) {
+        if (c->mode != kModeProp || !j.same_level || !j.rlast || *j.rlast + 1u < c->g) return false;
+        *thr = c->g - 1u;
+        return true;
+    }
+    return false;
+}
+
 
 // Find q with pre[q] <= i < pre[q+1] (pre exclusive, non-decreasing).
 __host__ __device__ inline uint32_t find_owner(const uint32_t *pre, uint32_t nq, uint32_t i) {

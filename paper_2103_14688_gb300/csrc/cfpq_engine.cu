@@ -814,7 +814,8 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     const size_t words = kClasses * lv + kClasses * (nqa + 1) + 2 * lv  // static
                          + 2 * kClasses + 2 * kClasses * nqa              // gather lists and unit counters
                          + kClasses + 2 * kClasses * nqa                  // extraction lists
-                         + 1 + 3 * nqa;                                   // tensor-core lists
+                         + 1 + 3 * nqa                                    // tensor-core lists
+                         + 1 + hj.size();                                 // active tile jobs
     std::vector<uint32_t> ht(words, 0);
     size_t o = 0;
     memset(&T, 0, sizeof(T));
@@ -851,6 +852,9 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
     T.t_pre = take(nqa);
     T.t_job_beg = take(nqa);
     T.t_job_end = take(nqa);
+    T.aj_n = take(1);
+    T.aj = take(hj.size());
+    T.jobs = hj.empty() ? nullptr : tcjobs.as<TcJob>();
     ENG_CK(cudaMemcpyAsync(dbase, ht.data(), words * 4, cudaMemcpyHostToDevice, st));
     ENG_CK(cudaMemsetAsync(tc_err.p, 0, 16, st));
     ENG_CK(cudaMemsetAsync(done_counter.p, 0, 16, st));

@@ -945,6 +945,22 @@ __device__ void control_body(QCtl *const *ctls, uint32_t nq, QCtl *mirror, cudaG
         if (threadIdx.x < K) s_carry[threadIdx.x] += s_wsum[nw - 1][threadIdx.x];
         __syncthreads();
     }
+    // The tile jobs of the next pass: those of the live levels that take part
+    // (their activity depends only on the loop state just written).
+    if (T.jobs) {
+        __shared__ uint32_t s_aj;
+        if (threadIdx.x == 0) s_aj = 0u;
+        __syncthreads();
+        for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
+            const uint32_t jb = T.t_job_beg[q], je = T.t_job_end[q];
+            for (uint32_t j = jb; j < je; ++j) {
+                uint32_t thr, it, g;
+                if (tc_job_active(T.jobs[j], &thr, &it, &g)) T.aj[atomicAdd(&s_aj, 1u)] = j;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *T.aj_n = s_aj;
+    }
     if (threadIdx.x < K) {
         const int k = threadIdx.x;
         if (k < kClasses) T.g_next[k] = 0u;  // dynamic gather units of the next pass

@@ -236,41 +236,6 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 
 }  // namespace tc
 
-// Decide whether the job takes part in this pass and with which threshold.
-__device__ __forceinline__ bool tc_job_active(const TcJob &j, uint32_t *thr, uint32_t *iter, uint32_t *g) {
-    if (!j.ctl) {
-        *thr = 0;
-        *iter = 0;
-        *g = 0;
-        return true;
-    }
-    const QCtl *c = j.ctl;
-    if (c->phase != kPhaseRun || c->level != j.level) return false;
-    if (j.switchable && (j.box >= 32u || !((c->dense_mask >> j.box) & 1u))) return false;
-    *iter = c->iter;
-    *g = c->g;
-    const uint32_t g0 = c->g_iter_start;
-    if (j.chan == 1u) {
-        if (c->mode != kModeNew) return false;
-        if (j.box_new_it && *j.box_new_it != c->iter) return false;
-        if (!j.box_new_it && c->iter != 1) return false;
-        *thr = 0;
-        return true;
-    }
-    if (j.chan == 2u) {
-        if (c->mode != kModeNew || j.same_level || !j.rlast || *j.rlast < g0) return false;
-        if (!j.box_new_it && c->iter == 1) return false;  // terminals: iteration 1 is covered by channel 1
-        *thr = g0;
-        return true;
-    }
-    if (j.chan == 4u) {
-        if (c->mode != kModeProp || !j.same_level || !j.rlast || *j.rlast + 1u < c->g) return false;
-        *thr = c->g - 1u;
-        return true;
-    }
-    return false;
-}
-
 // The inner dimension of a job in this pass: compacted (the dirty rows listed
 // by k_tc_rows, operands expanded by k_tc_a8/k_tc_b8, multiplied by
 // k_tc_product_tma) when the job has buffers and the list fits them, else all
@@ -579,22 +544,21 @@ __device__ __forceinline__ uint32_t reserve_rows(unsigned long long *kc, uint32_
     return 0xFFFFFFFFu;
 }
 
-// Units (job, chunk) of the live jobs are numbered in job order; the CTA
-// takes those congruent to its index.  `body(J, c)` runs for each.
+// Units (job, chunk) of the pass's active jobs (the control kernel's list)
+// are numbered in list order; the CTA takes those congruent to its index.
+// `body(J, c)` runs for each.
 template <typename F>
 __device__ __forceinline__ void for_job_chunks(const TcJob *jobs, const ExecTables &T, uint32_t rows_per_chunk,
                                                F body) {
     uint32_t u0 = 0;
-    for (uint32_t q = 0; q < T.nq; ++q) {
-        const uint32_t jb = T.t_job_beg[q], je = T.t_job_end[q];
-        for (uint32_t j = jb; j < je; ++j) {
-            const TcJob &J = jobs[j];
-            const uint32_t chunks = (J.n + rows_per_chunk - 1) / rows_per_chunk;
-            const uint32_t first = (blockIdx.x + gridDim.x - (u0 % gridDim.x)) % gridDim.x;
-            u0 += chunks;
-            if (first >= chunks || !J.ys) continue;
-            for (uint32_t c = first; c < chunks; c += gridDim.x) body(J, c);
-        }
+    const uint32_t na = *T.aj_n;
+    for (uint32_t a = 0; a < na; ++a) {
+        const TcJob &J = jobs[T.aj[a]];
+        const uint32_t chunks = (J.n + rows_per_chunk - 1) / rows_per_chunk;
+        const uint32_t first = (blockIdx.x + gridDim.x - (u0 % gridDim.x)) % gridDim.x;
+        u0 += chunks;
+        if (first >= chunks || !J.ys) continue;
+        for (uint32_t c = first; c < chunks; c += gridDim.x) body(J, c);
     }
 }
 
@@ -773,61 +737,59 @@ __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, E
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     uint32_t u0 = 0;
-    for (uint32_t q = 0; q < T.nq; ++q) {
-        const uint32_t jb = T.t_job_beg[q], je = T.t_job_end[q];
-        for (uint32_t j = jb; j < je; ++j) {
-            const TcJob &J = jobs[j];
-            if (!J.ys) continue;
-            uint32_t thr, iter, g;
-            if (!tc_job_active(J, &thr, &iter, &g)) continue;
-            const KDim K = job_kdim(J, g);
-            if (!K.compact || K.kdim == 0u) continue;
-            uint32_t wc0, wc1;
-            job_window(J, &wc0, &wc1);
-            const uint32_t D = K.kdim, W = J.W, zend = min(W * 64u, wc1), zbeg = min(wc0, zend);
-            // (the window and n_pad are multiples of 128 columns; an FP4 job's
-            // K stage is 256 elements, zero-padded within kcap)
-            const uint32_t kpad = J.fp4 ? min((D + 255u) & ~255u, J.kcap) : (D + 127u) & ~127u;
-            const uint32_t kchunks = kpad / 32u, zchunks = (zend - zbeg) / 128u;
-            const uint32_t units = kchunks * zchunks;
-            const uint32_t first = (gw + nw - (u0 % nw)) % nw;
-            u0 += units;
-            // two units per step, both rows loaded before either is transposed
-            // (the list and row loads are a dependent pair)
-            for (uint32_t u = first; u < units; u += 2u * nw) {
-                uint4 row[2];
-                uint32_t k0s[2], zbs[2];
+    const uint32_t na = *T.aj_n;
+    for (uint32_t a = 0; a < na; ++a) {
+        const TcJob &J = jobs[T.aj[a]];
+        if (!J.ys) continue;
+        uint32_t thr, iter, g;
+        if (!tc_job_active(J, &thr, &iter, &g)) continue;
+        const KDim K = job_kdim(J, g);
+        if (!K.compact || K.kdim == 0u) continue;
+        uint32_t wc0, wc1;
+        job_window(J, &wc0, &wc1);
+        const uint32_t D = K.kdim, W = J.W, zend = min(W * 64u, wc1), zbeg = min(wc0, zend);
+        // (the window and n_pad are multiples of 128 columns; an FP4 job's
+        // K stage is 256 elements, zero-padded within kcap)
+        const uint32_t kpad = J.fp4 ? min((D + 255u) & ~255u, J.kcap) : (D + 127u) & ~127u;
+        const uint32_t kchunks = kpad / 32u, zchunks = (zend - zbeg) / 128u;
+        const uint32_t units = kchunks * zchunks;
+        const uint32_t first = (gw + nw - (u0 % nw)) % nw;
+        u0 += units;
+        // two units per step, both rows loaded before either is transposed
+        // (the list and row loads are a dependent pair)
+        for (uint32_t u = first; u < units; u += 2u * nw) {
+            uint4 row[2];
+            uint32_t k0s[2], zbs[2];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t uu = u + (uint32_t)h * nw;
-                    k0s[h] = uu < units ? (uu / zchunks) * 32u : D;
-                    zbs[h] = zbeg + (uu % zchunks) * 128u;
-                    const uint32_t k = k0s[h] + (uint32_t)lane;
-                    row[h] = make_uint4(0u, 0u, 0u, 0u);
-                    if (uu < units && k < D)
-                        row[h] = *reinterpret_cast<const uint4 *>(J.B + (size_t)J.ys[k] * W + (zbs[h] >> 6));
-                }
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t uu = u + (uint32_t)h * nw;
+                k0s[h] = uu < units ? (uu / zchunks) * 32u : D;
+                zbs[h] = zbeg + (uu % zchunks) * 128u;
+                const uint32_t k = k0s[h] + (uint32_t)lane;
+                row[h] = make_uint4(0u, 0u, 0u, 0u);
+                if (uu < units && k < D)
+                    row[h] = *reinterpret_cast<const uint4 *>(J.B + (size_t)J.ys[k] * W + (zbs[h] >> 6));
+            }
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (u + (uint32_t)h * nw >= units) continue;  // (uniform over the warp)
-                    const uint32_t parts[4] = {row[h].x, row[h].y, row[h].z, row[h].w};
+            for (int h = 0; h < 2; ++h) {
+                if (u + (uint32_t)h * nw >= units) continue;  // (uniform over the warp)
+                const uint32_t parts[4] = {row[h].x, row[h].y, row[h].z, row[h].w};
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        const uint32_t bits = parts[p], z0 = zbs[h] + 32u * (uint32_t)p;
-                        uint32_t mine = 0u;
+                for (int p = 0; p < 4; ++p) {
+                    const uint32_t bits = parts[p], z0 = zbs[h] + 32u * (uint32_t)p;
+                    uint32_t mine = 0u;
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) {
-                            const uint32_t m = __ballot_sync(0xffffffffu, (bits >> c) & 1u);
-                            if (lane == c) mine = m;  // bit i: row ys[k0 + i] has column z0 + c
-                        }
-                        unsigned char *rowp = J.b8 + (size_t)(z0 + (uint32_t)lane) * J.kstride;
-                        if (J.fp4) {
-                            *reinterpret_cast<uint4 *>(rowp + k0s[h] / 2u) = tc::expand32_e2m1(mine);
-                        } else {
-                            uint4 *dst = reinterpret_cast<uint4 *>(rowp + k0s[h]);
-                            dst[0] = tc::expand16(mine & 0xFFFFu, 0x38u);
-                            dst[1] = tc::expand16(mine >> 16, 0x38u);
-                        }
+                    for (int c = 0; c < 32; ++c) {
+                        const uint32_t m = __ballot_sync(0xffffffffu, (bits >> c) & 1u);
+                        if (lane == c) mine = m;  // bit i: row ys[k0 + i] has column z0 + c
+                    }
+                    unsigned char *rowp = J.b8 + (size_t)(z0 + (uint32_t)lane) * J.kstride;
+                    if (J.fp4) {
+                        *reinterpret_cast<uint4 *>(rowp + k0s[h] / 2u) = tc::expand32_e2m1(mine);
+                    } else {
+                        uint4 *dst = reinterpret_cast<uint4 *>(rowp + k0s[h]);
+                        dst[0] = tc::expand16(mine & 0xFFFFu, 0x38u);
+                        dst[1] = tc::expand16(mine >> 16, 0x38u);
                     }
                 }
             }

@@ -36,7 +36,9 @@ def test_tune_measures_and_chooses(C):
     rates = {C.CFPQ_TILES_FP8: t.fp8_tflops, C.CFPQ_TILES_FP4: t.fp4_tflops, C.CFPQ_TILES_FP8_128: t.fp8_128_tflops,
              C.CFPQ_TILES_NVFP4: t.nvfp4_tflops}
     assert all(v > 0 for v in rates.values())
-    assert t.tile_format == max(rates, key=rates.get)
+    # the built-in FP4 kernel unless another is more than 3% faster
+    best = max(rates, key=rates.get)
+    assert t.tile_format == (best if rates[best] > 1.03 * rates[C.CFPQ_TILES_FP4] else C.CFPQ_TILES_FP4)
     for ratio, gbs in ((t.edge_ratio, t.gather_gbs), (t.edge_ratio_hbm, t.gather_gbs_hbm)):
         want = rates[t.tile_format] * 1e3 / (16.0 * gbs)
         assert 8 <= ratio <= 4096
