@@ -854,6 +854,8 @@ struct JobCache {
     bool ok = false;
 };
 
+constexpr uint32_t kGroupCols = 8;  // column tiles per group of the tile walk
+
 // ROWS: output rows per tile, 128, or 256 (two accumulators, PAIR).  COLS:
 // output columns per tile, 256 (FP8), or 192 (FP4: the two accumulators
 // leave TMEM columns for the scale factors).  KSTAGE: elements of K per
@@ -869,18 +871,24 @@ __device__ __forceinline__ bool next_tile(const TcJob *jobs, const ExecTables &T
                 li += ((jc.li1 - 1u - li) / gridDim.x) * gridDim.x;
                 continue;
             }
-            // Column-major tile order: CTAs running side by side share the
-            // B tile (256 columns x K) and each reads its own A tile (128
-            // rows x K), half the operand bytes of the row-major order when
-            // the operands do not fit L2.  A channel-1 job walks only the
-            // tile rows its row list fills.
+            // Grouped tile order: the column tiles form groups of
+            // kGroupCols; a group is walked row tile by row tile, its
+            // columns inner.  CTAs running side by side then share each A
+            // tile (ROWS rows x K) kGroupCols times and each B tile (COLS
+            // columns x K) about gridDim / kGroupCols times, and A is read
+            // once per group instead of once per column tile (a plain
+            // column-major walk re-read A -- n x K operand bytes, beyond L2
+            // at n = 65536 -- for every column tile).  A channel-1 job walks
+            // only the tile rows its row list fills.
             const uint32_t t = li - jc.li0, mt = (jc.mlim + ROWS - 1u) / ROWS;
             if (t >= mt * jc.ntn) {  // past the job's row tiles: the rest of the job too
                 li += ((jc.li1 - 1u - li) / gridDim.x) * gridDim.x;
                 continue;
             }
-            tl.m0 = (t % mt) * ROWS;
-            tl.n0 = (t / mt) * COLS;
+            const uint32_t gsz = mt * kGroupCols, grp = t / gsz, within = t - grp * gsz;
+            const uint32_t gcols = min(kGroupCols, jc.ntn - grp * kGroupCols);
+            tl.m0 = (within / gcols) * ROWS;
+            tl.n0 = (grp * kGroupCols + within % gcols) * COLS;
             // another rank's columns (rank windows are multiples of 256
             // columns; a 192-column tile may straddle one and is masked)
             if (tl.n0 + COLS <= jc.c0 || tl.n0 >= jc.c1) continue;
