@@ -527,6 +527,10 @@ def run_dyck(args):
         "autotune": tuning,
         "closure_time_split_ms": {"gather": ps.ms_gather, "tile_operands": ps.ms_tile_operands,
                                   "tile_products": ps.ms_tile_products, "host_loop_result_equal": prof_equal},
+        "tile_operands": {"bytes_expanded": ps.tile_operand_bytes,
+                          "write_gbs": ps.tile_operand_bytes / max(ps.ms_tile_operands, 1e-9) / 1e6,
+                          "note": "0/1 operand bytes written by k_tc_a8/k_tc_b8 over the operand kernels' event time "
+                                  "(which also lists the dirty rows and new-edge columns)"},
         "closure_bool_gops": stats.row_ors * stats.row_bytes * 8 / (step_ms / 1000.0) / 1e9,
         "closure_bool_gops_paper_accounting": (cbits + m3bits) * Nq / (step_ms / 1000.0) / 1e9,
         "tensor_tflops_issued": stats.tile_kstages * TILE_FLOP_PER_KSTAGE / (step_ms / 1000.0) / 1e12,

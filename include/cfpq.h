@@ -170,6 +170,7 @@ typedef struct {
     double ms_tile_products;   /* tcgen05 tile-product launches */
     uint32_t gather_launches;  /* row-gather launches timed */
     uint32_t tile_launches;    /* passes whose tile-product launches were timed */
+    uint64_t tile_operand_bytes; /* bytes of 0/1 operands the tile jobs expanded (A and B) */
 } cfpq_run_stats;
 
 /* Result of the autotuner (cfpq_tune). */

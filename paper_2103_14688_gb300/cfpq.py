@@ -70,7 +70,8 @@ class cfpq_run_stats(Structure):
                 ("ms_setup", c_double), ("ms_loop", c_double),
                 ("closure_launches", c_uint32), ("pad_", c_uint32),
                 ("tile_kstages", c_uint64), ("ms_gather", c_double), ("ms_tile_operands", c_double),
-                ("ms_tile_products", c_double), ("gather_launches", c_uint32), ("tile_launches", c_uint32)]
+                ("ms_tile_products", c_double), ("gather_launches", c_uint32), ("tile_launches", c_uint32),
+                ("tile_operand_bytes", c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -78,6 +78,7 @@ void fill_stats(cfpq_run_stats *s, const QCtl &c, const QueryDev &q, double ms) 
     s->row_ors = c.row_ors;
     s->tile_mmas = c.tile_mmas;
     s->tile_kstages = c.tile_kstages;
+    s->tile_operand_bytes = c.tile_operand_bytes;
     s->closure_blocks = q.blocks.size();
     s->device_bytes = q.device_bytes;
     s->ms_total = ms;
@@ -972,6 +973,7 @@ extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_quer
         tot.row_ors += s.row_ors;
         tot.tile_mmas += s.tile_mmas;
         tot.tile_kstages += s.tile_kstages;
+        tot.tile_operand_bytes += s.tile_operand_bytes;
         tot.closure_blocks += s.closure_blocks;
         tot.device_bytes += s.device_bytes;
         if (status_of(ctls[i])) worst = status_of(ctls[i]);

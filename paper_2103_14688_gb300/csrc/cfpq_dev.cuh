@@ -86,6 +86,7 @@ struct QCtl {
     uint32_t col_v0, col_v1;
     uint32_t pad4;
     unsigned long long shard_new;
+    unsigned long long tile_operand_bytes;  // 0/1 operand bytes the tile jobs expanded (all passes)
 };
 
 // One source of an output block C[s,t]: a transition s -l-> u with t = u or

@@ -755,6 +755,13 @@ __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, E
         const uint32_t units = kchunks * zchunks;
         const uint32_t first = (gw + nw - (u0 % nw)) % nw;
         u0 += units;
+        if (first == 0u && lane == 0 && units && J.ctl) {
+            // operand bytes of the job in this pass: B's (this kernel) and A's (k_tc_a8)
+            const uint32_t ka = J.fp4 ? min((D + 255u) & ~255u, J.kcap) / 2u : (D + 127u) & ~127u;
+            const unsigned long long rows_a = J.covers_new ? *J.mcount : (unsigned long long)J.n;
+            atomicAdd(&J.ctl->tile_operand_bytes,
+                      (unsigned long long)(zend - zbeg) * (J.fp4 ? kpad / 2u : kpad) + rows_a * ka);
+        }
         // two units per step, both rows loaded before either is transposed
         // (the list and row loads are a dependent pair)
         for (uint32_t u = first; u < units; u += 2u * nw) {
