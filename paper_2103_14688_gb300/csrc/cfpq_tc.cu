@@ -728,11 +728,12 @@ __global__ void __launch_bounds__(256) k_tc_a8(const TcJob *__restrict__ jobs, E
 // b8[z][k] = B[ys[k]][z] as a 0/1 FP8 byte (B's listed rows transposed), for
 // the columns z of the rank's window below n_pad and k below the next
 // multiple of 128 of D (FP4 jobs: E2M1 nibbles, k below the next multiple of
-// 256 within kcap).  Unit of a warp: 32 listed rows x 128 columns.  Lane
-// l loads the 128 bits of row ys[k0 + l] at those columns (one 16-byte load);
-// for every 32 of those columns, 32 ballots transpose them (ballot c = column
-// z0 + c over the 32 rows, kept by lane c), and every lane writes its
-// column's 32 bytes.
+// 256 within kcap).  Unit of a warp: 64 listed rows x 256 columns (128 at
+// the end of a row).  Lane l loads 32 bytes of rows ys[k0 + l] and
+// ys[k0 + 32 + l] at those columns (whole 32-byte sectors); for every 32 of
+// the columns, 2 x 32 ballots transpose them (ballot c = column z0 + c over
+// 32 rows, kept by lane c), and every lane writes its column's 64 elements:
+// 32 bytes of E2M1 nibbles (a whole sector) or 64 FP8 bytes.
 __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, ExecTables T) {
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -751,7 +752,7 @@ __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, E
         // (the window and n_pad are multiples of 128 columns; an FP4 job's
         // K stage is 256 elements, zero-padded within kcap)
         const uint32_t kpad = J.fp4 ? min((D + 255u) & ~255u, J.kcap) : (D + 127u) & ~127u;
-        const uint32_t kchunks = kpad / 32u, zchunks = (zend - zbeg) / 128u;
+        const uint32_t kchunks = kpad / 64u, zchunks = (zend - zbeg + 255u) / 256u;
         const uint32_t units = kchunks * zchunks;
         const uint32_t first = (gw + nw - (u0 % nw)) % nw;
         u0 += units;
@@ -762,41 +763,48 @@ __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, E
             atomicAdd(&J.ctl->tile_operand_bytes,
                       (unsigned long long)(zend - zbeg) * (J.fp4 ? kpad / 2u : kpad) + rows_a * ka);
         }
-        // two units per step, both rows loaded before either is transposed
-        // (the list and row loads are a dependent pair)
-        for (uint32_t u = first; u < units; u += 2u * nw) {
-            uint4 row[2];
-            uint32_t k0s[2], zbs[2];
+        for (uint32_t u = first; u < units; u += nw) {
+            const uint32_t k0 = (u / zchunks) * 64u, z0 = zbeg + (u % zchunks) * 256u;
+            const uint32_t halves = min(2u, (zend - z0) / 128u);  // 128-column halves in the row
+            // rows k0 + lane (h = 0) and k0 + 32 + lane (h = 1), columns z0 .. z0 + 255
+            uint4 row[2][2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const uint32_t uu = u + (uint32_t)h * nw;
-                k0s[h] = uu < units ? (uu / zchunks) * 32u : D;
-                zbs[h] = zbeg + (uu % zchunks) * 128u;
-                const uint32_t k = k0s[h] + (uint32_t)lane;
-                row[h] = make_uint4(0u, 0u, 0u, 0u);
-                if (uu < units && k < D)
-                    row[h] = *reinterpret_cast<const uint4 *>(J.B + (size_t)J.ys[k] * W + (zbs[h] >> 6));
+                const uint32_t k = k0 + 32u * (uint32_t)h + (uint32_t)lane;
+                const uint4 *src = k < D ? reinterpret_cast<const uint4 *>(J.B + (size_t)J.ys[k] * W + (z0 >> 6))
+                                         : nullptr;
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+                    row[h][c] = (src && (uint32_t)c < halves) ? src[c] : make_uint4(0u, 0u, 0u, 0u);
             }
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (u + (uint32_t)h * nw >= units) continue;  // (uniform over the warp)
-                const uint32_t parts[4] = {row[h].x, row[h].y, row[h].z, row[h].w};
+            for (int c = 0; c < 2; ++c) {
+                if ((uint32_t)c >= halves) continue;  // (uniform over the warp)
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
-                    const uint32_t bits = parts[p], z0 = zbs[h] + 32u * (uint32_t)p;
-                    uint32_t mine = 0u;
+                    const uint32_t zc = z0 + 128u * (uint32_t)c + 32u * (uint32_t)p;
+                    uint32_t mine[2] = {0u, 0u};
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) {
-                        const uint32_t m = __ballot_sync(0xffffffffu, (bits >> c) & 1u);
-                        if (lane == c) mine = m;  // bit i: row ys[k0 + i] has column z0 + c
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t bits = p == 0 ? row[h][c].x : p == 1 ? row[h][c].y : p == 2 ? row[h][c].z
+                                                                                                     : row[h][c].w;
+#pragma unroll
+                        for (int b = 0; b < 32; ++b) {
+                            const uint32_t m = __ballot_sync(0xffffffffu, (bits >> b) & 1u);
+                            if (lane == b) mine[h] = m;  // bit i: row ys[k0 + 32 h + i] has column zc + b
+                        }
                     }
-                    unsigned char *rowp = J.b8 + (size_t)(z0 + (uint32_t)lane) * J.kstride;
+                    unsigned char *rowp = J.b8 + (size_t)(zc + (uint32_t)lane) * J.kstride;
                     if (J.fp4) {
-                        *reinterpret_cast<uint4 *>(rowp + k0s[h] / 2u) = tc::expand32_e2m1(mine);
+                        uint4 *dst = reinterpret_cast<uint4 *>(rowp + k0 / 2u);
+                        dst[0] = tc::expand32_e2m1(mine[0]);
+                        dst[1] = tc::expand32_e2m1(mine[1]);
                     } else {
-                        uint4 *dst = reinterpret_cast<uint4 *>(rowp + k0s[h]);
-                        dst[0] = tc::expand16(mine & 0xFFFFu, 0x38u);
-                        dst[1] = tc::expand16(mine >> 16, 0x38u);
+                        uint4 *dst = reinterpret_cast<uint4 *>(rowp + k0);
+                        dst[0] = tc::expand16(mine[0] & 0xFFFFu, 0x38u);
+                        dst[1] = tc::expand16(mine[0] >> 16, 0x38u);
+                        dst[2] = tc::expand16(mine[1] & 0xFFFFu, 0x38u);
+                        dst[3] = tc::expand16(mine[1] >> 16, 0x38u);
                     }
                 }
             }
