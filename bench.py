@@ -591,12 +591,25 @@ def batched_summary(count, device):
             want = solo.reachable_words(b)
             mism += int(not ((actx.batch_reachable_words(i, b) == want).all() and
                              (bctx.batch_reachable_words(i, b) == want).all()))
-    for c in (actx, bctx, solo):
+    # the plain bit-packed single-query path, one query at a time
+    plain = cfpq.Context(device=device, closure_mode=cfpq.CFPQ_CLOSURE_BITPACKED)
+    pt = 0.0
+    for g, r in qs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plain.load_graph(g)
+        plain.load_rsm(r)
+        plain.run()
+        torch.cuda.synchronize()
+        pt += time.perf_counter() - t0
+    for c in (actx, bctx, solo, plain):
         c.close()
     return {"queries": len(qs), "batched_qps": len(qs) / at, "batched_bitpacked_qps": len(qs) / bt,
-            "one_at_a_time_qps": len(qs) / st, "speedup_vs_one_at_a_time": st / at,
+            "one_at_a_time_qps": len(qs) / st, "one_at_a_time_bitpacked_qps": len(qs) / pt,
+            "speedup_vs_one_at_a_time": st / at, "speedup_vs_bitpacked_one_at_a_time": pt / at,
             "mismatches_vs_solo": mism, "split": split,
-            "timing": "host clock around one batch_run after a warm-up batch"}
+            "timing": "host clock around one batch_run after a warm-up batch; one at a time: AUTO and "
+                      "bit-packed contexts, each query staged and run"}
 
 
 def served_summary(lam, horizon, device):
@@ -625,20 +638,24 @@ def served_summary(lam, horizon, device):
             time.sleep(max(0.0, min(0.001, pending[i][0] - now)))
     el = time.perf_counter() - t_start
     srv.close()
-    solo = cfpq.Context(device=device)
-    solo.load_graph(wl.graph)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for j in wl.choice.tolist():
-        solo.load_rsm(wl.pool[j])
-        solo.run()
-    torch.cuda.synchronize()
-    solo_s = time.perf_counter() - t0
-    solo.close()
+    solo_t = {}
+    for name, mode in (("auto", cfpq.CFPQ_CLOSURE_AUTO), ("bitpacked", cfpq.CFPQ_CLOSURE_BITPACKED)):
+        solo = cfpq.Context(device=device, closure_mode=mode)
+        solo.load_graph(wl.graph)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j in wl.choice.tolist():
+            solo.load_rsm(wl.pool[j])
+            solo.run()
+        torch.cuda.synchronize()
+        solo_t[name] = time.perf_counter() - t0
+        solo.close()
+    solo_s = solo_t["auto"]
     lat = np.array(lat)
     return {"lambda": lam, "horizon_s": horizon, "queries": int(len(lat)), "qps": len(lat) / el,
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "one_at_a_time_qps": len(wl.choice) / solo_s}
+            "one_at_a_time_qps": len(wl.choice) / solo_s,
+            "one_at_a_time_bitpacked_qps": len(wl.choice) / solo_t["bitpacked"]}
 
 
 def _traffic_from_profiles(name):

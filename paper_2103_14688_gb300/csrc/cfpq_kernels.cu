@@ -343,7 +343,51 @@ __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
         r_end = min(it.row1, r_first + per * (uint32_t)rpw);
         r_step = (uint32_t)rpw;
     }
+    // Rows with nothing to do: when every source taking part in the pass
+    // reads only the iteration's new edges of a nonterminal (channel 1; the
+    // late passes of Dyck-4's x_i and p levels), a row has work only if one
+    // of those boxes has a new edge in it (its A2 stamp is this iteration),
+    // so a warp that owns whole rows (dynamic units) jumps from one such row
+    // to the next, 32 stamps per coalesced load, instead of visiting every
+    // row and source.
+    const uint32_t *skip_it[2] = {nullptr, nullptr};
+    bool skip_rows = false;
+    if constexpr (kDyn) {
+        skip_rows = it.nsrc <= 16u;
+        uint32_t ns = 0;
+        for (uint32_t k = 0; k < it.nsrc && skip_rows; ++k) {
+            const uint32_t chans = (uint32_t)(chpack >> (4u * k)) & 15u;
+            if (!chans) continue;
+            const SrcDesc &d = srcs[it.src0 + k];
+            if ((chans & ~9u) != 0u || d.csr_off != nullptr || d.nt_new_it == nullptr) {
+                skip_rows = false;
+                break;
+            }
+            if (ns < 2u && (ns == 0u || skip_it[0] != d.nt_new_it)) skip_it[ns++] = d.nt_new_it;
+            else if (skip_it[0] != d.nt_new_it && skip_it[1] != d.nt_new_it) skip_rows = false;
+        }
+        skip_rows = skip_rows && ns > 0u && lpr == 32;
+    }
     for (uint32_t rbase = r_first; rbase < r_end; rbase += r_step) {
+        if constexpr (kDyn) {
+            if (skip_rows) {
+                // the next row at or after rbase with a new edge in one of the boxes
+                bool found = false;
+                while (rbase < r_end) {
+                    const uint32_t b32 = rbase & ~31u, r = b32 + (uint32_t)lane;
+                    const bool w = r >= rbase && r < r_end &&
+                                   (skip_it[0][r] == iter || (skip_it[1] != nullptr && skip_it[1][r] == iter));
+                    const unsigned m = __ballot_sync(FULLMASK, w);
+                    if (m) {
+                        rbase = b32 + (uint32_t)(__ffs(m) - 1);
+                        found = true;
+                        break;
+                    }
+                    rbase = b32 + 32u;
+                }
+                if (!found) break;
+            }
+        }
         const uint32_t row = rbase + grp;
         bool valid = row < r_end;
         if constexpr (kDyn) valid = valid && (!it.rmask || ((it.rmask[row >> 6] >> (row & 63u)) & 1ull));
