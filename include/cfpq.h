@@ -115,6 +115,9 @@ typedef struct {
     uint32_t no_autotune;    /* 0 = the first AUTO query that may use tiles (n >= 2048) on a
                                 device runs the autotuner's probe once (cfpq_tune); 1 = use the
                                 built-in choices, never probe */
+    uint32_t tile_ratio;     /* cost model of the new-edge tiles: run them while M * K <
+                                tile_ratio * new edges (see cfpq_tuning::edge_ratio); 0 = the
+                                autotuner's (or built-in) value; the result does not depend on it */
 } cfpq_options;
 
 /* Recursive state machine (Sec. 2.3, Def. of an RSM).  States are numbered
@@ -182,6 +185,9 @@ typedef struct {
                                after compaction) run as tiles while M * K < edge_ratio * e; for
                                queries whose n x n closure blocks fit in half the L2 ... */
     uint32_t edge_ratio_hbm;/* ... and for larger ones (their gather reads rows from HBM) */
+    uint32_t edge_ratio_formula; /* tile rate / (16 x gather rate) from the measured rates: the
+                               search tried 1/2, 1, 2, 4 and 8 times it on the probe query in
+                               AUTO and kept the fastest as edge_ratio */
     int32_t probe_status;   /* CFPQ status of the probe (0 = ok) */
     double gather_gbs;      /* measured: bytes of source rows ORed per second by the row gather
                                (probe blocks of 8 MiB: L2-resident) */
@@ -282,11 +288,12 @@ int cfpq_set_start(cfpq_ctx *ctx, const uint64_t *bits, uint32_t n_boxes, uint32
  * with the bit-packed closure and with each tile kernel, times their kernel
  * groups with CUDA events, times reads of an L2-sized and an HBM-sized
  * buffer, and derives: the fastest tile kernel (AUTO's default) and the
- * cost-model ratio between that kernel's multiply-add rate and the gather's
- * row bytes (edge_ratio = tile rate / (16 x gather rate): one new edge costs
- * the gather n/8 bytes, a tile product 2n multiply-adds per (row, column) of
- * its M x K box), with the gather rate scaled by the measured HBM/L2 read
- * bandwidths for queries whose closure blocks exceed half the L2.  The result is kept per
+ * cost-model ratio (new-edge tiles run while M * K < ratio x new edges),
+ * searched around tile rate / (16 x gather rate) -- one new edge costs the
+ * gather n/8 bytes, a tile product 2n multiply-adds per (row, column) of its
+ * M x K box -- by timing the probe query in AUTO, and scaled by the measured
+ * L2/HBM read bandwidths for queries whose closure blocks exceed half the
+ * L2.  The result is kept per
  * device for the process; force = 1 measures again.  Every answer is the
  * same whichever choices are made.  The probe uses the context's stream and
  * allocator and about 3 GB of device memory for its duration.  Errors:

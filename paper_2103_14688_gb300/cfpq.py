@@ -51,7 +51,8 @@ class cfpq_options(Structure):
                 ("max_rounds", c_uint32), ("closure_mode", c_uint32), ("loop_mode", c_uint32),
                 ("profile", c_uint32), ("no_single_cta", c_uint32), ("gather_slices", c_uint32),
                 ("memory_budget", c_size_t), ("alloc", cfpq_alloc_fn), ("free", cfpq_free_fn),
-                ("alloc_user", c_void_p), ("tile_format", c_uint32), ("no_autotune", c_uint32)]
+                ("alloc_user", c_void_p), ("tile_format", c_uint32), ("no_autotune", c_uint32),
+                ("tile_ratio", c_uint32)]
 
 
 class cfpq_rsm(Structure):
@@ -79,7 +80,8 @@ class cfpq_run_stats(Structure):
 
 class cfpq_tuning(Structure):
     _fields_ = [("struct_size", c_uint32), ("tuned", c_uint32), ("tile_format", c_uint32), ("edge_ratio", c_uint32),
-                ("edge_ratio_hbm", c_uint32), ("probe_status", c_int32), ("gather_gbs", c_double),
+                ("edge_ratio_hbm", c_uint32), ("edge_ratio_formula", c_uint32), ("probe_status", c_int32),
+                ("gather_gbs", c_double),
                 ("gather_gbs_hbm", c_double), ("read_l2_gbs", c_double), ("read_hbm_gbs", c_double),
                 ("fp8_tflops", c_double), ("fp4_tflops", c_double), ("fp8_128_tflops", c_double),
                 ("nvfp4_tflops", c_double), ("probe_ms", c_double)]

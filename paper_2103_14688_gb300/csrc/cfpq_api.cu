@@ -28,7 +28,7 @@ void set_tiles(QueryDev &q, const cfpq_options &o, cudaStream_t st, uint32_t n) 
     const Tuning t = o.no_autotune ? Tuning{} : device_tuning(o, st, want, false);
     q.tile_kind = tile_kind_of(o.closure_mode, o.tile_format, t);
     q.tile_fp4 = tile_kind_fp4(q.tile_kind);
-    q.tile_ratio = tile_ratio_of(q.tile_kind, t, n);
+    q.tile_ratio = o.tile_ratio ? o.tile_ratio : tile_ratio_of(q.tile_kind, t, n);
 }
 }  // namespace cfpq
 

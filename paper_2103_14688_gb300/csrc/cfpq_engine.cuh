@@ -281,12 +281,14 @@ struct Tuning {
     double gather_gbs = 0, tflops[kTileKinds] = {0, 0, 0, 0}, probe_ms = 0;
     double read_l2_gbs = 0, read_hbm_gbs = 0;  // device reads of an L2-sized / HBM-sized buffer
     uint64_t l2_bytes = 0;
+    uint32_t ratio_l2 = 0;  // the searched cost-model ratio of `kind` (L2-resident queries)
     int status = 0;  // CFPQ status of the probe (0 = ok)
     // the gather's rate for closure blocks of `block_bytes`: measured on
     // L2-resident blocks, scaled by the read bandwidths beyond half the L2
-    double gather_rate(uint64_t block_bytes) const {
-        if (block_bytes * 2 <= l2_bytes || read_l2_gbs <= 0 || read_hbm_gbs <= 0) return gather_gbs;
-        return gather_gbs * std::min(1.0, read_hbm_gbs / read_l2_gbs);
+    double gather_rate(uint64_t block_bytes) const { return gather_gbs * memory_scale(block_bytes); }
+    double memory_scale(uint64_t block_bytes) const {
+        if (block_bytes * 2 <= l2_bytes || read_l2_gbs <= 0 || read_hbm_gbs <= 0) return 1.0;
+        return std::min(1.0, read_hbm_gbs / read_l2_gbs);
     }
 };
 // The device's tuning; runs the probe first when `run` and it has not run

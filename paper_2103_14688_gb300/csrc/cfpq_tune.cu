@@ -82,14 +82,17 @@ struct ProbeRsm {
     }
 };
 
-constexpr uint32_t kProbeN = 8192, kProbeDeg = 3, kProbeLabels = 8;
+constexpr uint32_t kProbeN = 8192, kProbeMaxDeg = 192, kProbeLabels = 8;
 constexpr double kTileFlopPerKstage = 2.0 * 128 * 256 * 128;
 
 // One probe run (the second of two: the first pays for set-up and module
-// loading); returns a CFPQ status.
-int probe_run(const cfpq_options &like, cudaStream_t st, uint32_t mode, uint32_t fmt, const ProbeRsm &pr,
-              const std::vector<uint32_t> &src, const std::vector<uint32_t> &lbl, const std::vector<uint32_t> &dst,
-              cfpq_run_stats *out) {
+// loading); returns a CFPQ status.  profiled: the host-driven loop with
+// per-kernel events (the kernel groups' rates); else the device loop, and
+// *ms gets the host time of the second run.
+int probe_run(const cfpq_options &like, cudaStream_t st, uint32_t mode, uint32_t fmt, uint32_t ratio,
+              bool profiled, const ProbeRsm &pr, const std::vector<uint32_t> &src,
+              const std::vector<uint32_t> &lbl, const std::vector<uint32_t> &dst, cfpq_run_stats *out,
+              double *ms = nullptr) {
     cfpq_options o;
     cfpq_default_options(&o);
     o.device = like.device;
@@ -98,8 +101,9 @@ int probe_run(const cfpq_options &like, cudaStream_t st, uint32_t mode, uint32_t
     o.alloc_user = like.alloc_user;
     o.closure_mode = mode;
     o.tile_format = fmt;
-    o.loop_mode = CFPQ_LOOP_HOST;
-    o.profile = 1;
+    o.tile_ratio = ratio;
+    o.loop_mode = profiled ? CFPQ_LOOP_HOST : CFPQ_LOOP_DEVICE;
+    o.profile = profiled ? 1u : 0u;
     o.no_single_cta = 1;
     o.no_autotune = 1;
     cfpq_ctx *c = nullptr;
@@ -108,7 +112,9 @@ int probe_run(const cfpq_options &like, cudaStream_t st, uint32_t mode, uint32_t
     rc = cfpq_load_graph(c, kProbeN, kProbeLabels, src.size(), src.data(), lbl.data(), dst.data());
     if (!rc) rc = cfpq_load_rsm(c, &pr.r);
     if (!rc) rc = cfpq_run(c, out);
-    if (!rc) rc = cfpq_run(c, out);
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!rc) rc = cfpq_run(c, out);  // (returns after reading the loop's final state)
+    if (ms) *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     cfpq_destroy(c);
     return rc;
 }
@@ -159,6 +165,12 @@ double read_gbs(Allocator &A, cudaStream_t st, int dev, size_t bytes, uint32_t r
     return best;
 }
 
+uint32_t ratio_for(double tflops, double gather_gbs) {
+    // M * K < e * rate_tile / (16 * rate_gather): TFLOP/s over GB/s is 1e3
+    const double r = tflops * 1e3 / (16.0 * gather_gbs);
+    return (uint32_t)std::min(4096.0, std::max(8.0, std::floor(r + 0.5)));
+}
+
 Tuning run_probe(const cfpq_options &like, cudaStream_t st) {
     Tuning t;
     const auto t0 = std::chrono::steady_clock::now();
@@ -177,19 +189,26 @@ Tuning run_probe(const cfpq_options &like, cudaStream_t st) {
     ProbeRsm pr;
     std::vector<uint32_t> src, lbl, dst;
     uint64_t seed = 0x2103146880000001ull;
-    for (uint32_t v = 0; v < kProbeN; ++v)
-        for (uint32_t k = 0; k < kProbeDeg; ++k) {
+    // out-degree Zipf(2.1) on 1..192 (mean about 3), targets and labels uniform
+    double cdf[kProbeMaxDeg], acc = 0;
+    for (uint32_t k = 1; k <= kProbeMaxDeg; ++k) cdf[k - 1] = (acc += std::pow((double)k, -2.1));
+    for (uint32_t v = 0; v < kProbeN; ++v) {
+        const double u = (double)(splitmix64(seed) >> 11) * 0x1.0p-53 * acc;
+        uint32_t deg = 1;
+        while (deg < kProbeMaxDeg && cdf[deg - 1] < u) ++deg;
+        for (uint32_t k = 0; k < deg; ++k) {
             src.push_back(v);
             dst.push_back((uint32_t)(splitmix64(seed) % kProbeN));
             lbl.push_back((uint32_t)(splitmix64(seed) % kProbeLabels));
         }
+    }
     cfpq_run_stats s;
-    int rc = probe_run(like, st, CFPQ_CLOSURE_BITPACKED, CFPQ_TILES_DEFAULT, pr, src, lbl, dst, &s);
+    int rc = probe_run(like, st, CFPQ_CLOSURE_BITPACKED, CFPQ_TILES_DEFAULT, 0, true, pr, src, lbl, dst, &s);
     if (!rc && s.ms_gather > 0) t.gather_gbs = (double)s.row_ors * (double)s.row_bytes / (s.ms_gather * 1e6);
     const uint32_t fmts[kTileKinds] = {CFPQ_TILES_FP8, CFPQ_TILES_FP8_128, CFPQ_TILES_FP4, CFPQ_TILES_NVFP4};
     for (uint32_t k = 0; k < kTileKinds && !rc; ++k) {
         const uint32_t mode = tile_kind_fp4(k) ? CFPQ_CLOSURE_TC_FP4 : CFPQ_CLOSURE_TC_FP8;
-        rc = probe_run(like, st, mode, fmts[k], pr, src, lbl, dst, &s);
+        rc = probe_run(like, st, mode, fmts[k], 0, true, pr, src, lbl, dst, &s);
         if (!rc && s.ms_tile_products > 0)
             t.tflops[k] = (double)s.tile_kstages * kTileFlopPerKstage / (s.ms_tile_products * 1e9);
     }
@@ -206,15 +225,32 @@ Tuning run_probe(const cfpq_options &like, cudaStream_t st) {
     for (uint32_t k = 0; k < kTileKinds; ++k)
         if (t.tflops[k] > 1.03 * t.tflops[best]) best = k;
     t.kind = best;
+    // The cost model's ratio, searched: the rate formula's value and 1/2,
+    // 2, 4, 8 times it, each timed on the whole probe query in AUTO with
+    // that kernel (the formula's rates average over all the gather's work,
+    // while the rows the new-edge tiles replace are the hub rows it handles
+    // worst).  The fastest is kept for L2-resident queries.
+    const uint32_t base = ratio_for(t.tflops[best], t.gather_gbs);
+    double best_ms = 0;
+    for (uint32_t f = 0; f < 5 && !rc; ++f) {
+        const uint32_t r = std::min<uint32_t>(4096u, std::max<uint32_t>(8u, f == 0 ? base / 2u : base << (f - 1)));
+        double ms = 0;
+        rc = probe_run(like, st, CFPQ_CLOSURE_AUTO, fmts[best], r, false, pr, src, lbl, dst, &s, &ms);
+        if (!rc && (best_ms == 0 || ms < best_ms)) {
+            best_ms = ms;
+            t.ratio_l2 = r;
+        }
+    }
+    t.probe_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (rc) {
+        t.status = rc;
+        t.kind = kTileFp4Pair;
+        return t;
+    }
     t.tuned = true;
     return t;
 }
 
-uint32_t ratio_for(double tflops, double gather_gbs) {
-    // M * K < e * rate_tile / (16 * rate_gather): TFLOP/s over GB/s is 1e3
-    const double r = tflops * 1e3 / (16.0 * gather_gbs);
-    return (uint32_t)std::min(4096.0, std::max(8.0, std::floor(r + 0.5)));
-}
 
 }  // namespace
 
@@ -241,6 +277,11 @@ uint32_t tile_kind_of(uint32_t mode, uint32_t fmt, const Tuning &t) {
 
 uint32_t tile_ratio_of(uint32_t kind, const Tuning &t, uint32_t n) {
     const uint64_t block = (uint64_t)n * (((uint64_t)n + 127u) & ~127ull) / 8u;
+    if (t.tuned && kind == t.kind && t.ratio_l2) {
+        // the searched ratio, for rows from HBM scaled like the gather's rate
+        const double r = (double)t.ratio_l2 / t.memory_scale(block);
+        return (uint32_t)std::min(4096.0, std::floor(r + 0.5));
+    }
     if (t.tuned && kind < kTileKinds && t.tflops[kind] > 0) return ratio_for(t.tflops[kind], t.gather_rate(block));
     return (uint32_t)(tile_kind_fp4(kind) ? kTileEdgeRatioFp4 : kTileEdgeRatio);
 }
@@ -259,6 +300,7 @@ extern "C" int cfpq_tune(cfpq_ctx *ctx, int force, cfpq_tuning *out) {
         out->tile_format = fmt_of[kind];
         out->edge_ratio = tile_ratio_of(kind, t, 8192u);        // 8 MiB blocks: L2-resident
         out->edge_ratio_hbm = tile_ratio_of(kind, t, 65536u);   // 512 MiB blocks
+        out->edge_ratio_formula = t.tflops[kind] > 0 && t.gather_gbs > 0 ? ratio_for(t.tflops[kind], t.gather_gbs) : 0u;
         out->probe_status = t.status;
         out->gather_gbs = t.gather_gbs;
         out->gather_gbs_hbm = t.gather_rate(~0ull >> 8);

@@ -39,10 +39,14 @@ def test_tune_measures_and_chooses(C):
     # the built-in FP4 kernel unless another is more than 3% faster
     best = max(rates, key=rates.get)
     assert t.tile_format == (best if rates[best] > 1.03 * rates[C.CFPQ_TILES_FP4] else C.CFPQ_TILES_FP4)
-    for ratio, gbs in ((t.edge_ratio, t.gather_gbs), (t.edge_ratio_hbm, t.gather_gbs_hbm)):
-        want = rates[t.tile_format] * 1e3 / (16.0 * gbs)
-        assert 8 <= ratio <= 4096
-        assert abs(ratio - min(4096.0, max(8.0, want))) <= 1.0
+    # the searched ratio: 1/2, 1, 2, 4 or 8 times the rate formula's value,
+    # scaled by the L2/HBM read bandwidths for queries beyond the L2
+    base = t.edge_ratio_formula
+    assert abs(base - min(4096.0, max(8.0, rates[t.tile_format] * 1e3 / (16.0 * t.gather_gbs)))) <= 1.0
+    cands = [min(4096, max(8, x)) for x in (base // 2, base, 2 * base, 4 * base, 8 * base)]
+    assert t.edge_ratio in cands
+    want_hbm = t.edge_ratio / min(1.0, t.read_hbm_gbs / t.read_l2_gbs)
+    assert abs(t.edge_ratio_hbm - min(4096.0, want_hbm)) <= 1.0
     # cached per device: a second call returns the same choice without a probe
     with C.Context() as ctx:
         t2 = ctx.tune()
