@@ -460,6 +460,13 @@ class Server:
             if stream is None:
                 with torch.cuda.device(device):
                     stream = torch.cuda.current_stream().cuda_stream
+            # without memory_budget the server admits queries into the device's
+            # free memory at creation: return PyTorch's cached blocks first (an
+            # earlier server's or context's buffers would otherwise count as used)
+            if not o.memory_budget:
+                with torch.cuda.device(device):
+                    torch.cuda.synchronize()
+                    torch.cuda.empty_cache()
         s, l, d = _u32(g.src), _u32(g.lbl), _u32(g.dst)
         h = c_void_p()
         rc = self.lib.cfpq_server_create(ctypes.byref(h), ctypes.byref(o), c_void_p(stream or 0), g.n, g.n_terminals,
