@@ -191,6 +191,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// As tmem_ld32, without waiting: the registers are valid after tmem_wait_ld.
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // 4 bits -> 4 bytes of 0/1 (bit i -> byte i).
 __device__ __forceinline__ uint32_t spread4(uint32_t b) { return ((b & 0xFu) * 0x00204081u) & 0x01010101u; }
 
@@ -1098,17 +1112,24 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
             if (__any_sync(0xffffffffu, to)) { to = true; break; }
             tc_after();
             const TcJob &J = *tl.J;
+            // three 32-column loads in flight per wait: two waits per tile
             uint32_t mask[6];
 #pragma unroll 1
-            for (int c = 0; c < 6; ++c) {
-                uint32_t v[32];
-                tmem_ld32(tmem + hh * 256u + 32u * (uint32_t)c + ((quarter * 32u) << 16), v);
-                uint32_t mb = 0u;
+            for (int c3 = 0; c3 < 6; c3 += 3) {
+                uint32_t v[3][32];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) mb |= (v[i] != 0u ? 1u : 0u) << i;
+                for (int c = 0; c < 3; ++c)
+                    tmem_ld32_nowait(tmem + hh * 256u + 32u * (uint32_t)(c3 + c) + ((quarter * 32u) << 16), v[c]);
+                tmem_wait_ld();
 #pragma unroll
-                for (int cc = 0; cc < 6; ++cc)
-                    if (cc == c) mask[cc] = mb;
+                for (int c = 0; c < 3; ++c) {
+                    uint32_t mb = 0u;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) mb |= (v[c][i] != 0u ? 1u : 0u) << i;
+#pragma unroll
+                    for (int cc = 0; cc < 6; ++cc)  // (constant indices keep mask in registers)
+                        if (cc == c3 + c) mask[cc] = mb;
+                }
             }
             tc_before();
             __syncwarp();
