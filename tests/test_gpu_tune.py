@@ -77,3 +77,14 @@ def test_no_autotune_and_bad_struct(C):
         t = C.cfpq_tuning()
         t.struct_size = 3
         assert ctx.lib.cfpq_tune(ctx.h, 0, ctypes.byref(t)) == C.CFPQ_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("ratio", [8, 4096])
+def test_tile_ratio_extremes_keep_the_answer(C, ratio):
+    """The cost ratio only moves new-edge products between the gather and the
+    tiles: at the smallest ratio the gather takes nearly all of them, at the
+    largest the tiles whenever their list fits; both answers are Oracle B's."""
+    g, r = W.dyck_zipf(3000, seed=23)
+    st, a = _answer(C, g, r, tile_ratio=ratio, no_single_cta=1)
+    assert st.tile_mmas > 0
+    assert (a == oracle.worklist(g, r)).all()
