@@ -922,6 +922,11 @@ extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_quer
     ctx->bexec.drop_graph();
     ctx->bqueries.clear();
     ctx->bgraphs.clear();
+    // the graphs and queries of the batch take their buffers from the slab
+    // (rewound, its chunks kept from the previous batch)
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    bind_slab(&ctx->bslab, &ctx->A, ctx->stream);
+    ctx->bslab.reset();
     std::string e;
     // one tile kernel for the batch: tuned for its largest graph
     uint32_t max_n = 0;
@@ -934,7 +939,7 @@ extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_quer
     for (uint32_t i = 0; i < n_queries; ++i) {
         const cfpq_query &qq = queries[i];
         std::unique_ptr<GraphDev> g(new GraphDev());
-        int rc = stage_graph(g.get(), &ctx->A, ctx->stream, qq.n_vertices, qq.n_terminals, qq.n_edges, qq.src,
+        int rc = stage_graph(g.get(), &ctx->bslab.A, ctx->stream, qq.n_vertices, qq.n_terminals, qq.n_edges, qq.src,
                              qq.label, qq.dst, false, &e);
         if (rc) return fail(ctx, rc, "query " + std::to_string(i) + ": " + e);
         std::unique_ptr<QueryDev> q(new QueryDev());
@@ -944,7 +949,7 @@ extern "C" int cfpq_batch_run(cfpq_ctx *ctx, uint32_t n_queries, const cfpq_quer
         rc = copy_rsm(qq.rsm, &q->rsm, &e);
         if (rc) return fail(ctx, rc, "query " + std::to_string(i) + ": " + e);
         q->g = g.get();
-        rc = q->prepare(&ctx->A, &e);
+        rc = q->prepare(&ctx->bslab.A, &e);
         if (rc) return fail(ctx, rc, "query " + std::to_string(i) + ": " + e);
         ctx->bgraphs.push_back(std::move(g));
         ctx->bqueries.push_back(std::move(q));

@@ -38,7 +38,9 @@ struct cfpq_ctx {
     bool shard_on = false;
     uint32_t shard_c0 = 0, shard_c1 = 0;
     DBuf shard_cnt;  // per box: new edges, new to this rank (k_shard_apply)
-    // batch
+    // batch (its graphs' and queries' buffers come from bslab, declared
+    // first so that it outlives them)
+    cfpq::SlabArena bslab;
     std::vector<std::unique_ptr<GraphDev>> bgraphs;
     std::vector<std::unique_ptr<QueryDev>> bqueries;
     Executor bexec;

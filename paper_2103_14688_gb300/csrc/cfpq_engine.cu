@@ -42,6 +42,45 @@ void Allocator::put(void *p, size_t bytes) {
     in_use -= std::min(in_use, bytes);
 }
 
+void *SlabArena::take(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    while (chunk < chunks.size()) {
+        if (chunks[chunk].second - used >= bytes) {
+            void *p = static_cast<char *>(chunks[chunk].first) + used;
+            used += bytes;
+            return p;
+        }
+        ++chunk;  // (the rest of this chunk stays unused until reset)
+        used = 0;
+    }
+    const size_t cb = std::max(chunk_bytes, bytes);
+    void *p = parent->get(cb, nullptr);
+    if (!p) return nullptr;
+    chunks.push_back({p, cb});
+    chunk = chunks.size() - 1;
+    used = bytes;
+    return p;
+}
+
+void SlabArena::release() {
+    for (auto &c : chunks)
+        if (parent) parent->put(c.first, c.second);
+    chunks.clear();
+    reset();
+}
+
+static void *slab_alloc(size_t bytes, void *, void *user) { return static_cast<SlabArena *>(user)->take(bytes); }
+static void slab_free(void *, size_t, void *, void *) {}
+
+void bind_slab(SlabArena *s, Allocator *parent, cudaStream_t st) {
+    s->parent = parent;
+    s->A.alloc = slab_alloc;
+    s->A.free = slab_free;
+    s->A.user = s;
+    s->A.stream = st;
+    s->A.budget = 0;  // the parent's budget applies to the chunks
+}
+
 // ---------------------------------------------------------------------------
 // RSM validation (Sec. 2.3, Def. of an RSM).
 // ---------------------------------------------------------------------------

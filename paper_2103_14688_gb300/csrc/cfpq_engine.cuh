@@ -114,6 +114,25 @@ struct Allocator {
     void put(void *p, size_t bytes);
 };
 
+// A bump allocator over large chunks taken from a parent allocator, for the
+// many buffers of a batch of queries (one parent call per chunk instead of
+// one per buffer; the parent may be a caller's callback, e.g. into
+// PyTorch).  Buffers handed out are never freed one by one: reset() rewinds
+// to the start and keeps the chunks for the next batch, release() returns
+// them to the parent.  `A` is an Allocator that draws from it.
+struct SlabArena {
+    Allocator *parent = nullptr;
+    std::vector<std::pair<void *, size_t>> chunks;
+    size_t chunk = 0, used = 0;  // current chunk and bytes used in it
+    size_t chunk_bytes = (size_t)1 << 30;
+    Allocator A;
+    void *take(size_t bytes);
+    void reset() { chunk = 0; used = 0; A.in_use = 0; }
+    void release();
+    ~SlabArena() { release(); }
+};
+void bind_slab(SlabArena *s, Allocator *parent, cudaStream_t st);
+
 // An owned device buffer.
 struct DBuf {
     Allocator *A = nullptr;
