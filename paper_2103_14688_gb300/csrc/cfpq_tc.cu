@@ -744,10 +744,10 @@ __global__ void __launch_bounds__(256) k_tc_a8(const TcJob *__restrict__ jobs, E
 // multiple of 128 of D (FP4 jobs: E2M1 nibbles, k below the next multiple of
 // 256 within kcap).  Unit of a warp: 64 listed rows x 256 columns (128 at
 // the end of a row).  Lane l loads 32 bytes of rows ys[k0 + l] and
-// ys[k0 + 32 + l] at those columns (whole 32-byte sectors); for every 32 of
-// the columns, 2 x 32 ballots transpose them (ballot c = column z0 + c over
-// 32 rows, kept by lane c), and every lane writes its column's 64 elements:
-// 32 bytes of E2M1 nibbles (a whole sector) or 64 FP8 bytes.
+// ys[k0 + 32 + l] at those columns (whole 32-byte sectors); every 32 x 32
+// bit block is transposed across the warp with shuffles (lane c then holds
+// column z0 + c over the 32 rows), and every lane writes its column's 64
+// elements: 32 bytes of E2M1 nibbles (a whole sector) or 64 FP8 bytes.
 __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, ExecTables T) {
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -797,16 +797,14 @@ __global__ void __launch_bounds__(256) k_tc_b8(const TcJob *__restrict__ jobs, E
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
                     const uint32_t zc = z0 + 128u * (uint32_t)c + 32u * (uint32_t)p;
-                    uint32_t mine[2] = {0u, 0u};
+                    uint32_t mine[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const uint32_t bits = p == 0 ? row[h][c].x : p == 1 ? row[h][c].y : p == 2 ? row[h][c].z
                                                                                                      : row[h][c].w;
-#pragma unroll
-                        for (int b = 0; b < 32; ++b) {
-                            const uint32_t m = __ballot_sync(0xffffffffu, (bits >> b) & 1u);
-                            if (lane == b) mine[h] = m;  // bit i: row ys[k0 + 32 h + i] has column zc + b
-                        }
+                        // lane l holds columns zc .. zc + 31 of row ys[k0 + 32 h + l]; after
+                        // the shuffle transpose lane c holds column zc + c (bit i: row i)
+                        mine[h] = tc::transpose32(bits, lane);
                     }
                     unsigned char *rowp = J.b8 + (size_t)(zc + (uint32_t)lane) * J.kstride;
                     if (J.fp4) {
