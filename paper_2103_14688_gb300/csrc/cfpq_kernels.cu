@@ -244,6 +244,7 @@ struct GatherDyn {
 // than 256-4096 bits to enumerate to a second launch split over 16 warps
 // gained 1-2% in AUTO and cost 10-20% bit-packed: not kept.)
 constexpr uint32_t kGatherParts = 8;
+constexpr uint32_t kStrideWaves = 8;  // launch_gather / launch_extract: waves of resident CTAs at most
 
 template <int VPL, bool NT>
 __global__ void __launch_bounds__(256, GatherOcc<VPL>::value)
@@ -1284,16 +1285,21 @@ cudaError_t launch_gather(int vpl, bool nt, const GItem *items, uint32_t n_items
     int dev = 0;
     cudaGetDevice(&dev);
     const uint32_t sms = (dev >= 0 && dev < 64 && g_gather_sms[dev]) ? (uint32_t)g_gather_sms[dev] : 0u;
-    // dynamic scheduling: a persistent grid (resident CTAs), at most one warp per unit
+    // dynamic scheduling: a persistent grid (resident CTAs), at most one warp
+    // per unit; otherwise one CTA per live item, at most kStrideWaves waves of
+    // resident CTAs (the CTAs stride over the live items): n_items bounds the
+    // live items of any pass, and a batch's pass with few live queries would
+    // otherwise launch tens of thousands of CTAs that exit at once
     auto grid_of = [&](bool dyn, int occ) -> uint32_t {
-        if (!dyn || !sms) return n_items;
+        if (!sms) return n_items;
+        if (!dyn) return std::min<uint32_t>(n_items, sms * (uint32_t)occ * kStrideWaves);
         const uint32_t want = (n_items * kGatherParts + 7u) / 8u;
         return std::max<uint32_t>(1u, std::min<uint32_t>(want, sms * (uint32_t)occ));
     };
 #define CFPQ_GATHER(V)                                                                                          \
     if (nt) k_gather<V, true><<<grid_of(GatherDyn<V, true>::on, GatherOcc<V>::value), 256, GatherRing<V>::bytes, \
                                 st>>>(items, srcs, T, cls);                                                     \
-    else k_gather<V, false><<<n_items, 256, 0, st>>>(items, srcs, T, cls);
+    else k_gather<V, false><<<grid_of(false, GatherOcc<V>::value), 256, 0, st>>>(items, srcs, T, cls);
     switch (vpl) {
         case 1: CFPQ_GATHER(1) break;
         case 2: CFPQ_GATHER(2) break;
@@ -1335,12 +1341,17 @@ cudaError_t launch_extract(int vpl, const XItem *items, uint32_t n_items, const 
                            int use_handle, int *running_out, unsigned int *done_counter, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     FusedControl fc{ctls, mirror, running_out, done_counter, h, nq, use_handle, ctls != nullptr ? 1 : 0};
+    // (the CTAs stride over the live items; see launch_gather)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint32_t sms = (dev >= 0 && dev < 64 && g_gather_sms[dev]) ? (uint32_t)g_gather_sms[dev] : 0u;
+    const uint32_t grid = sms ? std::min<uint32_t>(n_items, sms * 8u * kStrideWaves) : n_items;
     switch (vpl) {
-        case 1: k_extract<1><<<n_items, 256, 0, st>>>(items, fds, T, cls, fc); break;
-        case 2: k_extract<2><<<n_items, 256, 0, st>>>(items, fds, T, cls, fc); break;
-        case 4: k_extract<4><<<n_items, 256, 0, st>>>(items, fds, T, cls, fc); break;
-        case 8: k_extract<8><<<n_items, 256, 0, st>>>(items, fds, T, cls, fc); break;
-        case 16: k_extract<16><<<n_items, 256, 0, st>>>(items, fds, T, cls, fc); break;
+        case 1: k_extract<1><<<grid, 256, 0, st>>>(items, fds, T, cls, fc); break;
+        case 2: k_extract<2><<<grid, 256, 0, st>>>(items, fds, T, cls, fc); break;
+        case 4: k_extract<4><<<grid, 256, 0, st>>>(items, fds, T, cls, fc); break;
+        case 8: k_extract<8><<<grid, 256, 0, st>>>(items, fds, T, cls, fc); break;
+        case 16: k_extract<16><<<grid, 256, 0, st>>>(items, fds, T, cls, fc); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
