@@ -1136,15 +1136,26 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
             const uint32_t x = mr >= tl.mlim ? J.n : (J.covers_new ? J.xs[mr] : mr);
             bool ch = false;
             if (x < J.n) {
+                // read the three output words first and OR only those that
+                // gain a bit (the bits of a block are only ever set, so a
+                // stale read costs at most a redundant atomic): after the
+                // first passes most products add nothing new
+                uint64_t add[3], cur[3];
 #pragma unroll
                 for (int w = 0; w < 3; ++w) {
                     const uint32_t ww = (tl.n0 >> 6) + (uint32_t)w, z = ww * 64u;
-                    uint64_t add = (uint64_t)mask[2 * w] | ((uint64_t)mask[2 * w + 1] << 32);
-                    if (z < jc.c0 || z >= jc.c1) add = 0ull;  // another rank's columns
-                    if (ww >= J.W || !add) continue;
+                    add[w] = (uint64_t)mask[2 * w] | ((uint64_t)mask[2 * w + 1] << 32);
+                    if (z < jc.c0 || z >= jc.c1 || ww >= J.W) add[w] = 0ull;  // another rank's columns; past the row
+                    cur[w] = add[w] ? __ldcg(reinterpret_cast<const unsigned long long *>(J.out + (size_t)x * J.W + ww))
+                                    : 0ull;
+                }
+#pragma unroll
+                for (int w = 0; w < 3; ++w) {
+                    if (!(add[w] & ~cur[w])) continue;
+                    const uint32_t ww = (tl.n0 >> 6) + (uint32_t)w;
                     const uint64_t old = atomicOr(
-                        reinterpret_cast<unsigned long long *>(J.out + (size_t)x * J.W + ww), (unsigned long long)add);
-                    if (add & ~old) ch = true;
+                        reinterpret_cast<unsigned long long *>(J.out + (size_t)x * J.W + ww), (unsigned long long)add[w]);
+                    if (add[w] & ~old) ch = true;
                 }
             }
             if (ch && J.out_stamp) J.out_stamp[x] = tl.g;
@@ -1195,14 +1206,22 @@ __global__ void __launch_bounds__(tc2::kThreads, 1)
                 bool ch = false;
                 if (x < J.n) {
                     const uint32_t w0 = (tl.n0 >> 6) + half * 2u;
+                    // (read first, OR only the words that gain a bit: as in the E2M1 epilogue)
+                    uint64_t add[2], cur[2];
 #pragma unroll
                     for (int w = 0; w < 2; ++w) {
                         const uint32_t ww = w0 + (uint32_t)w;
-                        const uint64_t add = (uint64_t)mask[hh][2 * w] | ((uint64_t)mask[hh][2 * w + 1] << 32);
-                        if (ww >= J.W || !add) continue;
+                        add[w] = ww < J.W ? ((uint64_t)mask[hh][2 * w] | ((uint64_t)mask[hh][2 * w + 1] << 32)) : 0ull;
+                        cur[w] = add[w] ? __ldcg(reinterpret_cast<const unsigned long long *>(J.out + (size_t)x * J.W + ww))
+                                        : 0ull;
+                    }
+#pragma unroll
+                    for (int w = 0; w < 2; ++w) {
+                        if (!(add[w] & ~cur[w])) continue;
                         const uint64_t old = atomicOr(
-                            reinterpret_cast<unsigned long long *>(J.out + (size_t)x * J.W + ww), (unsigned long long)add);
-                        if (add & ~old) ch = true;
+                            reinterpret_cast<unsigned long long *>(J.out + (size_t)x * J.W + w0 + (uint32_t)w),
+                            (unsigned long long)add[w]);
+                        if (add[w] & ~old) ch = true;
                     }
                 }
                 if (ch && J.out_stamp) J.out_stamp[x] = tl.g;  // both column halves may stamp: same value
