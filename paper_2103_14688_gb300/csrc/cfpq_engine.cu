@@ -624,7 +624,10 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
         }
         const int vi = vpl_index(q.vpl);
         const uint32_t rows_per_step = 8u * (32u / q.lpr);
-        const uint32_t rpi = std::max<uint32_t>(64u, rows_per_step * 4u);
+        // rows per work item (extraction; the gather's narrow rows), times the
+        // executor's item scale (the server's larger items keep its frequent
+        // re-assembly cheap), at most 1024
+        const uint32_t rpi = std::min<uint32_t>(1024u, std::max<uint32_t>(64u, rows_per_step * 4u) * item_scale);
         // product jobs: tcgen05 tiles of 128 rows x 256 columns
         const uint32_t tiles_m = (q.n + 127u) / 128u, tiles_n = (q.n + 255u) / 256u;
         for (uint32_t L = 0; L <= q.n_levels; ++L) {
@@ -666,7 +669,8 @@ int Executor::assemble(Allocator *A, cudaStream_t st, std::string *err) {
                 if (q.gather_slices) n_slices = sliceable ? std::min<uint32_t>(q.gather_slices, 16u) : 1u;
                 // nonterminal blocks of wide rows: 128-row items (measured on
                 // Dyck-4; the CSR blocks of the RPQ bench prefer 64)
-                const uint32_t rows_item = (has_nt && q.W >= 256u) ? std::max<uint32_t>(rpi, 128u) : rpi;
+                const uint32_t rows_item =
+                    (has_nt && q.W >= 256u) ? std::min<uint32_t>(1024u, std::max<uint32_t>(rpi, 128u * item_scale)) : rpi;
                 // the gather keeps an item's row mask in 16 words of shared memory
                 if (rows_item > 1024u || rows_item % 64u != 0u) {
                     *err = "gather items: rows per item must be a multiple of 64 and at most 1024";

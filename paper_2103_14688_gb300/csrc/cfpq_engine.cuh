@@ -338,6 +338,7 @@ struct Executor {
     uint32_t max_live[kClasses] = {0};  // bound on live items of a pass: sum over queries of the largest level
     uint32_t n_tcjobs = 0, max_tc_tiles = 0, max_tc_w = 0;
     uint32_t tile_kind = kTileFp8Pair;  // the tile jobs' kernel (every query of an executor shares it)
+    uint32_t item_scale = 1;            // work items span item_scale times the usual rows (a power of 2)
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream: capture is not allowed on the legacy default stream

@@ -86,6 +86,10 @@ int cfpq_server_create(cfpq_server **out, const cfpq_options *opt, void *stream,
         s->A.free = s->opt.free;
         s->A.user = s->opt.alloc_user;
         s->A.stream = s->stream;
+        // work items of 4x the rows: the running set changes (and the work
+        // lists are re-assembled on the host) at most every step, and the
+        // assembly's cost grows with the number of items
+        s->exec.item_scale = 4;
         std::string e;
         int rc = stage_graph(&s->graph, &s->A, s->stream, n_vertices, n_terminals, n_edges, src, label, dst, false, &e);
         if (rc) return rc;
