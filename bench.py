@@ -361,7 +361,7 @@ def _roofline_gather(st, peaks, n):
             "accounting": "(source rows ORed + 2 x output rows changed) x row bytes"}
 
 
-def _roofline_tiles(st, peaks, n, fp4=False):
+def _roofline_tiles(st, peaks, n, fp4=False, nv=False):
     """Tile products: dense 0/1 multiply-adds over the compacted inner
     dimension (2 x 128 x 256 x 128 per K stage) over the product launches'
     event time, against the peak of the tiles' format (measured sustained
@@ -376,7 +376,8 @@ def _roofline_tiles(st, peaks, n, fp4=False):
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
             "traffic": _traffic_from_profiles(f"k_tc_product_tma_{'fp4_' if fp4 else ''}dyck4_n{n}"),
-            "kernel": "cfpq::k_tc_product_tma (tcgen05 " + ("kind::mxf4, 0/1 E2M1" if fp4 else "kind::f8f6f4") + ")",
+            "kernel": "cfpq::k_tc_product_tma (tcgen05 " + (("kind::mxf4nvf4" if nv else "kind::mxf4") + ", 0/1 E2M1"
+                                                           if fp4 else "kind::f8f6f4") + ")",
             "peak_source": f"{peaks['kind']} bf16_tflops_sustained x {ratio} (nominal {fmt}/bf16)",
             "launches_timed": launches, "flop_per_launch": flop / launches,
             "ms_per_launch": st.ms_tile_products / launches,
@@ -506,7 +507,10 @@ def run_dyck(args):
     pctx.close()
     peaks = _peaks()
     roof_g = _roofline_gather(ps, peaks, n)
-    roof_t = _roofline_tiles(ps, peaks, n, fp4=True) if ps.tile_launches else None  # AUTO's default tiles: FP4
+    # AUTO's tiles are the autotuner's kernel (E2M1 on GB300): its format sets the peak
+    tiles_fp4 = tuning.get("tile_format") in (cfpq.CFPQ_TILES_FP4, cfpq.CFPQ_TILES_NVFP4)
+    roof_t = (_roofline_tiles(ps, peaks, n, fp4=tiles_fp4, nv=tuning.get("tile_format") == cfpq.CFPQ_TILES_NVFP4)
+              if ps.tile_launches else None)
     dominant, other = (roof_g, roof_t)
     if roof_t is not None and ps.ms_tile_products > ps.ms_gather:
         dominant, other = roof_t, roof_g
