@@ -284,7 +284,8 @@ int cfpq_set_start(cfpq_ctx *ctx, const uint64_t *bits, uint32_t n_boxes, uint32
 /* Autotuner of the closure's tile products (no counterpart in the paper,
  * whose closure runs on a CPU Boolean-matrix library).  On the context's
  * device it runs a probe query -- Dyck-4 (S -> S S | o_i c_i | o_i S c_i)
- * on a seeded graph of 8192 vertices with 3 out-edges each, 8 labels --
+ * on a seeded graph of 8192 vertices with Zipf(2.1) out-degrees (mean
+ * about 3), 8 labels --
  * with the bit-packed closure and with each tile kernel, times their kernel
  * groups with CUDA events, times reads of an L2-sized and an HBM-sized
  * buffer, and derives: the fastest tile kernel (AUTO's default) and the

@@ -6,8 +6,9 @@
 // 128 x 256, E2M1 256 x 192 with 32-element UE8M0 or 16-element UE4M3
 // scales).  Which is faster depends on the device, so this file measures
 // it: once per device and process it runs a probe query through the
-// library's own API -- Dyck-4 on a seeded graph of 8192 vertices, 3
-// out-edges each, 8 labels -- with the bit-packed closure and with every
+// library's own API -- Dyck-4 on a seeded graph of 8192 vertices with
+// Zipf(2.1) out-degrees (mean about 3), 8 labels -- with the bit-packed
+// closure and with every
 // tile kernel, in the host-driven loop with per-kernel CUDA events, times
 // reads of an L2-sized and an HBM-sized buffer, and keeps
 //   - the rate of each tile kernel (0/1 multiply-adds per second over its

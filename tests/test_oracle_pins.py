@@ -1,5 +1,6 @@
 """Pins for the CPU oracle: values printed in the paper, closed forms, textbook
 routines, brute force and invariants.  Nothing here touches the CUDA path."""
+import collections
 import itertools
 import json
 import os
@@ -382,3 +383,76 @@ def test_fixpoint_row_check_accepts_the_answer_and_catches_dropped_pairs():
     rows = [(q0, x) for x in xs[:3]] + [(1, xs[0])]
     assert (oracle.closure_rows_words(g, r, words.reshape(1, g.n, -1), rows) ==
             oracle.closure_rows(g, r, bits, rows)).all()
+
+
+# --- all-path semantics (Oracle C), pinned by plain enumeration ------------------
+
+def _walks(g, vs, vf, max_len):
+    """Every walk vs -> vf of at most max_len edges, by depth-first search over
+    the deduplicated edge set (a path is a sequence of (u, label, v) triples;
+    paths may repeat vertices and edges)."""
+    edges = sorted(set(zip(np.asarray(g.src).tolist(), np.asarray(g.lbl).tolist(), np.asarray(g.dst).tolist())))
+    out = collections.defaultdict(list)
+    for u, l, v in edges:
+        out[u].append((u, l, v))
+    found = []
+
+    def dfs(x, path):
+        if x == vf:
+            found.append(tuple(path))
+        if len(path) == max_len:
+            return
+        for e in out[x]:
+            path.append(e)
+            dfs(e[2], path)
+            path.pop()
+
+    dfs(vs, [])
+    return found
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_brute_paths_complete_for_the_regex(seed):
+    """Oracle C's paths of the RPQ (ab)*c|a*b* on small random graphs are
+    exactly the walks whose word Python's re module accepts: a dropped or an
+    extra path fails."""
+    rng = np.random.Generator(np.random.PCG64(7000 + seed))
+    n = int(rng.integers(2, 5))
+    es = [(int(rng.integers(0, n)), int(rng.integers(0, 3)), int(rng.integers(0, n))) for _ in range(int(rng.integers(3, 8)))]
+    g = W.make_graph(n, 3, es)
+    r = W.abc_dfa_rsm()
+    L = 5
+    total = 0
+    for vs in range(n):
+        for vf in range(n):
+            want = sorted((p for p in _walks(g, vs, vf, L)
+                           if re.fullmatch(W.ABC_REGEX, "".join("abc"[l] for _, l, _ in p))),
+                          key=lambda p: (len(p), p))
+            assert oracle.brute_paths(g, r, 0, vs, vf, L) == want, (seed, vs, vf)
+            total += len(want)
+    assert total > 0
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 4, 5, 6])
+def test_brute_paths_complete_for_anbn(seed):
+    """The same for S -> a S b | a b (Fig. 3's box): the words a^k b^k, k >= 1,
+    recognised by counting."""
+    rng = np.random.Generator(np.random.PCG64(7100 + seed))
+    n = int(rng.integers(2, 5))
+    es = [(int(rng.integers(0, n)), int(rng.integers(0, 2)), int(rng.integers(0, n))) for _ in range(int(rng.integers(5, 10)))]
+    g = W.make_graph(n, 2, es)
+    r = W.anbn_rsm()
+
+    def anbn(word):
+        k = len(word) // 2
+        return len(word) >= 2 and len(word) % 2 == 0 and word == [0] * k + [1] * k
+
+    L = 6
+    total = 0
+    for vs in range(n):
+        for vf in range(n):
+            want = sorted((p for p in _walks(g, vs, vf, L) if anbn([l for _, l, _ in p])),
+                          key=lambda p: (len(p), p))
+            assert oracle.brute_paths(g, r, 0, vs, vf, L) == want, (seed, vs, vf)
+            total += len(want)
+    assert total > 0  # the seeds are chosen so that some pair has a path
