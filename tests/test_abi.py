@@ -3,6 +3,7 @@ No compute call is made here (no GPU is needed)."""
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -47,3 +48,29 @@ def test_binding_names_match_the_header():
     src = open(cfpq.__file__).read()
     for n in _declared():
         assert f'"{n}"' in src, n
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes mirrors of the header's structs have the header's
+    size and field offsets (a C program built with gcc prints them)."""
+    from paper_2103_14688_gb300 import cfpq
+    structs = [cfpq.cfpq_options, cfpq.cfpq_rsm, cfpq.cfpq_run_stats, cfpq.cfpq_tuning, cfpq.cfpq_query]
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "cfpq.h"', "int main(void) {"]
+    for S in structs:
+        lines.append(f'    printf("{S.__name__} sizeof %zu\\n", sizeof({S.__name__}));')
+        for f, _ in S._fields_:
+            lines.append(f'    printf("{S.__name__} {f} %zu\\n", offsetof({S.__name__}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", inc, "-o", str(exe), str(src)])
+    got = {}
+    for ln in subprocess.check_output([str(exe)], text=True).splitlines():
+        s, f, v = ln.split()
+        got[(s, f)] = int(v)
+    for S in structs:
+        assert ctypes.sizeof(S) == got[(S.__name__, "sizeof")], S.__name__
+        for f, _ in S._fields_:
+            assert getattr(S, f).offset == got[(S.__name__, f)], (S.__name__, f)
