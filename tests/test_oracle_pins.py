@@ -385,6 +385,56 @@ def test_fixpoint_row_check_accepts_the_answer_and_catches_dropped_pairs():
             oracle.closure_rows(g, r, bits, rows)).all()
 
 
+def test_fixpoint_check_of_every_box_on_generated_grammars():
+    """The same check for every box of generated multi-box grammars (the
+    batched workload's recipe, small n), including nullable boxes: each box
+    b's row x is OR over finals f of b of C[(q0_b, x), (f, .)], plus (x, x)
+    when q0_b is final.  Oracle B's answer passes at every row; one pair
+    dropped from a row that keeps other pairs fails at that row for at least
+    some rows of each query."""
+    checked = 0
+    cases = [W.small_random_instance(900 + seed, n=24, m=60, n_labels=3, max_states=14) for seed in range(6)]
+    # S0 -> eps | a S1 b, S1 -> S0 c | c: a nullable box read by another
+    gram = {0: [(), (("t", 0), ("n", 1), ("t", 1))], 1: [(("n", 0), ("t", 2)), (("t", 2),)]}
+    rng = np.random.Generator(np.random.PCG64(906))
+    es = [(int(rng.integers(0, 24)), int(rng.integers(0, 3)), int(rng.integers(0, 24))) for _ in range(70)]
+    cases.append((W.make_graph(24, 3, es), W.grammar_to_rsm(gram, 2)))
+    assert cases[-1][1].state_final[cases[-1][1].box_start[0]]
+    for seed, (g, r) in enumerate(cases):
+        words = oracle.worklist_words(g, r).copy()
+        rows = [(int(r.box_start[b]), x) for b in range(r.n_boxes) for x in range(g.n)]
+        crow = oracle.closure_rows_words(g, r, words, rows)
+
+        def derived(b, x, c):
+            q0 = int(r.box_start[b])
+            row = np.zeros(g.n, dtype=bool)
+            for f in range(r.n_states):
+                if r.state_final[f] and r.state_box[f] == b:
+                    row |= c[f * g.n:(f + 1) * g.n]
+            if r.state_final[q0]:
+                row[x] = True
+            return row
+
+        for k, (q0, x) in enumerate(rows):
+            b = int(r.state_box[q0])
+            have = np.unpackbits(words[b, x].view(np.uint8), bitorder="little")[: g.n].astype(bool)
+            assert (derived(b, x, crow[k]) == have).all(), (seed, b, x)
+        caught = 0
+        for b in range(r.n_boxes):
+            for x in range(g.n):
+                ys = np.flatnonzero(np.unpackbits(words[b, x].view(np.uint8), bitorder="little")[: g.n])
+                if len(ys) < 2:
+                    continue
+                bad = words.copy()
+                bad[b, x, ys[0] >> 6] &= ~np.uint64(1 << (int(ys[0]) & 63))
+                c = oracle.closure_rows_words(g, r, bad, [(int(r.box_start[b]), x)])[0]
+                got = np.unpackbits(bad[b, x].view(np.uint8), bitorder="little")[: g.n].astype(bool)
+                caught += int((derived(b, x, c) != got).any())
+                checked += 1
+        assert caught >= 1 or checked == 0, seed
+    assert checked > 0
+
+
 # --- all-path semantics (Oracle C), pinned by plain enumeration ------------------
 
 def _walks(g, vs, vf, max_len):
