@@ -20,6 +20,8 @@
 #include <map>
 #include <set>
 #include <tuple>
+#include <unordered_map>
+#include <unordered_set>
 #include <utility>
 #include <vector>
 
@@ -126,19 +128,28 @@ struct PathEnum {
         }
         return fdist.emplace(v, std::move(d)).first->second.data();
     }
-    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, std::set<std::vector<uint32_t>>> memo;
+    using Key = std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>;
+    struct KeyHash {
+        size_t operator()(const Key &k) const {
+            uint64_t h = ((uint64_t)std::get<0>(k) << 32 | std::get<3>(k)) * 0x9E3779B97F4A7C15ull;
+            h ^= ((uint64_t)std::get<1>(k) << 32 | std::get<2>(k)) * 0xC2B2AE3D27D4EB4Full;
+            return (size_t)(h ^ (h >> 31));
+        }
+    };
+    // the path set of every key (references stay valid when the map rehashes)
+    std::unordered_map<Key, std::set<std::vector<uint32_t>>, KeyHash> memo;
     size_t stored = 0, cap = 4000000;
     bool over = false;
 
     size_t key_cap = 1u << 20;
-    using Key = std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>;
     // Worklist of keys to (re)evaluate and, per key, the keys whose
     // evaluation read it: a key is evaluated again only when a set it reads
     // has grown.
     std::deque<Key> work;
-    std::set<Key> queued;
-    std::map<Key, std::set<Key>> readers;
-    const Key *reading = nullptr;  // key under evaluation
+    std::unordered_set<Key, KeyHash> queued;
+    std::unordered_map<Key, std::vector<Key>, KeyHash> readers;
+    const Key *reading = nullptr;                // key under evaluation
+    std::unordered_set<Key, KeyHash> read_now;  // the keys its evaluation read
 
     const std::set<std::vector<uint32_t>> &get(uint32_t N, uint32_t x, uint32_t y, uint32_t len) {
         const Key key = std::make_tuple(N, x, y, len);
@@ -150,7 +161,7 @@ struct PathEnum {
             queued.insert(key);
             if (!lay.count(Target(N, y))) wanted.insert(Target(N, y));
         }
-        if (reading) readers[key].insert(*reading);
+        if (reading) read_now.insert(key);
         return it->second;
     }
 
@@ -239,8 +250,10 @@ struct PathEnum {
             work.pop_front();
             queued.erase(k);
             reading = &k;
+            read_now.clear();
             auto v = eval(std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k));
             reading = nullptr;
+            for (const Key &rk : read_now) readers[rk].push_back(k);
             auto &cur = memo[k];
             if (v.size() == cur.size()) continue;
             stored += v.size() - cur.size();
