@@ -128,6 +128,48 @@ struct PathEnum {
         }
         return fdist.emplace(v, std::move(d)).first->second.data();
     }
+    // Graph distance to y over any labels, capped like dist_from (breadth-first
+    // over the reversed edges): a path of `len` edges ending at y passes a
+    // vertex u after k edges only if the distance from u to y is <= len - k.
+    // The layers give a weaker bound, as they count a nonterminal edge as one
+    // edge whatever the graph distance it spans.
+    std::vector<uint32_t> roff, rsrc;  // reversed terminal edges, by target
+    std::map<uint32_t, std::vector<uint16_t>> bdist;
+    uint32_t dist_L = ~0u;             // the bound the cached distances were taken to
+    const uint16_t *dist_to(uint32_t y) {
+        if (roff.size() != (size_t)n + 1) {
+            roff.assign((size_t)n + 1, 0);
+            for (uint32_t d : ed) ++roff[d + 1];
+            for (uint32_t v = 0; v < n; ++v) roff[v + 1] += roff[v];
+            rsrc.resize(ed.size());
+            std::vector<uint32_t> fill(roff.begin(), roff.end() - 1);
+            for (size_t e = 0; e < ed.size(); ++e) rsrc[fill[ed[e]]++] = es[e];
+        }
+        auto it = bdist.find(y);
+        if (it != bdist.end()) return it->second.data();
+        const uint16_t far = (uint16_t)std::min<uint32_t>(Lmax + 1u, 65535u);
+        std::vector<uint16_t> d(n, far);
+        std::vector<uint32_t> cur{y}, nxt;
+        d[y] = 0;
+        for (uint32_t depth = 1; depth <= Lmax && !cur.empty(); ++depth) {
+            nxt.clear();
+            for (uint32_t a : cur)
+                for (uint32_t k = roff[a]; k < roff[a + 1]; ++k)
+                    if (d[rsrc[k]] == far) {
+                        d[rsrc[k]] = (uint16_t)depth;
+                        nxt.push_back(rsrc[k]);
+                    }
+            cur.swap(nxt);
+        }
+        return bdist.emplace(y, std::move(d)).first->second.data();
+    }
+    // both distance caches hold distances capped at the current bound
+    void check_dist_bound() {
+        if (dist_L == Lmax) return;
+        fdist.clear();
+        bdist.clear();
+        dist_L = Lmax;
+    }
     using Key = std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>;
     struct KeyHash {
         size_t operator()(const Key &k) const {
@@ -178,7 +220,9 @@ struct PathEnum {
         std::vector<std::map<std::pair<uint32_t, uint32_t>, PSet>> layer(len + 1);
         const uint32_t q0 = r->box_start[N];
         word_lengths();
-        if (!words[N][len] || !live(q0, x, len)) return PSet();
+        check_dist_bound();
+        const uint16_t *dy = dist_to(y);
+        if (!words[N][len] || !live(q0, x, len) || dy[x] > len) return PSet();
         layer[0][{q0, x}].insert(std::vector<uint32_t>());
         for (uint32_t k = 0; k <= len; ++k) {
             bool grew = true;
@@ -193,7 +237,7 @@ struct PathEnum {
                         if (t.kind == 0) {
                             if (k + 1 > len) continue;
                             for (uint32_t e = eoff[v]; e < eoff[v + 1]; ++e) {
-                                if (el[e] != t.sym || !live(t.to, ed[e], len - k - 1)) continue;
+                                if (el[e] != t.sym || dy[ed[e]] > len - k - 1 || !live(t.to, ed[e], len - k - 1)) continue;
                                 PSet &Dst = layer[k + 1][{t.to, ed[e]}];
                                 for (const auto &p : S) {
                                     auto q = p;
@@ -211,7 +255,9 @@ struct PathEnum {
                                 while (b) {
                                     const uint32_t v2 = (uint32_t)(w * 64 + (uint64_t)__builtin_ctzll(b));
                                     b &= b - 1;
-                                    for (uint32_t j = dv[v2]; k + j <= len; ++j) {
+                                    // j <= len - k - (distance from v2 to y)
+                                    if (dy[v2] > len - k) continue;
+                                    for (uint32_t j = dv[v2]; k + j + dy[v2] <= len; ++j) {
                                         if (!words[t.sym][j] || !live(t.to, v2, len - k - j)) continue;
                                         const PSet &sub = get(t.sym, v, v2, j);
                                         if (sub.empty()) continue;
