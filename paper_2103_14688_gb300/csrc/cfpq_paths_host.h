@@ -170,6 +170,19 @@ struct PathEnum {
         bdist.clear();
         dist_L = Lmax;
     }
+    // Without nonterminal transitions the layers are exact product distances,
+    // at least the graph distance: the distance bound adds nothing there.
+    std::vector<uint16_t> no_dist;
+    int has_nt = -1;
+    const uint16_t *target_dist(uint32_t y) {
+        if (has_nt < 0) {
+            has_nt = 0;
+            for (const auto &t : r->tr) has_nt |= t.kind != 0 ? 1 : 0;
+        }
+        if (has_nt) return dist_to(y);
+        if (no_dist.size() != n) no_dist.assign(n, 0);
+        return no_dist.data();
+    }
     using Key = std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>;
     struct KeyHash {
         size_t operator()(const Key &k) const {
@@ -221,7 +234,7 @@ struct PathEnum {
         const uint32_t q0 = r->box_start[N];
         word_lengths();
         check_dist_bound();
-        const uint16_t *dy = dist_to(y);
+        const uint16_t *dy = target_dist(y);
         if (!words[N][len] || !live(q0, x, len) || dy[x] > len) return PSet();
         layer[0][{q0, x}].insert(std::vector<uint32_t>());
         for (uint32_t k = 0; k <= len; ++k) {
