@@ -109,6 +109,7 @@ struct PathEnum {
     // Graph distance from v over any labels, capped at Lmax + 1 (breadth-first,
     // depth Lmax): a subpath v -> v2 of j edges exists only if it is <= j.
     std::map<uint32_t, std::vector<uint16_t>> fdist;
+    size_t dist_cache_bytes = (size_t)1 << 30;  // per distance cache
     const uint16_t *dist_from(uint32_t v) {
         auto it = fdist.find(v);
         if (it != fdist.end()) return it->second.data();
@@ -126,6 +127,9 @@ struct PathEnum {
                     }
             cur.swap(nxt);
         }
+        // a pointer from an earlier call is not used after this one, so the
+        // cache can be dropped when it outgrows its share of host memory
+        if ((fdist.size() + 1) * (size_t)n * sizeof(uint16_t) > dist_cache_bytes) fdist.clear();
         return fdist.emplace(v, std::move(d)).first->second.data();
     }
     // Graph distance to y over any labels, capped like dist_from (breadth-first
@@ -161,6 +165,7 @@ struct PathEnum {
                     }
             cur.swap(nxt);
         }
+        if ((bdist.size() + 1) * (size_t)n * sizeof(uint16_t) > dist_cache_bytes) bdist.clear();
         return bdist.emplace(y, std::move(d)).first->second.data();
     }
     // both distance caches hold distances capped at the current bound

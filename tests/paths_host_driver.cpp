@@ -9,6 +9,7 @@
 // Built by tests/test_paths_host.py with g++; test infrastructure only.
 #include <stdint.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -46,6 +47,8 @@ extern "C" int phd_paths(uint32_t n, uint64_t m, const uint32_t *tri, uint32_t Q
     P.r = &r;
     P.n = n;
     P.wn = wn;
+    // a test can shrink the distance caches to a few entries (their eviction)
+    if (const char *e = std::getenv("PHD_DIST_CACHE_ENTRIES")) P.dist_cache_bytes = (size_t)std::atoi(e) * n * 2;
     P.Qd = Q;
     P.Wd = (uint32_t)wn;
     P.eoff.assign(n + 1, 0);

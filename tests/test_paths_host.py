@@ -127,3 +127,13 @@ def test_word_lengths_against_brute_force(lib, seed):
             want = any(oracle.rsm_accepts(r, g.n_terminals, b, list(w))
                        for w in itertools.product(range(g.n_terminals), repeat=j))
             assert got[b, j] == want, (b, j)
+
+
+def test_small_distance_caches(lib, monkeypatch):
+    """Distance caches that hold two entries (dropped as they fill) give the
+    same paths."""
+    monkeypatch.setenv("PHD_DIST_CACHE_ENTRIES", "2")
+    g, r = W.dyck_zipf(n=24, k=2, seed=3)
+    _check(lib, g, r, [(0, vs, vf, 6) for vs in range(g.n) for vf in range(g.n)])
+    g, r = W.small_random_instance(305, n=7, m=14, n_labels=2, max_states=12)
+    _check(lib, g, r, [(b, vs, vf, 5) for b in range(r.n_boxes) for vs in range(g.n) for vf in range(g.n)])
