@@ -833,7 +833,7 @@ def run_other(args):
         from collections import deque
         out = []
         for name, (g, r), lens in (("rpq_abc_n8192_deg8", W.rpq_abc(n=8192, out_deg=8), (4, 6, 8)),
-                                   ("dyck4_zipf_n4096", W.dyck_zipf(n=4096), (4, 8, 12))):
+                                   ("dyck4_zipf_n4096", W.dyck_zipf(n=4096), (4, 8, 12, 16))):
             ctx = cfpq.Context()
             ctx.load_graph(g)
             ctx.load_rsm(r)
