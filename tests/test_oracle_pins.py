@@ -169,6 +169,22 @@ def test_brute_force_exact_on_dags(seed):
     assert (oracle.worklist(g, r) == a.m2).all()
 
 
+def test_brute_reach_bound_is_exact():
+    """On the chain 0 -a-> 1 ... -a-> k -b-> ... -b-> 2k with S -> a S b | a b
+    the pair (k-i, k+i) needs exactly 2i edges, so brute_reach with bound L
+    holds exactly the pairs with 2i <= L (an off-by-one in the bound fails)."""
+    k = 4
+    es = [(v, 0, v + 1) for v in range(k)] + [(v, 1, v + 1) for v in range(k, 2 * k)]
+    g = W.make_graph(2 * k + 1, 2, es)
+    r = W.grammar_to_rsm({0: [(("t", 0), ("n", 0), ("t", 1)), (("t", 0), ("t", 1))]}, 1)
+    for L in range(0, 2 * k + 2):
+        want = np.zeros((g.n, g.n), dtype=bool)
+        for i in range(1, k + 1):
+            if 2 * i <= L:
+                want[k - i, k + i] = True
+        assert (oracle.brute_reach(g, r, L)[0] == want).all(), L
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_brute_force_subset_on_cyclic(seed):
     g, r = W.small_random_instance(500 + seed, n=4, m=6, n_labels=2)
