@@ -9,8 +9,10 @@
 // The forward walk keeps a partial path of k edges ending at (s, v) only if
 // (s, v) is in layer len - k of the backward search from the targets of
 // (N, y), run on the device (PathsDev): the vertices that can still reach a
-// target with the edges left.  A nonterminal step v -> v2 asks for subpaths
-// of j edges only from j = the graph distance from v to v2 on.
+// target with the edges left; and, for RSMs with nonterminal transitions,
+// only if the graph distance from v to y is at most len - k.  A nonterminal
+// step v -> v2 asks for subpaths of j edges only from j = the graph distance
+// from v to v2 on.
 #pragma once
 #include <stdint.h>
 
