@@ -86,13 +86,13 @@ def test_rpq_iteration_count_equals_oracle_a(cfpq, seed):
         assert (ctx.reachable_bits(0) == ref.m2[0]).all()
 
 
-def test_rpq_full_size_sampled(cfpq):
+def test_rpq_full_size_whole_answer(cfpq):
+    """The RPQ workload at its full size (n = 8192, 8 out-edges): the whole
+    answer equals Oracle B's (about 20 s of one host core)."""
     g, r = W.rpq_abc()
     ctx, st, out = _run(cfpq, g, r)
     rng = np.random.Generator(np.random.PCG64(7))
-    srcs = sorted(set(rng.integers(0, g.n, 24).tolist()) | {0, g.n - 1})
-    ref = oracle.worklist(g, r, sources=srcs)
-    assert (out[0][srcs] == ref[0][srcs]).all()
+    assert (ctx.reachable_words(0) == oracle.worklist_words(g, r)[0]).all()
     assert st.iterations == 2
     # closure rows of sampled product vertices = BFS over M3 (RPQ: M3 is fixed)
     rows = [(int(s), int(x)) for s, x in zip(rng.integers(0, r.n_states, 12), rng.integers(0, g.n, 12))]
