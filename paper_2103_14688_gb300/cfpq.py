@@ -223,7 +223,11 @@ def default_options(**kw) -> cfpq_options:
     lib = load()
     o = cfpq_options()
     lib.cfpq_default_options(ctypes.byref(o))
+    names = {f for f, _ in cfpq_options._fields_}
     for k, v in kw.items():
+        # a ctypes structure would keep a misspelt name as a plain attribute
+        if k not in names:
+            raise TypeError(f"unknown cfpq option {k!r}")
         setattr(o, k, v)
     return o
 

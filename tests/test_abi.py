@@ -74,3 +74,44 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert ctypes.sizeof(S) == got[(S.__name__, "sizeof")], S.__name__
         for f, _ in S._fields_:
             assert getattr(S, f).offset == got[(S.__name__, f)], (S.__name__, f)
+
+
+def test_default_options_reject_unknown_names():
+    from paper_2103_14688_gb300 import cfpq
+    o = cfpq.default_options(closure_mode=cfpq.CFPQ_CLOSURE_TC_FP4, tile_format=cfpq.CFPQ_TILES_NVFP4, tile_ratio=64)
+    assert (o.closure_mode, o.tile_format, o.tile_ratio) == (cfpq.CFPQ_CLOSURE_TC_FP4, cfpq.CFPQ_TILES_NVFP4, 64)
+    assert o.struct_size == ctypes.sizeof(cfpq.cfpq_options) and o.loop_mode == cfpq.CFPQ_LOOP_DEVICE
+    with pytest.raises(TypeError):
+        cfpq.default_options(tile_fromat=2)
+
+
+def test_create_validates_its_options_before_touching_a_device():
+    """Options out of range are refused with INVALID_ARG (or UNSUPPORTED) before
+    any CUDA call, so this runs on a machine without a GPU."""
+    from paper_2103_14688_gb300 import cfpq
+    lib = cfpq.load()
+
+    def create(**kw):
+        o = cfpq.default_options(**kw)
+        h = ctypes.c_void_p()
+        return lib.cfpq_create(ctypes.byref(h), ctypes.byref(o), None)
+
+    assert create(closure_mode=99) == cfpq.CFPQ_ERR_INVALID_ARG
+    assert create(tile_format=99) == cfpq.CFPQ_ERR_INVALID_ARG
+    assert create(loop_mode=7) == cfpq.CFPQ_ERR_INVALID_ARG
+    assert create(profile=1) == cfpq.CFPQ_ERR_INVALID_ARG  # profiling needs the host-driven loop
+    assert create(closure_mode=cfpq.CFPQ_CLOSURE_TC_I8) == cfpq.CFPQ_ERR_UNSUPPORTED
+    assert create(struct_size=3) == cfpq.CFPQ_ERR_INVALID_ARG
+
+
+def test_create_fails_loudly_without_a_gpu():
+    """No CPU path: without a CUDA device the context cannot be created."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2103_14688_gb300 import cfpq
+    lib = cfpq.load()
+    o = cfpq.default_options()
+    h = ctypes.c_void_p()
+    assert lib.cfpq_create(ctypes.byref(h), ctypes.byref(o), None) == cfpq.CFPQ_ERR_CUDA
+    assert not h.value
