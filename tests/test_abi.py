@@ -115,3 +115,23 @@ def test_create_fails_loudly_without_a_gpu():
     h = ctypes.c_void_p()
     assert lib.cfpq_create(ctypes.byref(h), ctypes.byref(o), None) == cfpq.CFPQ_ERR_CUDA
     assert not h.value
+
+
+def test_null_and_size_checks_without_gpu():
+    """Calls refuse NULL handles and wrong struct sizes with INVALID_ARG,
+    before any CUDA call."""
+    from paper_2103_14688_gb300 import cfpq
+    lib = cfpq.load()
+    t = cfpq.cfpq_tuning()
+    t.struct_size = ctypes.sizeof(cfpq.cfpq_tuning)
+    assert lib.cfpq_tune(None, 0, ctypes.byref(t)) == cfpq.CFPQ_ERR_INVALID_ARG
+    assert lib.cfpq_run(None, None) == cfpq.CFPQ_ERR_INVALID_ARG
+    assert lib.cfpq_destroy(None) == cfpq.CFPQ_OK
+    h = ctypes.c_void_p()
+    e = (ctypes.c_uint32 * 1)(0)
+    for kw in ({"closure_mode": 99}, {"tile_format": 99}, {"struct_size": 3},
+               {"closure_mode": cfpq.CFPQ_CLOSURE_TC_I8}):
+        o = cfpq.default_options(**kw)
+        rc = lib.cfpq_server_create(ctypes.byref(h), ctypes.byref(o), None, 4, 1, 1, e, e, e)
+        assert rc in (cfpq.CFPQ_ERR_INVALID_ARG, cfpq.CFPQ_ERR_UNSUPPORTED), (kw, rc)
+        assert not h.value
